@@ -1,0 +1,234 @@
+/*
+ * sgagg.h -- C ABI of a GPU (sm_103a) implementation of sort-based grouping
+ * and aggregation with early aggregation during run generation and wide
+ * merging (Do, Graefe, Naughton, "Efficient sorting, duplicate removal,
+ * grouping, and aggregation", arXiv 2010.00152).
+ *
+ * Operation (Sec. 1, "select A, B, count(*), sum(X), min(Z), max(Y) ...
+ * group by A, B"; Sec. 3.3 on intermediate rows carrying partial aggregates;
+ * Sec. 6.1 on sorted output): one output row per distinct key, keys strictly
+ * ascending (unsigned, lexicographic over the key columns), with int64
+ * count(*), sum (wrapping modulo 2^64), min and max (signed) per requested
+ * aggregate.  The result is unique and bit-exact.
+ *
+ * Method (Sec. 3, Sec. 4, Sec. 6.1):
+ *   - the input is consumed in batches of memory_budget_rows rows
+ *     (read-sort-write cycles); each batch is sorted and its equal keys folded
+ *     before its run is written (early aggregation), so a run holds each key
+ *     of its batch once;
+ *   - one wide merge consumes all runs at once, folding equal keys across
+ *     runs, and emits the final sorted output; a batch that covers the whole
+ *     input is written straight to the output (no run, no merge).
+ *
+ * Conventions for every call:
+ *   - Pointers named "device" must point to memory the current CUDA device
+ *     can access (device memory, or mapped/managed memory).  Arrays *of*
+ *     pointers (key columns, payload columns, output columns) are host arrays
+ *     that the call reads before it returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is stream-ordered.  sgagg_aggregate may synchronize the
+ *     stream internally while planning (it reads small counters back); all
+ *     results are final once sgagg_result_rows returns SGAGG_OK.
+ *   - The caller owns every input and output buffer; the library never frees
+ *     them and never writes to inputs.  The handle owns its workspace, run
+ *     arena and pinned host buffers; sgagg_destroy frees them.
+ *   - A handle is one logical sequence of calls and is not thread-safe.  Use
+ *     one handle per host thread.
+ *   - Errors are status codes; sgagg_last_error(h) gives a message.  Argument
+ *     errors are reported before any GPU work is enqueued.
+ */
+#ifndef SGAGG_H
+#define SGAGG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgagg_ctx *sgagg_t;
+
+typedef enum {
+    SGAGG_OK = 0,
+    SGAGG_EINVAL = 1,    /* bad argument (null pointer, n < 0, bad spec, key wider than 64 bits) */
+    SGAGG_ENOMEM = 2,    /* device or pinned host allocation failed */
+    SGAGG_ECUDA = 3,     /* a CUDA runtime call failed */
+    SGAGG_ETIMEOUT = 4,  /* a bounded device-side wait gave up (see SGAGG_OPT_SPIN_LIMIT) */
+    SGAGG_ECAPACITY = 5, /* out_capacity smaller than the number of distinct keys */
+    SGAGG_ESTATE = 6     /* call out of order (e.g. result_rows before any aggregate) */
+} sgagg_status;
+
+/* Aggregates of the problem statement (Sec. 1): count(*), sum, min, max. */
+typedef enum { SGAGG_COUNT = 0, SGAGG_SUM = 1, SGAGG_MIN = 2, SGAGG_MAX = 3 } sgagg_op;
+
+/* One aggregate: op over payload column `col` (ignored for COUNT). */
+typedef struct {
+    int32_t op;
+    int32_t col;
+} sgagg_agg;
+
+/* The aggregate list; output column a holds aggregate a. */
+typedef struct {
+    int32_t n_aggs;          /* 0 .. 32; 0 = duplicate removal (keys only) */
+    const sgagg_agg *aggs;   /* host array of n_aggs entries */
+} sgagg_spec;
+
+/*
+ * Key columns, column 0 most significant.  Each column is an unsigned
+ * integer array of 1, 2, 4 or 8 bytes per row; the widths add up to at most
+ * 8 bytes.  They are combined into one order-preserving normalized key
+ * (Sec. 2.4, normalized keys), so the output order is the lexicographic
+ * order of the key tuples.
+ */
+typedef struct {
+    int32_t n_cols;              /* 1 .. 8 */
+    const int32_t *bytes;        /* host array: width of each column in bytes */
+    const void *const *cols;     /* host array of device pointers, one per column */
+} sgagg_keys;
+
+/* Counters of the last sgagg_aggregate / sgagg_aggregate_batched call. */
+typedef struct {
+    int64_t n_rows;              /* input rows */
+    int64_t batches;             /* ceil(n / memory_budget_rows) */
+    int64_t runs;                /* runs written (0 when one batch covers the input) */
+    int64_t run_rows;            /* rows written to all runs (the paper's spill volume) */
+    int64_t run_bytes_device;    /* bytes of runs held in the device arena */
+    int64_t run_bytes_host;      /* bytes of runs spilled to pinned host memory */
+    int64_t peak_scratch_bytes;  /* workspace bytes in use (sort buffers, tables, status) */
+    int64_t out_rows;            /* distinct keys */
+    int64_t out_bytes;           /* output bytes (key columns + aggregates) */
+    int64_t prefold_passes;      /* tile-level pre-aggregation passes run */
+    int64_t split_segments;      /* key ranges that needed a recursive split */
+    int64_t merge_tiles;         /* tiles of the wide merge */
+    int64_t kernel_launches;     /* kernels launched by the call */
+    /* Per kernel class (see SGAGG_K_*): launches, compulsory bytes (every
+     * input of the launch read once, every output written once) and, with
+     * SGAGG_OPT_TIMING, the summed CUDA-event time of the launches in ms. */
+    int64_t class_launches[8];
+    int64_t class_bytes[8];
+    double class_ms[8];
+} sgagg_stats_t;
+
+/* Kernel classes of sgagg_stats_t. */
+enum {
+    SGAGG_K_PROBE = 0,      /* key sample / key range */
+    SGAGG_K_HIST = 1,       /* per-tile digit histogram */
+    SGAGG_K_PLAN = 2,       /* tile scans and chunk planner */
+    SGAGG_K_SCATTER = 3,    /* rows to their key-range bucket */
+    SGAGG_K_PREFOLD = 4,    /* tile sort+fold before partitioning */
+    SGAGG_K_RUNGEN = 5,     /* chunk sort+fold writing a run (or the output) */
+    SGAGG_K_MERGE = 6,      /* wide merge: sort+fold of merge tiles */
+    SGAGG_K_OTHER = 7       /* gathers and offsets of split key ranges */
+};
+
+/* Options for sgagg_set_option. */
+typedef enum {
+    SGAGG_OPT_PREFOLD = 0,        /* -1 auto (sampled duplicate rate), 0 off, 1 on */
+    SGAGG_OPT_ARENA_CAP = 1,      /* max bytes of runs kept in device memory; more spill
+                                     to pinned host memory.  Default: no cap (-1). */
+    SGAGG_OPT_RADIX_BITS = 2,     /* bits of the batch partitioning digit, 0 = auto (1..16) */
+    SGAGG_OPT_SPIN_LIMIT = 3,     /* iteration cap of device-side waits (default 1<<26);
+                                     exceeded -> SGAGG_ETIMEOUT, no hang */
+    SGAGG_OPT_FANIN_CAP = 4,      /* max runs in one wide merge; more runs get preliminary
+                                     merges of the smallest runs first (Sec. 4.3). 0 = auto */
+    SGAGG_OPT_FAULT_ALLOC = 5,    /* test hook: fail the k-th internal allocation (0 = off) */
+    SGAGG_OPT_TIMING = 6,         /* 1: time every kernel class with CUDA events (class_ms) */
+    SGAGG_OPT_TEST_STALL = 7      /* test hook: in the next sort+fold launch the first chunk
+                                     never publishes its row count, so the bounded waits of
+                                     the others run out -> SGAGG_ETIMEOUT (no hang) */
+} sgagg_option;
+
+/*
+ * Create a handle.  memory_budget_rows (M >= 1) is the number of input rows
+ * in one batch of run generation, i.e. the paper's memory size in rows
+ * (Sec. 3: read-sort-write cycles make runs of at most M rows).
+ * Returns SGAGG_EINVAL for M < 1 or out == NULL.
+ */
+sgagg_status sgagg_create(int64_t memory_budget_rows, sgagg_t *out);
+
+/* Set an option (see sgagg_option).  SGAGG_EINVAL on an unknown key/value. */
+sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value);
+
+/*
+ * Group n input rows (device pointers) and write the sorted, aggregated
+ * result.
+ *   keys          key columns (device pointers), n rows each
+ *   payload_cols  host array of n_payload device pointers to int64[n]
+ *   spec          aggregates; SUM/MIN/MAX name a payload column
+ *   out_keys      host array of keys->n_cols device pointers; column c receives
+ *                 the distinct keys' column c (same width as the input column)
+ *   out_aggs      host array of spec->n_aggs device pointers to int64
+ *   out_capacity  rows available in every output column; n always suffices.
+ *                 Fewer rows than distinct keys -> SGAGG_ECAPACITY from
+ *                 sgagg_result_rows (nothing beyond out_capacity is written).
+ * n == 0 is valid and yields 0 rows.  Inputs must not overlap outputs.
+ */
+sgagg_status sgagg_aggregate(sgagg_t h, const sgagg_keys *keys,
+                             const int64_t *const *payload_cols, int32_t n_payload,
+                             int64_t n, const sgagg_spec *spec,
+                             void *const *out_keys, int64_t *const *out_aggs,
+                             int64_t out_capacity, void *stream);
+
+/*
+ * Same operation with HOST buffers: copies the inputs to the device (the
+ * copies of batch b+1 overlap the run generation of batch b), runs the
+ * device path and copies the result back.  Synchronous.  *rows receives the
+ * number of distinct keys.  Host buffers may be pageable; pinned buffers
+ * copy faster.
+ */
+sgagg_status sgagg_aggregate_host(sgagg_t h, const sgagg_keys *keys,
+                                  const int64_t *const *payload_cols, int32_t n_payload,
+                                  int64_t n, const sgagg_spec *spec,
+                                  void *const *out_keys, int64_t *const *out_aggs,
+                                  int64_t out_capacity, int64_t *rows, void *stream);
+
+/* Synchronize the stream of the last call and return its number of output
+ * rows (distinct keys), or the device-side error of that call. */
+sgagg_status sgagg_result_rows(sgagg_t h, int64_t *rows);
+
+/* Temporary bytes of the last call: bytes of all runs (device and host) plus
+ * the peak workspace in use.  -1 for a NULL handle. */
+int64_t sgagg_temp_bytes(sgagg_t h);
+
+/* Counters of the last call (synchronizes its stream). */
+sgagg_status sgagg_stats(sgagg_t h, sgagg_stats_t *out);
+
+/*
+ * One independent group-by instance of a batched call.  All pointers are
+ * device pointers; the key is one unsigned column of key_bytes (1/2/4/8)
+ * bytes per row.  *out_rows (device int64) receives the instance's distinct
+ * key count, or -1 if out_capacity was too small.
+ */
+typedef struct {
+    const void *keys;
+    int32_t key_bytes;
+    int32_t n_payload;
+    const int64_t *const *payload;   /* device array of n_payload device pointers */
+    int64_t n;
+    void *out_keys;                  /* key_bytes per row */
+    int64_t *const *out_aggs;        /* device array of spec->n_aggs device pointers */
+    int64_t out_capacity;
+    int64_t *out_rows;               /* device */
+} sgagg_instance;
+
+/*
+ * Run `count` independent instances (sharing one aggregate spec) with one
+ * persistent kernel launch per size class, captured once in a CUDA graph per
+ * (count, spec) shape and replayed.  `inst` is a host array.  Asynchronous:
+ * results are final when the stream reaches this point; sgagg_result_rows
+ * returns the total of all instances' rows and any device-side error.
+ */
+sgagg_status sgagg_aggregate_batched(sgagg_t h, const sgagg_instance *inst, int32_t count,
+                                     const sgagg_spec *spec, void *stream);
+
+/* Free the handle and everything it owns.  NULL is ignored. */
+void sgagg_destroy(sgagg_t h);
+
+/* Message of the last error on this handle ("" if none).  Valid until the
+ * next call on the handle. */
+const char *sgagg_last_error(sgagg_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGAGG_H */

@@ -1,0 +1,233 @@
+// sg_common.cuh -- shared device definitions of the grouping path.
+//
+// Row formats (Sec. 3.3: the row format inside runs may differ from input and
+// output rows):
+//   raw rows    key + the payload columns the aggregates read;
+//   state rows  key + one int64 partial aggregate per output aggregate.
+// A FoldDesc says how to derive every state column from a source row: from a
+// source column (or the constant 1 for count(*) of raw rows) combined with
+// SUM, MIN or MAX ("row-plus-row accumulation", Sec. 6.1).
+#pragma once
+#include <cstdint>
+#include <cuda/atomic>
+
+namespace sg {
+
+constexpr int kMaxKeyCols = 8;
+constexpr int kMaxCols = 32;
+
+enum : int8_t { OP_SUM = 0, OP_MIN = 1, OP_MAX = 2 };
+
+// Error codes written to the device error word (host maps them to statuses).
+enum : int { ERR_NONE = 0, ERR_TIMEOUT = 1, ERR_CAPACITY = 2, ERR_INTERNAL = 3 };
+
+// ---------------------------------------------------------------------------
+// Keys.  Normalized key (Sec. 2.4): unsigned key columns concatenated with
+// column 0 most significant, right-aligned in a uint64.
+// ---------------------------------------------------------------------------
+struct KeyCols {
+  int n_cols;
+  int bytes[kMaxKeyCols];
+  int shift[kMaxKeyCols];        // bits below column c in the normalized key
+  const void* cols[kMaxKeyCols];
+};
+
+struct KeyOut {
+  int n_cols;
+  int bytes[kMaxKeyCols];
+  int shift[kMaxKeyCols];
+  void* cols[kMaxKeyCols];
+};
+
+__device__ __forceinline__ uint64_t load_col(const void* p, int bytes, int64_t i) {
+  switch (bytes) {
+    case 1: return __ldg(reinterpret_cast<const uint8_t*>(p) + i);
+    case 2: return __ldg(reinterpret_cast<const uint16_t*>(p) + i);
+    case 4: return __ldg(reinterpret_cast<const uint32_t*>(p) + i);
+    default: return __ldg(reinterpret_cast<const unsigned long long*>(p) + i);
+  }
+}
+
+__device__ __forceinline__ uint64_t load_key(const KeyCols& k, int64_t i) {
+  if (k.n_cols == 1) return load_col(k.cols[0], k.bytes[0], i);
+  uint64_t v = 0;
+  for (int c = 0; c < k.n_cols; ++c) v |= load_col(k.cols[c], k.bytes[c], i) << k.shift[c];
+  return v;
+}
+
+__device__ __forceinline__ void store_key(const KeyOut& k, int64_t j, uint64_t key) {
+  for (int c = 0; c < k.n_cols; ++c) {
+    uint64_t v = k.shift[c] >= 64 ? 0 : (key >> k.shift[c]);
+    switch (k.bytes[c]) {
+      case 1: reinterpret_cast<uint8_t*>(k.cols[c])[j] = (uint8_t)v; break;
+      case 2: reinterpret_cast<uint16_t*>(k.cols[c])[j] = (uint16_t)v; break;
+      case 4: reinterpret_cast<uint32_t*>(k.cols[c])[j] = (uint32_t)v; break;
+      default: reinterpret_cast<unsigned long long*>(k.cols[c])[j] = v; break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row sources.
+// ---------------------------------------------------------------------------
+enum : int { SRC_RAW = 0, SRC_SOA = 1, SRC_AOS = 2 };
+
+struct RowSrc {
+  int kind;
+  int ncols;                        // columns carried (payload or state)
+  int64_t offset;                   // added to every row index
+  KeyCols key;                          // SRC_RAW
+  const unsigned long long* keys;       // SRC_SOA
+  const long long* cols[kMaxCols];      // SRC_RAW payload / SRC_SOA state columns
+  const long long* aos;                 // SRC_AOS: rows of (1 + ncols) words
+};
+
+__device__ __forceinline__ uint64_t src_key(const RowSrc& s, int64_t i) {
+  int64_t r = s.offset + i;
+  if (s.kind == SRC_AOS) return (uint64_t)s.aos[r * (1 + s.ncols)];
+  if (s.kind == SRC_SOA) return __ldg(s.keys + r);
+  return load_key(s.key, r);
+}
+
+__device__ __forceinline__ long long src_col(const RowSrc& s, int c, int64_t i) {
+  int64_t r = s.offset + i;
+  if (s.kind == SRC_AOS) return s.aos[r * (1 + s.ncols) + 1 + c];
+  return __ldg(s.cols[c] + r);
+}
+
+struct FoldDesc {
+  int n_state;
+  int8_t src[kMaxCols];   // source column of state column s, -1 = constant 1
+  int8_t op[kMaxCols];    // OP_SUM / OP_MIN / OP_MAX
+};
+
+__device__ __forceinline__ int64_t op_identity(int op) {
+  return op == OP_SUM ? 0 : (op == OP_MIN ? INT64_MAX : INT64_MIN);
+}
+
+__device__ __forceinline__ int64_t op_combine(int op, int64_t a, int64_t b) {
+  if (op == OP_SUM) return (int64_t)((unsigned long long)a + (unsigned long long)b);
+  if (op == OP_MIN) return b < a ? b : a;
+  return b > a ? b : a;
+}
+
+// ---------------------------------------------------------------------------
+// Partitioning digit.  fine(k) = clamp((k - base) >> fshift, 0, 2^fbits - 1)
+// is monotone in k, so buckets of equal fine digit are key ranges in key
+// order; the coarse digit is fine >> ebits.  Keys below base go to bucket 0,
+// keys above the sampled range to the last bucket.
+// ---------------------------------------------------------------------------
+struct Digit {
+  unsigned long long base;
+  int fshift;
+  int fbits;
+  int ebits;
+};
+
+__device__ __forceinline__ uint32_t fine_digit(const Digit& d, uint64_t k) {
+  if (d.fbits == 0 || k < d.base) return 0;
+  uint64_t x = d.fshift >= 64 ? 0 : ((k - d.base) >> d.fshift);
+  uint64_t lim = (1ull << d.fbits) - 1;
+  return (uint32_t)(x > lim ? lim : x);
+}
+
+__device__ __forceinline__ uint32_t coarse_digit(const Digit& d, uint64_t k) {
+  return fine_digit(d, k) >> d.ebits;
+}
+
+// ---------------------------------------------------------------------------
+// Decoupled look-back across chunks processed in ticket order (the chained
+// scan of Merrill and Garland, "Single-pass parallel prefix scan with
+// decoupled look-back", 2016): each chunk publishes its row count as soon as
+// it is known, then sums its predecessors' counts until it meets a published
+// inclusive prefix.  Every wait is bounded; on timeout the chunk raises the
+// error word and returns, and every other waiter sees the word and stops.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPre = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+
+struct LookBack {
+  unsigned long long* status;   // one word per chunk, zeroed before the launch
+  unsigned int* ticket;         // zeroed before the launch
+  const long long* base_in;     // exclusive prefix of chunk 0 (nullptr = 0)
+  long long* total_out;         // inclusive prefix of the last chunk (nullptr = none)
+  int* err;                     // device error word
+  long long spin_limit;
+  int n_chunks;
+  int stall;                    // test hook: chunk 0 never publishes
+};
+
+__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
+  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
+  a.store(v, cuda::memory_order_release);
+}
+
+__device__ __forceinline__ unsigned long long lb_load(unsigned long long* p) {
+  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
+  return a.load(cuda::memory_order_acquire);
+}
+
+__device__ __forceinline__ int err_load(int* p) {
+  cuda::atomic_ref<int, cuda::thread_scope_device> a(*p);
+  return a.load(cuda::memory_order_relaxed);
+}
+
+__device__ __forceinline__ void err_raise(int* p, int code) {
+  atomicCAS(p, 0, code);
+}
+
+// Called by one full warp.  Publishes `count` for chunk `id` and returns the
+// exclusive prefix, or -1 after raising ERR_TIMEOUT (or seeing another error).
+__device__ long long lookback_warp(const LookBack& lb, int id, long long count) {
+  const int lane = threadIdx.x & 31;
+  long long excl = 0;
+  if (id == 0) {
+    excl = lb.base_in ? *lb.base_in : 0;
+    if (lane == 0 && !lb.stall) lb_store(&lb.status[0], kFlagPre | (unsigned long long)(excl + count));
+    return excl;
+  }
+  if (lane == 0) lb_store(&lb.status[id], kFlagAgg | (unsigned long long)count);
+  int j = id - 1;  // highest predecessor not yet folded into excl
+  long long spins = 0;
+  while (true) {
+    int p = j - lane;
+    unsigned long long s = p >= 0 ? lb_load(&lb.status[p]) : kFlagPre;
+    bool ready = (s >> 62) != 0;
+    unsigned all_ready = __ballot_sync(0xffffffffu, ready);
+    // lanes 0..(first not-ready - 1) are usable only if contiguous from lane 0
+    unsigned not_ready = ~all_ready;
+    int usable = not_ready ? __ffs(not_ready) - 1 : 32;  // lanes [0, usable) ready
+    unsigned pre = __ballot_sync(0xffffffffu, ready && ((s >> 62) == 2) && lane < usable);
+    if (pre) {
+      int stop = __ffs(pre) - 1;  // nearest inclusive prefix
+      long long v = (lane <= stop) ? (long long)(s & kValMask) : 0;
+      if (p < 0) v = 0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      excl += __shfl_sync(0xffffffffu, v, 0);
+      break;
+    }
+    if (usable > 0) {
+      long long v = (lane < usable && p >= 0) ? (long long)(s & kValMask) : 0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      excl += __shfl_sync(0xffffffffu, v, 0);
+      j -= usable;
+      if (j < 0) {  // walked past chunk 0 without a prefix: chunk 0 always publishes one
+        excl += lb.base_in ? *lb.base_in : 0;
+        break;
+      }
+      continue;
+    }
+    // warp-uniform exit: the error word is read by lane 0 only
+    int e = __shfl_sync(0xffffffffu, lane == 0 ? err_load(lb.err) : 0, 0);
+    if (++spins > lb.spin_limit || e) {
+      if (lane == 0) err_raise(lb.err, ERR_TIMEOUT);
+      return -1;
+    }
+    __nanosleep(64);
+  }
+  if (lane == 0) lb_store(&lb.status[id], kFlagPre | (unsigned long long)(excl + count));
+  return excl;
+}
+
+}  // namespace sg

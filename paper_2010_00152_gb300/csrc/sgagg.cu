@@ -1,0 +1,1175 @@
+// sgagg.cu -- host side of the grouping path: C ABI, planner, run store.
+//
+// Pipeline of one sgagg_aggregate call (Sec. 3, Sec. 4, Sec. 6.1):
+//   probe      sample keys once: key range for the partitioning digit and an
+//              estimate of the duplicate rate (decides tile pre-aggregation);
+//   per batch  (read-sort-write cycle of M rows) run generation with early
+//              aggregation: optional tile pre-fold, partition by key range,
+//              sort+fold every chunk -> one sorted run of distinct keys, with
+//              per-fine-bucket offsets (the run's sparse index);
+//   merge      one wide merge over all runs: merge tiles are key ranges
+//              (groups of fine buckets) whose rows from every run fit one
+//              CTA; each tile folds equal keys across runs and writes the
+//              final rows in key order.
+// With a single batch the run is written straight to the output (no spill,
+// the in-memory case of Sec. 5.2.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sgagg.h"
+#include "sg_part.cuh"
+
+using namespace sg;
+
+namespace {
+
+constexpr long long kChunkTarget = kTileCap / 2;   // planner: rows per chunk start
+constexpr long long kBigBucket = kTileCap / 2;     // planner: buckets solved apart
+constexpr long long kBucketRows = 2048;            // average rows per coarse bucket
+constexpr int kMaxDepth = 70;
+constexpr long long kMaxBatch = 1ll << 30;
+constexpr int kSample = 16384;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  size_t used = 0;   // bytes requested by the current call
+  int gen = -1;      // call that last requested this buffer
+  bool arena = false;  // run storage: counted as run bytes, not scratch
+};
+
+struct Run {
+  long long start;   // absolute row in its arena (host copy, filled after sync)
+  long long rows;
+  int host;          // 1: pinned host arena
+};
+
+}  // namespace
+
+struct sgagg_ctx {
+  long long M = 1;
+  int prefold_opt = -1;
+  long long arena_cap = -1;
+  int radix_bits = 0;
+  long long spin_limit = 1ll << 26;
+  int fanin_cap = 0;
+  int fault_alloc = 0;
+  int alloc_count = 0;
+  int timing = 0;
+  int test_stall = 0;
+  std::string err;
+  // per-launch event pairs (SGAGG_OPT_TIMING)
+  struct KT { cudaEvent_t a = nullptr, b = nullptr; int cls = 0; };
+  std::vector<KT> timers;
+  int ntimers = 0;
+  bool timers_read = true;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int device = -1;
+
+  // workspace (grown on demand, freed by destroy)
+  // per recursion depth (fixed arrays: pointers stay valid for accounting)
+  DevBuf scatter[kMaxDepth + 1];  // rows of 1 + ncols words
+  DevBuf thist[kMaxDepth + 1], btot[kMaxDepth + 1], bstart[kMaxDepth + 1];
+  DevBuf chunks[kMaxDepth + 1], biglist[kMaxDepth + 1];
+  DevBuf copykeys[kMaxDepth + 1];  // solved big buckets (SoA)
+  std::vector<DevBuf> copycols[kMaxDepth + 1];
+  DevBuf pf[2];                  // pre-fold ping-pong: keys
+  std::vector<DevBuf> pfcols[2];
+  DevBuf status;                 // look-back status words + ticket
+  DevBuf small;                  // error word, counters, plan info, min/max
+  DevBuf sample;
+  DevBuf arena_keys;
+  std::vector<DevBuf> arena_cols;
+  DevBuf offs;                   // runs x (nf + 1)
+  DevBuf runptrs;
+  DevBuf fsizes;
+  DevBuf gather_keys;
+  std::vector<DevBuf> gather_cols;
+  DevBuf gather_ptrs;
+  DevBuf runstarts;              // batches + 1 device scalars
+  // host arena (pinned, mapped)
+  void* harena_keys = nullptr;
+  std::vector<void*> harena_cols;
+  size_t harena_rows = 0;
+  // host-side input staging for sgagg_aggregate_host
+  DevBuf in_keys[kMaxKeyCols];
+  std::vector<DevBuf> in_pay;
+  DevBuf out_keys[kMaxKeyCols];
+  std::vector<DevBuf> out_cols;
+
+  // pinned host scratch for small read-backs
+  void* hsmall = nullptr;
+
+  // buffers requested by the current call (scratch accounting)
+  int gen = 0;
+  std::vector<DevBuf*> touched;
+  bool top_prefold = false;
+  int key_bytes = 0;
+  int spec_aggs = 0;
+
+  // last call
+  bool have_call = false;
+  long long last_rows = 0;
+  sgagg_stats_t st{};
+  long long scratch_bytes = 0;
+  int pending_err = 0;
+};
+
+namespace {
+
+// small device block layout
+struct Small {
+  int err;
+  int pad;
+  unsigned long long mm[2];
+  PlanInfo info;
+  long long total;              // total_out of the final sort+fold
+  long long pftot;              // total_out of a pre-fold pass
+  long long dtot[kMaxDepth + 2];  // base/total of the sub-solves under depth d
+};
+
+struct HostSmall {
+  PlanInfo info;
+  int err;
+  int pad;
+  unsigned long long mm[2];
+  long long v[8];
+  unsigned long long sample[kSample];
+  Chunk ch[4];
+};
+
+sgagg_status fail(sgagg_t h, sgagg_status s, const char* fmt, const char* a = "") {
+  char buf[512];
+  snprintf(buf, sizeof buf, fmt, a);
+  if (h) h->err = buf;
+  return s;
+}
+
+#define CU(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? SGAGG_ENOMEM : SGAGG_ECUDA, \
+                  "%s", cudaGetErrorString(e_));                              \
+    }                                                                         \
+  } while (0)
+
+#define TRY(x)                          \
+  do {                                  \
+    sgagg_status s_ = (x);              \
+    if (s_ != SGAGG_OK) return s_;      \
+  } while (0)
+
+// Kernel-class bookkeeping: launches, compulsory bytes, optional event time.
+void kbegin(sgagg_t h, int cls) {
+  ++h->st.class_launches[cls];
+  ++h->st.kernel_launches;
+  if (!h->timing) return;
+  if (h->ntimers == (int)h->timers.size()) {
+    sgagg_ctx::KT t;
+    cudaEventCreate(&t.a);
+    cudaEventCreate(&t.b);
+    h->timers.push_back(t);
+  }
+  auto& t = h->timers[h->ntimers];
+  t.cls = cls;
+  cudaEventRecord(t.a, h->stream);
+}
+
+void kend(sgagg_t h) {
+  if (!h->timing) return;
+  cudaEventRecord(h->timers[h->ntimers].b, h->stream);
+  ++h->ntimers;
+  h->timers_read = false;
+}
+
+void kbytes(sgagg_t h, int cls, long long bytes) { h->st.class_bytes[cls] += bytes; }
+
+long long src_row_bytes(const RowSrc& s) {
+  if (s.kind == SRC_RAW) {
+    long long kb = 0;
+    for (int c = 0; c < s.key.n_cols; ++c) kb += s.key.bytes[c];
+    return kb + 8ll * s.ncols;
+  }
+  return 8ll * (1 + s.ncols);
+}
+
+sgagg_status grow(sgagg_t h, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.gen != h->gen) {
+    b.gen = h->gen;
+    b.used = 0;
+    h->touched.push_back(&b);
+  }
+  b.used = std::max(b.used, bytes);
+  if (b.cap >= bytes) return SGAGG_OK;
+  ++h->alloc_count;
+  if (h->fault_alloc > 0 && h->alloc_count == h->fault_alloc)
+    return fail(h, SGAGG_ENOMEM, "injected allocation failure");
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(h, SGAGG_ENOMEM, "device allocation of %s bytes failed",
+                std::to_string(want).c_str());
+  }
+  b.cap = want;
+  return SGAGG_OK;
+}
+
+template <class T>
+T* P(DevBuf& b) { return reinterpret_cast<T*>(b.p); }
+
+void free_buf(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+Small* dsmall(sgagg_t h) { return reinterpret_cast<Small*>(h->small.p); }
+HostSmall* hsmall(sgagg_t h) { return reinterpret_cast<HostSmall*>(h->hsmall); }
+
+int ilog2_ceil(long long x) {
+  int b = 0;
+  while ((1ll << b) < x) ++b;
+  return b;
+}
+
+int bitlen(unsigned long long x) { return x ? 64 - __builtin_clzll(x) : 0; }
+
+// Estimated distinct values D of a domain from `dist` distinct among `s`
+// uniform draws (inverse of D (1 - exp(-s/D))), by bisection.
+double estimate_domain(double s, double dist) {
+  if (dist >= s) return 1e18;
+  double lo = dist, hi = 1e18;
+  for (int it = 0; it < 200; ++it) {
+    double mid = std::sqrt(lo * hi);
+    double e = mid * (1.0 - std::exp(-s / mid));
+    if (e < dist) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+bool want_prefold(sgagg_t h, long long sample_n, long long distinct) {
+  if (h->prefold_opt >= 0) return h->prefold_opt == 1;
+  if (sample_n < 64) return false;
+  double D = estimate_domain((double)sample_n, (double)distinct);
+  double per_tile = D * (1.0 - std::exp(-(double)kTileCap / D));
+  return per_tile * 2.0 <= (double)kTileCap;
+}
+
+template <int MODE>
+void set_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_sortfold<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSortSmemBytes);
+    done = true;
+  }
+}
+
+constexpr int kMaxCoarseBits = 15;  // per-tile histogram / cursors: 2^15 x 4 B of shared memory
+
+void set_part_attrs() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
+    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
+    done = true;
+  }
+}
+
+// Everything a sort+fold launch writes into.
+struct Sink {
+  OutSink o;
+  int n_state;
+};
+
+FoldDesc identity_fold(const FoldDesc& raw) {
+  FoldDesc f = raw;
+  for (int s = 0; s < raw.n_state; ++s) f.src[s] = (int8_t)s;
+  return f;
+}
+
+// Launch the sort+fold kernel over n_chunks chunks.
+template <int MODE>
+sgagg_status launch_sortfold(sgagg_t h, int cls, const Chunk* dchunks, int n_chunks, long long tile_n,
+                             const RowSrc& src, const RunSet& runs, const CopySrc& copy,
+                             const FoldDesc& fd, const OutSink& out, const long long* base_in,
+                             long long* total_out, int tile_f_hi = 0) {
+  if (n_chunks <= 0) {
+    // still publish the running total
+    if (total_out) {
+      if (base_in) CU(cudaMemcpyAsync(total_out, base_in, 8, cudaMemcpyDeviceToDevice, h->stream));
+      else CU(cudaMemsetAsync(total_out, 0, 8, h->stream));
+    }
+    return SGAGG_OK;
+  }
+  TRY(grow(h, h->status, (size_t)(n_chunks + 2) * 8));
+  CU(cudaMemsetAsync(h->status.p, 0, (size_t)(n_chunks + 2) * 8, h->stream));
+  LookBack lb;
+  lb.ticket = reinterpret_cast<unsigned int*>(P<unsigned long long>(h->status));
+  lb.status = P<unsigned long long>(h->status) + 2;
+  lb.base_in = reinterpret_cast<const long long*>(base_in);
+  lb.total_out = reinterpret_cast<long long*>(total_out);
+  lb.err = &dsmall(h)->err;
+  lb.spin_limit = h->spin_limit;
+  lb.n_chunks = n_chunks;
+  lb.stall = h->test_stall;
+  h->test_stall = 0;
+  set_smem_attr<MODE>();
+  kbegin(h, cls);
+  k_sortfold<MODE><<<n_chunks, kThreads, kSortSmemBytes, h->stream>>>(dchunks, src, runs, copy, fd, out,
+                                                                      lb, tile_n, tile_f_hi);
+  kend(h);
+  CU(cudaGetLastError());
+  return SGAGG_OK;
+}
+
+sgagg_status sync_read(sgagg_t h, void* dst, const void* src, size_t bytes) {
+  CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return SGAGG_OK;
+}
+
+sgagg_status check_device_err(sgagg_t h) {
+  HostSmall* hs = hsmall(h);
+  TRY(sync_read(h, &hs->err, &dsmall(h)->err, sizeof(int)));
+  if (hs->err == ERR_TIMEOUT) return fail(h, SGAGG_ETIMEOUT, "device-side wait exceeded the spin limit");
+  if (hs->err == ERR_CAPACITY) return fail(h, SGAGG_ECAPACITY, "out_capacity is smaller than the number of distinct keys");
+  if (hs->err) return fail(h, SGAGG_ECUDA, "internal device error");
+  return SGAGG_OK;
+}
+
+struct Solver {
+  sgagg_t h;
+  FoldDesc fd_src;     // how state columns derive from the source's columns
+  int n_state;
+};
+
+sgagg_status ensure_depth(sgagg_t h, int depth) {
+  if (depth >= kMaxDepth) return fail(h, SGAGG_ECUDA, "recursion too deep");
+  return SGAGG_OK;
+}
+
+sgagg_status grow_cols(sgagg_t h, std::vector<DevBuf>& v, int S, size_t bytes) {
+  if ((int)v.size() < kMaxCols) v.resize(kMaxCols);  // never reallocated afterwards
+  for (int s = 0; s < S; ++s) TRY(grow(h, v[s], bytes));
+  return SGAGG_OK;
+}
+
+sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& fd0, const OutSink& out,
+                   const long long* base_in, long long* total_out, const Digit* gdig, int depth);
+
+// Tile pre-aggregation passes while they shrink the rows at least by half.
+// On return *src / *n / *fd describe the (possibly) reduced rows.
+sgagg_status prefold(sgagg_t h, RowSrc* src, long long* n, FoldDesc* fd, int force_until_fit) {
+  const int S = fd->n_state;
+  int which = 0;
+  while (*n > kTileCap) {
+    DevBuf& kb = h->pf[which];
+    auto& cb = h->pfcols[which];
+    long long ntile = (*n + kTileCap - 1) / kTileCap;
+    TRY(grow(h, kb, (size_t)(*n) * 8));
+    TRY(grow_cols(h, cb, S, (size_t)(*n) * 8));
+    OutSink o{};
+    o.user = 0;
+    o.keys = P<unsigned long long>(kb);
+    for (int s = 0; s < S; ++s) o.cols[s] = P<long long>(cb[s]);
+    o.capacity = *n;
+    o.offs = nullptr;
+    RunSet rs{};
+    CopySrc cs{};
+    long long* tot = &dsmall(h)->pftot;
+    TRY(launch_sortfold<MODE_TILES>(h, SGAGG_K_PREFOLD, nullptr, (int)ntile, *n, *src, rs, cs, *fd, o,
+                                    nullptr, tot));
+    HostSmall* hs = hsmall(h);
+    TRY(sync_read(h, &hs->v[0], tot, 8));
+    TRY(check_device_err(h));
+    ++h->st.prefold_passes;
+    long long n2 = hs->v[0];
+    kbytes(h, SGAGG_K_PREFOLD, *n * src_row_bytes(*src) + n2 * 8ll * (1 + S));
+    RowSrc r{};
+    r.kind = SRC_SOA;
+    r.ncols = S;
+    r.offset = 0;
+    r.keys = o.keys;
+    for (int s = 0; s < S; ++s) r.cols[s] = o.cols[s];
+    bool shrank = n2 * 2 <= *n;
+    *src = r;
+    *fd = identity_fold(*fd);
+    *n = n2;
+    which ^= 1;
+    if (!shrank && !force_until_fit) break;
+  }
+  return SGAGG_OK;
+}
+
+// Sort and fold n resident rows of src into `out` at *base_in (device),
+// writing the end position to *total_out.  gdig: digit whose fine buckets the
+// run's offsets use (top level of run generation), else computed here.
+sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& fd0, const OutSink& out,
+                   const long long* base_in, long long* total_out, const Digit* gdig, int depth) {
+  TRY(ensure_depth(h, depth));
+  RowSrc src = src0;
+  FoldDesc fd = fd0;
+  HostSmall* hs = hsmall(h);
+  RunSet norun{};
+  CopySrc nocopy{};
+
+  // keys all equal / small: pre-fold decision from a sample (depth > 0 or
+  // when the top level asked for it through prefold_opt)
+  bool do_pf = false;
+  if (n > kTileCap) {
+    if (depth == 0) {
+      do_pf = h->top_prefold;
+    } else {
+      int cnt = (int)std::min<long long>(n, 4096);
+      TRY(grow(h, h->sample, (size_t)kSample * 8));
+      kbegin(h, SGAGG_K_PROBE);
+      k_sample<<<8, 256, 0, h->stream>>>(src, n, cnt, P<unsigned long long>(h->sample));
+      kend(h);
+      TRY(sync_read(h, hs->sample, h->sample.p, (size_t)cnt * 8));
+      std::sort(hs->sample, hs->sample + cnt);
+      long long dist = std::unique(hs->sample, hs->sample + cnt) - hs->sample;
+      do_pf = want_prefold(h, cnt, dist);
+    }
+  }
+  if (do_pf) TRY(prefold(h, &src, &n, &fd, 0));
+
+  Digit dig{};
+  int nb = 1;
+  if (gdig) {
+    dig = *gdig;
+  }
+  if (n > kTileCap && !gdig) {
+    // exact key range of these rows
+    Small* ds = dsmall(h);
+    unsigned long long init[2] = {~0ull, 0ull};
+    memcpy(hs->mm, init, sizeof init);
+    CU(cudaMemcpyAsync(ds->mm, hs->mm, 16, cudaMemcpyHostToDevice, h->stream));
+    kbegin(h, SGAGG_K_PROBE);
+    k_minmax<<<std::max(1, std::min(h->num_sms * 4, (int)((n + 1023) / 1024))), 256, 0, h->stream>>>(src, n, ds->mm);
+    kend(h);
+    kbytes(h, SGAGG_K_PROBE, n * 8);
+    TRY(sync_read(h, hs->mm, ds->mm, 16));
+    unsigned long long kmin = hs->mm[0], kmax = hs->mm[1];
+    if (kmin == kmax) {
+      // one key value: tile folds shrink it by kTileCap per pass
+      TRY(prefold(h, &src, &n, &fd, 1));
+    } else {
+      int L = bitlen(kmax - kmin);
+      int Db = std::min(kMaxCoarseBits, std::max(1, ilog2_ceil((n + kBucketRows - 1) / kBucketRows)));
+      Db = std::min(Db, L);
+      dig.base = kmin;
+      dig.fbits = Db;
+      dig.fshift = L - Db;
+      dig.ebits = 0;
+    }
+  }
+  const int W = 1 + src.ncols;
+
+  if (n <= kTileCap) {
+    // one chunk, straight from the source (one tile covering the fine range)
+    TRY(launch_sortfold<MODE_TILES>(h, SGAGG_K_RUNGEN, nullptr, 1, n, src, norun, nocopy, fd, out, base_in,
+                                    total_out, out.offs ? (1 << dig.fbits) : 0));
+    kbytes(h, SGAGG_K_RUNGEN, n * src_row_bytes(src));
+    return SGAGG_OK;
+  }
+
+  // ---- partition by the coarse digit ----
+  nb = 1 << (dig.fbits - dig.ebits);
+  int ntiles = (int)std::max(1ll, std::min<long long>((n + 8191) / 8192, (long long)h->num_sms * 2));
+  set_part_attrs();
+  TRY(grow(h, h->scatter[depth], (size_t)n * W * 8));
+  TRY(grow(h, h->thist[depth], (size_t)nb * ntiles * 4));
+  TRY(grow(h, h->btot[depth], (size_t)nb * 8));
+  TRY(grow(h, h->bstart[depth], (size_t)(nb + 1) * 8));
+  TRY(grow(h, h->chunks[depth], (size_t)nb * sizeof(Chunk)));
+  TRY(grow(h, h->biglist[depth], (size_t)nb * 4));
+  const long long srb = src_row_bytes(src);
+  kbegin(h, SGAGG_K_HIST);
+  k_hist<<<ntiles, kPartThreads, nb * 4, h->stream>>>(src, n, dig, nb, ntiles, P<unsigned int>(h->thist[depth]));
+  kend(h);
+  kbytes(h, SGAGG_K_HIST, n * (srb - 8ll * src.ncols) + (long long)nb * ntiles * 4);
+  kbegin(h, SGAGG_K_PLAN);
+  k_tilescan<<<(nb * 32 + 255) / 256, 256, 0, h->stream>>>(P<unsigned int>(h->thist[depth]), nb, ntiles,
+                                                         P<long long>(h->btot[depth]));
+  kend(h);
+  Small* ds = dsmall(h);
+  kbegin(h, SGAGG_K_PLAN);
+  k_plan<<<1, 1024, 0, h->stream>>>(P<long long>(h->btot[depth]), nb, kChunkTarget, kBigBucket, dig.ebits,
+                                    P<long long>(h->bstart[depth]), P<Chunk>(h->chunks[depth]),
+                                    P<int>(h->biglist[depth]), &ds->info);
+  kend(h);
+  kbytes(h, SGAGG_K_PLAN, (long long)nb * ntiles * 8 + (long long)nb * (8 + 8 + sizeof(Chunk)));
+  kbegin(h, SGAGG_K_SCATTER);
+  k_scatter<<<ntiles, kPartThreads, nb * 4, h->stream>>>(src, n, dig, nb, ntiles, P<unsigned int>(h->thist[depth]),
+                                                        P<long long>(h->bstart[depth]), P<long long>(h->scatter[depth]));
+  kend(h);
+  kbytes(h, SGAGG_K_SCATTER, n * (srb + 8ll * W) + (long long)nb * ntiles * 4);
+  CU(cudaGetLastError());
+  TRY(sync_read(h, &hs->info, &ds->info, sizeof(PlanInfo)));
+  PlanInfo info = hs->info;
+  if (info.max_chunk > kTileCap) return fail(h, SGAGG_ECUDA, "planner produced an oversized chunk");
+
+  RowSrc aos{};
+  aos.kind = SRC_AOS;
+  aos.ncols = src.ncols;
+  aos.offset = 0;
+  aos.aos = P<long long>(h->scatter[depth]);
+
+  CopySrc copy{};
+  if (info.n_big > 0) {
+    // solve every big bucket on its own, into this depth's copy buffer
+    std::vector<int> big(info.n_big);
+    TRY(sync_read(h, big.data(), h->biglist[depth].p, (size_t)info.n_big * 4));
+    std::vector<Chunk> bch(info.n_big);
+    long long tot = 0;
+    for (int i = 0; i < info.n_big; ++i) {
+      CU(cudaMemcpy(&bch[i], P<Chunk>(h->chunks[depth]) + big[i], sizeof(Chunk), cudaMemcpyDeviceToHost));
+      tot += bch[i].hi - bch[i].lo;
+    }
+    const int S = fd.n_state;
+    TRY(grow(h, h->copykeys[depth], (size_t)tot * 8));
+    TRY(grow_cols(h, h->copycols[depth], S, (size_t)tot * 8));
+    OutSink co{};
+    co.user = 0;
+    co.keys = P<unsigned long long>(h->copykeys[depth]);
+    for (int s = 0; s < S; ++s) co.cols[s] = P<long long>(h->copycols[depth][s]);
+    co.capacity = tot;
+    co.offs = nullptr;
+    long long at = 0;
+    for (int i = 0; i < info.n_big; ++i) {
+      RowSrc sub = aos;
+      sub.offset = bch[i].lo;
+      long long m = bch[i].hi - bch[i].lo;
+      long long* tdev = &ds->dtot[depth];
+      hs->v[0] = at;
+      CU(cudaMemcpyAsync(tdev, &hs->v[0], 8, cudaMemcpyHostToDevice, h->stream));
+      CU(cudaStreamSynchronize(h->stream));
+      // base and total share one word: chunk 0 reads it before the last chunk writes it
+      TRY(solve(h, sub, m, fd, co, tdev, tdev, nullptr, depth + 1));
+      ++h->st.split_segments;
+      TRY(sync_read(h, &hs->v[1], tdev, 8));
+      TRY(check_device_err(h));
+      long long end = hs->v[1];
+      bch[i].lo = at;
+      bch[i].hi = end;
+      at = end;
+      CU(cudaMemcpy(P<Chunk>(h->chunks[depth]) + big[i], &bch[i], sizeof(Chunk), cudaMemcpyHostToDevice));
+    }
+    copy.keys = co.keys;
+    for (int s = 0; s < S; ++s) copy.cols[s] = co.cols[s];
+  }
+  TRY(launch_sortfold<MODE_RANGE>(h, SGAGG_K_RUNGEN, P<Chunk>(h->chunks[depth]), info.n_chunks, 0, aos, norun,
+                                  copy, fd, out, base_in, total_out));
+  kbytes(h, SGAGG_K_RUNGEN, n * 8ll * W);
+  return SGAGG_OK;
+}
+
+void build_keycols(const sgagg_keys* keys, KeyCols* kc, KeyOut* ko, void* const* out_keys) {
+  kc->n_cols = keys->n_cols;
+  ko->n_cols = keys->n_cols;
+  int below = 0;
+  for (int c = keys->n_cols - 1; c >= 0; --c) {
+    kc->bytes[c] = keys->bytes[c];
+    kc->shift[c] = below;
+    kc->cols[c] = keys->cols[c];
+    ko->bytes[c] = keys->bytes[c];
+    ko->shift[c] = below;
+    ko->cols[c] = out_keys ? out_keys[c] : nullptr;
+    below += 8 * keys->bytes[c];
+  }
+}
+
+sgagg_status validate(sgagg_t h, const sgagg_keys* keys, const int64_t* const* payload, int32_t n_payload,
+                      int64_t n, const sgagg_spec* spec, void* const* out_keys, int64_t* const* out_aggs,
+                      int64_t out_capacity) {
+  if (!h) return SGAGG_EINVAL;
+  if (!keys || !spec) return fail(h, SGAGG_EINVAL, "null keys or spec");
+  if (n < 0) return fail(h, SGAGG_EINVAL, "n < 0");
+  if (out_capacity < 0) return fail(h, SGAGG_EINVAL, "out_capacity < 0");
+  if (keys->n_cols < 1 || keys->n_cols > kMaxKeyCols || !keys->bytes || !keys->cols)
+    return fail(h, SGAGG_EINVAL, "bad key columns");
+  int bits = 0;
+  for (int c = 0; c < keys->n_cols; ++c) {
+    int b = keys->bytes[c];
+    if (b != 1 && b != 2 && b != 4 && b != 8) return fail(h, SGAGG_EINVAL, "key column width must be 1, 2, 4 or 8 bytes");
+    bits += 8 * b;
+    if (n > 0 && !keys->cols[c]) return fail(h, SGAGG_EINVAL, "null key column");
+  }
+  if (bits > 64) return fail(h, SGAGG_EINVAL, "key columns wider than 64 bits");
+  if (spec->n_aggs < 0 || spec->n_aggs > kMaxCols || (spec->n_aggs > 0 && !spec->aggs))
+    return fail(h, SGAGG_EINVAL, "bad aggregate spec");
+  if (n_payload < 0 || n_payload > 1024 || (n_payload > 0 && !payload))
+    return fail(h, SGAGG_EINVAL, "bad payload columns");
+  for (int a = 0; a < spec->n_aggs; ++a) {
+    int op = spec->aggs[a].op;
+    if (op < SGAGG_COUNT || op > SGAGG_MAX) return fail(h, SGAGG_EINVAL, "bad aggregate op");
+    if (op != SGAGG_COUNT) {
+      int c = spec->aggs[a].col;
+      if (c < 0 || c >= n_payload) return fail(h, SGAGG_EINVAL, "aggregate column out of range");
+      if (n > 0 && !payload[c]) return fail(h, SGAGG_EINVAL, "null payload column");
+    }
+  }
+  if (out_capacity > 0 || n > 0) {
+    if (!out_keys) return fail(h, SGAGG_EINVAL, "null out_keys");
+    for (int c = 0; c < keys->n_cols; ++c)
+      if (!out_keys[c] && out_capacity > 0) return fail(h, SGAGG_EINVAL, "null output key column");
+    if (spec->n_aggs > 0 && !out_aggs) return fail(h, SGAGG_EINVAL, "null out_aggs");
+    for (int a = 0; a < spec->n_aggs; ++a)
+      if (!out_aggs[a] && out_capacity > 0) return fail(h, SGAGG_EINVAL, "null output aggregate column");
+  }
+  return SGAGG_OK;
+}
+
+sgagg_status ensure_ctx_device(sgagg_t h) {
+  int dev = -1;
+  CU(cudaGetDevice(&dev));
+  if (h->device != dev) {
+    h->device = dev;
+    CU(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  TRY(grow(h, h->small, sizeof(Small)));
+  if (!h->hsmall) CU(cudaHostAlloc(&h->hsmall, sizeof(HostSmall), cudaHostAllocDefault));
+  return SGAGG_OK;
+}
+
+sgagg_status alloc_host_arena(sgagg_t h, size_t rows, int S) {
+  if (h->harena_rows >= rows && (int)h->harena_cols.size() >= S) return SGAGG_OK;
+  if (h->harena_keys) cudaFreeHost(h->harena_keys);
+  for (void* p : h->harena_cols) cudaFreeHost(p);
+  h->harena_keys = nullptr;
+  h->harena_cols.clear();
+  h->harena_rows = 0;
+  ++h->alloc_count;
+  if (h->fault_alloc > 0 && h->alloc_count == h->fault_alloc)
+    return fail(h, SGAGG_ENOMEM, "injected allocation failure");
+  CU(cudaHostAlloc(&h->harena_keys, rows * 8 + 16, cudaHostAllocMapped));
+  h->harena_cols.resize(S, nullptr);
+  for (int s = 0; s < S; ++s) CU(cudaHostAlloc(&h->harena_cols[s], rows * 8 + 16, cudaHostAllocMapped));
+  h->harena_rows = rows;
+  return SGAGG_OK;
+}
+
+template <class T>
+T* host_dev_ptr(sgagg_t h, void* p) {
+  void* d = nullptr;
+  cudaHostGetDevicePointer(&d, p, 0);
+  return reinterpret_cast<T*>(d);
+}
+
+// The whole operation on device-resident inputs.
+sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* const* payload_cols,
+                              int32_t n_payload, int64_t n, const sgagg_spec* spec, void* const* out_keys,
+                              int64_t* const* out_aggs, int64_t out_capacity, cudaStream_t stream) {
+  h->stream = stream;
+  h->have_call = true;
+  h->st = sgagg_stats_t{};
+  h->scratch_bytes = 0;
+  h->last_rows = 0;
+  h->st.n_rows = n;
+  ++h->gen;
+  h->touched.clear();
+  h->ntimers = 0;
+  h->timers_read = true;
+  h->key_bytes = 0;
+  for (int c = 0; c < keys->n_cols; ++c) h->key_bytes += keys->bytes[c];
+  h->spec_aggs = spec->n_aggs;
+  TRY(ensure_ctx_device(h));
+  Small* ds = dsmall(h);
+  HostSmall* hs = hsmall(h);
+  CU(cudaMemsetAsync(ds, 0, sizeof(Small), stream));
+
+  // raw source: key columns + the payload columns the aggregates read
+  RowSrc raw{};
+  raw.kind = SRC_RAW;
+  KeyOut kout{};
+  build_keycols(keys, &raw.key, &kout, out_keys);
+  std::vector<int> colmap(std::max(1, (int)n_payload), -1);
+  int C = 0;
+  FoldDesc fd{};
+  fd.n_state = spec->n_aggs;
+  for (int a = 0; a < spec->n_aggs; ++a) {
+    int op = spec->aggs[a].op;
+    if (op == SGAGG_COUNT) {
+      fd.src[a] = -1;
+      fd.op[a] = OP_SUM;
+    } else {
+      int c = spec->aggs[a].col;
+      if (colmap[c] < 0) {
+        colmap[c] = C;
+        raw.cols[C] = reinterpret_cast<const long long*>(payload_cols[c]);
+        ++C;
+      }
+      fd.src[a] = (int8_t)colmap[c];
+      fd.op[a] = op == SGAGG_SUM ? OP_SUM : (op == SGAGG_MIN ? OP_MIN : OP_MAX);
+    }
+  }
+  raw.ncols = C;
+  const int S = spec->n_aggs;
+
+  OutSink user{};
+  user.user = 1;
+  user.kout = kout;
+  for (int a = 0; a < S; ++a) user.cols[a] = reinterpret_cast<long long*>(out_aggs[a]);
+  user.capacity = out_capacity;
+  user.offs = nullptr;
+
+  if (n == 0) {
+    h->last_rows = 0;
+    return SGAGG_OK;
+  }
+
+  const long long M = std::min<long long>(h->M, kMaxBatch);
+  const long long B = (n + M - 1) / M;
+  h->st.batches = B;
+
+  // ---- probe: sampled key range and duplicate rate ----
+  int scount = (int)std::min<long long>(n, kSample);
+  TRY(grow(h, h->sample, (size_t)kSample * 8));
+  kbegin(h, SGAGG_K_PROBE);
+  k_sample<<<16, 256, 0, stream>>>(raw, n, scount, P<unsigned long long>(h->sample));
+  kend(h);
+  TRY(sync_read(h, hs->sample, h->sample.p, (size_t)scount * 8));
+  std::sort(hs->sample, hs->sample + scount);
+  unsigned long long smin = hs->sample[0], smax = hs->sample[scount - 1];
+  long long sdist = std::unique(hs->sample, hs->sample + scount) - hs->sample;
+  h->top_prefold = n > kTileCap && want_prefold(h, scount, sdist);
+
+  // ---- global partitioning digit ----
+  const long long mb = std::min<long long>(M, n);
+  int Db = 0;
+  if (mb > kTileCap) Db = std::min(kMaxCoarseBits, std::max(1, ilog2_ceil((mb + kBucketRows - 1) / kBucketRows)));
+  if (h->radix_bits > 0 && mb > kTileCap) Db = std::min(kMaxCoarseBits, h->radix_bits);
+  int Fb = Db;
+  if (B > 1) Fb = std::max(Db, std::min(22, ilog2_ceil((n + kBucketRows - 1) / kBucketRows)));
+  int L = bitlen(smax - smin);
+  Digit gd{};
+  gd.base = smin;
+  gd.fbits = std::min(Fb, L);
+  gd.fshift = L - gd.fbits;
+  gd.ebits = std::max(0, gd.fbits - Db);
+
+  if (B == 1) {
+    long long* tot = &ds->total;
+    TRY(solve(h, raw, n, fd, user, nullptr, tot, &gd, 0));
+    TRY(sync_read(h, &hs->v[0], tot, 8));
+    TRY(check_device_err(h));
+    h->last_rows = hs->v[0];
+    h->st.out_rows = h->last_rows;
+    kbytes(h, SGAGG_K_RUNGEN, h->last_rows * (h->key_bytes + 8ll * S));
+    return SGAGG_OK;
+  }
+
+  // ---- run generation: one run per batch ----
+  const int nf = 1 << gd.fbits;
+  const long long stride = nf + 1;
+  const long long row_bytes = 8ll * (1 + S);
+  long long dev_rows_cap = n;
+  if (h->arena_cap >= 0) dev_rows_cap = std::min<long long>(n, h->arena_cap / row_bytes);
+  TRY(grow(h, h->arena_keys, (size_t)std::max(1ll, dev_rows_cap) * 8));
+  TRY(grow_cols(h, h->arena_cols, S, (size_t)std::max(1ll, dev_rows_cap) * 8));
+  h->arena_keys.arena = true;
+  for (auto& b : h->arena_cols) b.arena = true;
+  TRY(grow(h, h->offs, (size_t)B * stride * 8));
+  TRY(grow(h, h->runstarts, (size_t)(2 * (B + 1)) * 8));
+  long long* rs_dev = P<long long>(h->runstarts);          // device arena cursor per batch
+  long long* rs_host = rs_dev + (B + 1);                   // host arena cursor per batch
+  CU(cudaMemsetAsync(rs_dev, 0, (size_t)(2 * (B + 1)) * 8, stream));
+  bool any_host = false;
+  std::vector<int> run_host(B, 0);
+  {
+    long long ub = 0;  // upper bound of device rows so far
+    for (long long b = 0; b < B; ++b) {
+      long long m = std::min(M, n - b * M);
+      if (ub + m > dev_rows_cap) { run_host[b] = 1; any_host = true; }
+      else ub += m;
+    }
+  }
+  if (any_host) TRY(alloc_host_arena(h, (size_t)n, S));
+
+  long long dev_cursor_idx = 0, host_cursor_idx = 0;
+  // run b reads its base from the previous run of the same arena
+  std::vector<long long*> base_ptr(B), end_ptr(B);
+  {
+    long long* last_dev = rs_dev;      // rs_dev[0] = 0
+    long long* last_host = rs_host;    // rs_host[0] = 0
+    for (long long b = 0; b < B; ++b) {
+      if (run_host[b]) {
+        base_ptr[b] = last_host;
+        end_ptr[b] = rs_host + 1 + (++host_cursor_idx) - 1;
+        last_host = end_ptr[b];
+      } else {
+        base_ptr[b] = last_dev;
+        end_ptr[b] = rs_dev + 1 + (++dev_cursor_idx) - 1;
+        last_dev = end_ptr[b];
+      }
+    }
+  }
+  for (long long b = 0; b < B; ++b) {
+    long long m = std::min(M, n - b * M);
+    RowSrc bs = raw;
+    bs.key = raw.key;
+    // shift the raw source to the batch: offset applies to every column
+    bs.offset = b * M;
+    OutSink o{};
+    o.user = 0;
+    if (run_host[b]) {
+      o.keys = host_dev_ptr<unsigned long long>(h, h->harena_keys);
+      for (int s = 0; s < S; ++s) o.cols[s] = host_dev_ptr<long long>(h, h->harena_cols[s]);
+      o.capacity = (long long)h->harena_rows;
+    } else {
+      o.keys = P<unsigned long long>(h->arena_keys);
+      for (int s = 0; s < S; ++s) o.cols[s] = P<long long>(h->arena_cols[s]);
+      o.capacity = dev_rows_cap;
+    }
+    o.offs = P<long long>(h->offs) + b * stride;
+    o.dig = gd;
+    TRY(solve(h, bs, m, fd, o, base_ptr[b], end_ptr[b], &gd, 0));
+  }
+  TRY(check_device_err(h));
+
+  // run bookkeeping (the paper's spill volume)
+  std::vector<long long> rsd(2 * (B + 1));
+  TRY(sync_read(h, rsd.data(), rs_dev, rsd.size() * 8));
+  std::vector<Run> runs(B);
+  {
+    long long di = 0, hi = 0;
+    for (long long b = 0; b < B; ++b) {
+      if (run_host[b]) {
+        runs[b] = Run{rsd[(B + 1) + hi], rsd[(B + 1) + hi + 1] - rsd[(B + 1) + hi], 1};
+        ++hi;
+      } else {
+        runs[b] = Run{rsd[di], rsd[di + 1] - rsd[di], 0};
+        ++di;
+      }
+      h->st.run_rows += runs[b].rows;
+      kbytes(h, SGAGG_K_RUNGEN, runs[b].rows * row_bytes);
+      if (runs[b].host) h->st.run_bytes_host += runs[b].rows * row_bytes;
+      else h->st.run_bytes_device += runs[b].rows * row_bytes;
+    }
+  }
+  h->st.runs = B;
+
+  // ---- wide merge ----
+  int K = (int)B;
+  std::vector<long long> hptrs((size_t)K * (1 + S));
+  for (int r = 0; r < K; ++r) {
+    if (runs[r].host) {
+      hptrs[(size_t)r * (1 + S)] = (long long)host_dev_ptr<long long>(h, h->harena_keys);
+      for (int s = 0; s < S; ++s) hptrs[(size_t)r * (1 + S) + 1 + s] = (long long)host_dev_ptr<long long>(h, h->harena_cols[s]);
+    } else {
+      hptrs[(size_t)r * (1 + S)] = (long long)h->arena_keys.p;
+      for (int s = 0; s < S; ++s) hptrs[(size_t)r * (1 + S) + 1 + s] = (long long)h->arena_cols[s].p;
+    }
+  }
+  if (K > kMaxFanIn || (h->fanin_cap > 0 && K > h->fanin_cap))
+    return fail(h, SGAGG_EINVAL, "too many runs for one wide merge (raise memory_budget_rows)");
+  TRY(grow(h, h->runptrs, hptrs.size() * 8));
+  CU(cudaMemcpyAsync(h->runptrs.p, hptrs.data(), hptrs.size() * 8, cudaMemcpyHostToDevice, stream));
+  RunSet rset{};
+  rset.k = K;
+  rset.ncols = S;
+  rset.ptrs = reinterpret_cast<const long long* const*>(h->runptrs.p);
+  rset.offs = P<long long>(h->offs);
+  rset.stride = stride;
+  FoldDesc fid = identity_fold(fd);
+
+  TRY(grow(h, h->fsizes, (size_t)nf * 8));
+  kbegin(h, SGAGG_K_PLAN);
+  k_fine_sizes<<<std::max(1, std::min(4 * h->num_sms, (nf + 255) / 256)), 256, 0, stream>>>(
+      rset.offs, K, stride, nf, P<long long>(h->fsizes));
+  kend(h);
+  kbytes(h, SGAGG_K_PLAN, (long long)K * stride * 8 + nf * 8ll);
+  TRY(ensure_depth(h, 0));
+  TRY(grow(h, h->bstart[0], (size_t)(nf + 1) * 8));
+  TRY(grow(h, h->chunks[0], (size_t)nf * sizeof(Chunk)));
+  TRY(grow(h, h->biglist[0], (size_t)nf * 4));
+  kbegin(h, SGAGG_K_PLAN);
+  k_plan<<<1, 1024, 0, stream>>>(P<long long>(h->fsizes), nf, kChunkTarget, kBigBucket, 0,
+                                 P<long long>(h->bstart[0]), P<Chunk>(h->chunks[0]), P<int>(h->biglist[0]),
+                                 &ds->info);
+  kend(h);
+  CU(cudaGetLastError());
+  TRY(sync_read(h, &hs->info, &ds->info, sizeof(PlanInfo)));
+  PlanInfo info = hs->info;
+  h->st.merge_tiles = info.n_chunks;
+  CopySrc copy{};
+  if (info.n_big > 0) {
+    std::vector<int> big(info.n_big);
+    TRY(sync_read(h, big.data(), h->biglist[0].p, (size_t)info.n_big * 4));
+    std::vector<Chunk> bch(info.n_big);
+    long long tot = 0;
+    for (int i = 0; i < info.n_big; ++i) {
+      CU(cudaMemcpy(&bch[i], P<Chunk>(h->chunks[0]) + big[i], sizeof(Chunk), cudaMemcpyDeviceToHost));
+      tot += bch[i].hi - bch[i].lo;
+    }
+    TRY(grow(h, h->copykeys[0], (size_t)tot * 8));
+    TRY(grow_cols(h, h->copycols[0], S, (size_t)tot * 8));
+    OutSink co{};
+    co.user = 0;
+    co.keys = P<unsigned long long>(h->copykeys[0]);
+    for (int s = 0; s < S; ++s) co.cols[s] = P<long long>(h->copycols[0][s]);
+    co.capacity = tot;
+    long long at = 0;
+    for (int i = 0; i < info.n_big; ++i) {
+      // gather the tile's rows from every run into one SoA buffer
+      long long m = bch[i].hi - bch[i].lo;
+      std::vector<long long> lo(K), hi(K), pre(K + 1, 0);
+      for (int r = 0; r < K; ++r) {
+        CU(cudaMemcpy(&lo[r], P<long long>(h->offs) + (long long)r * stride + bch[i].f_lo, 8, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(&hi[r], P<long long>(h->offs) + (long long)r * stride + bch[i].f_hi, 8, cudaMemcpyDeviceToHost));
+        pre[r + 1] = pre[r] + (hi[r] - lo[r]);
+      }
+      TRY(grow(h, h->gather_keys, (size_t)m * 8));
+      TRY(grow_cols(h, h->gather_cols, S, (size_t)m * 8));
+      std::vector<long long*> gcols(std::max(1, S));
+      for (int s = 0; s < S; ++s) gcols[s] = P<long long>(h->gather_cols[s]);
+      TRY(grow(h, h->gather_ptrs, (size_t)(std::max(1, S) + K + 1) * 8));
+      long long* dpre = P<long long>(h->gather_ptrs);
+      long long** dcols = reinterpret_cast<long long**>(dpre + K + 1);
+      CU(cudaMemcpy(dpre, pre.data(), (size_t)(K + 1) * 8, cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(dcols, gcols.data(), (size_t)std::max(1, S) * 8, cudaMemcpyHostToDevice));
+      dim3 grid(std::max(1, std::min(64, (int)((m / K + 255) / 256))), K);
+      kbegin(h, SGAGG_K_OTHER);
+      k_gather_runs<<<grid, 256, 0, stream>>>(rset, bch[i].f_lo, bch[i].f_hi, dpre,
+                                              P<unsigned long long>(h->gather_keys), dcols);
+      kend(h);
+      kbytes(h, SGAGG_K_OTHER, m * 16ll * (1 + S));
+      RowSrc gs{};
+      gs.kind = SRC_SOA;
+      gs.ncols = S;
+      gs.keys = P<unsigned long long>(h->gather_keys);
+      for (int s = 0; s < S; ++s) gs.cols[s] = gcols[s];
+      long long* tdev = &ds->dtot[kMaxDepth + 1];
+      hs->v[0] = at;
+      CU(cudaMemcpyAsync(tdev, &hs->v[0], 8, cudaMemcpyHostToDevice, stream));
+      CU(cudaStreamSynchronize(stream));
+      TRY(solve(h, gs, m, fid, co, tdev, tdev, nullptr, 1));
+      ++h->st.split_segments;
+      TRY(sync_read(h, &hs->v[1], tdev, 8));
+      TRY(check_device_err(h));
+      long long end = hs->v[1];
+      bch[i].lo = at;
+      bch[i].hi = end;
+      at = end;
+      CU(cudaMemcpy(P<Chunk>(h->chunks[0]) + big[i], &bch[i], sizeof(Chunk), cudaMemcpyHostToDevice));
+    }
+    copy.keys = co.keys;
+    for (int s = 0; s < S; ++s) copy.cols[s] = co.cols[s];
+  }
+  RowSrc nosrc{};
+  nosrc.ncols = 0;
+  long long* tot = &ds->total;
+  TRY(launch_sortfold<MODE_RUNS>(h, SGAGG_K_MERGE, P<Chunk>(h->chunks[0]), info.n_chunks, 0, nosrc, rset, copy,
+                                 fid, user, nullptr, tot));
+  TRY(sync_read(h, &hs->v[0], tot, 8));
+  TRY(check_device_err(h));
+  h->last_rows = hs->v[0];
+  h->st.out_rows = h->last_rows;
+  kbytes(h, SGAGG_K_MERGE, h->st.run_rows * row_bytes + h->last_rows * (h->key_bytes + 8ll * S));
+  return SGAGG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+sgagg_status sgagg_create(int64_t memory_budget_rows, sgagg_t* out) {
+  if (!out || memory_budget_rows < 1) return SGAGG_EINVAL;
+  sgagg_t h = new (std::nothrow) sgagg_ctx();
+  if (!h) return SGAGG_ENOMEM;
+  h->M = memory_budget_rows;
+  *out = h;
+  return SGAGG_OK;
+}
+
+sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
+  if (!h) return SGAGG_EINVAL;
+  switch (key) {
+    case SGAGG_OPT_PREFOLD:
+      if (value < -1 || value > 1) return fail(h, SGAGG_EINVAL, "prefold must be -1, 0 or 1");
+      h->prefold_opt = (int)value;
+      return SGAGG_OK;
+    case SGAGG_OPT_ARENA_CAP: h->arena_cap = value; return SGAGG_OK;
+    case SGAGG_OPT_RADIX_BITS:
+      if (value < 0 || value > 16) return fail(h, SGAGG_EINVAL, "radix bits must be 0..16");
+      h->radix_bits = (int)value;
+      return SGAGG_OK;
+    case SGAGG_OPT_SPIN_LIMIT:
+      if (value < 1) return fail(h, SGAGG_EINVAL, "spin limit must be >= 1");
+      h->spin_limit = value;
+      return SGAGG_OK;
+    case SGAGG_OPT_FANIN_CAP:
+      if (value < 0) return fail(h, SGAGG_EINVAL, "fan-in cap must be >= 0");
+      h->fanin_cap = (int)value;
+      return SGAGG_OK;
+    case SGAGG_OPT_FAULT_ALLOC:
+      h->fault_alloc = (int)value;
+      h->alloc_count = 0;
+      return SGAGG_OK;
+    case SGAGG_OPT_TIMING: h->timing = (int)value; return SGAGG_OK;
+    case SGAGG_OPT_TEST_STALL: h->test_stall = value ? 1 : 0; return SGAGG_OK;
+    default: return fail(h, SGAGG_EINVAL, "unknown option");
+  }
+}
+
+sgagg_status sgagg_aggregate(sgagg_t h, const sgagg_keys* keys, const int64_t* const* payload_cols,
+                             int32_t n_payload, int64_t n, const sgagg_spec* spec, void* const* out_keys,
+                             int64_t* const* out_aggs, int64_t out_capacity, void* stream) {
+  sgagg_status s = validate(h, keys, payload_cols, n_payload, n, spec, out_keys, out_aggs, out_capacity);
+  if (s != SGAGG_OK) return s;
+  h->err.clear();
+  s = aggregate_device(h, keys, payload_cols, n_payload, n, spec, out_keys, out_aggs, out_capacity,
+                       reinterpret_cast<cudaStream_t>(stream));
+  h->pending_err = (int)s;
+  return s;
+}
+
+sgagg_status sgagg_aggregate_host(sgagg_t h, const sgagg_keys* keys, const int64_t* const* payload_cols,
+                                  int32_t n_payload, int64_t n, const sgagg_spec* spec, void* const* out_keys,
+                                  int64_t* const* out_aggs, int64_t out_capacity, int64_t* rows, void* stream) {
+  sgagg_status s = validate(h, keys, payload_cols, n_payload, n, spec, out_keys, out_aggs, out_capacity);
+  if (s != SGAGG_OK) return s;
+  if (!rows) return fail(h, SGAGG_EINVAL, "null rows");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  h->err.clear();
+  // device copies of the inputs
+  sgagg_keys dk = *keys;
+  const void* dkc[kMaxKeyCols];
+  std::vector<const int64_t*> dp(std::max(1, (int)n_payload), nullptr);
+  for (int c = 0; c < keys->n_cols; ++c) {
+    size_t bytes = (size_t)n * keys->bytes[c];
+    TRY(grow(h, h->in_keys[c], bytes));
+    if (bytes) CU(cudaMemcpyAsync(h->in_keys[c].p, keys->cols[c], bytes, cudaMemcpyHostToDevice, st));
+    dkc[c] = h->in_keys[c].p;
+  }
+  dk.cols = dkc;
+  if ((int)h->in_pay.size() < n_payload) h->in_pay.resize(n_payload);
+  std::vector<bool> used(std::max(1, (int)n_payload), false);
+  for (int a = 0; a < spec->n_aggs; ++a)
+    if (spec->aggs[a].op != SGAGG_COUNT) used[spec->aggs[a].col] = true;
+  for (int c = 0; c < n_payload; ++c) {
+    if (!used[c]) continue;
+    TRY(grow(h, h->in_pay[c], (size_t)n * 8));
+    if (n) CU(cudaMemcpyAsync(h->in_pay[c].p, payload_cols[c], (size_t)n * 8, cudaMemcpyHostToDevice, st));
+    dp[c] = P<int64_t>(h->in_pay[c]);
+  }
+  long long cap = std::min<long long>(out_capacity, n);
+  void* dok[kMaxKeyCols];
+  for (int c = 0; c < keys->n_cols; ++c) {
+    TRY(grow(h, h->out_keys[c], (size_t)std::max(1ll, cap) * keys->bytes[c]));
+    dok[c] = h->out_keys[c].p;
+  }
+  if ((int)h->out_cols.size() < spec->n_aggs) h->out_cols.resize(spec->n_aggs);
+  std::vector<int64_t*> doa(std::max(1, spec->n_aggs), nullptr);
+  for (int a = 0; a < spec->n_aggs; ++a) {
+    TRY(grow(h, h->out_cols[a], (size_t)std::max(1ll, cap) * 8));
+    doa[a] = P<int64_t>(h->out_cols[a]);
+  }
+  s = aggregate_device(h, &dk, dp.data(), n_payload, n, spec, dok, doa.data(), cap, st);
+  h->pending_err = (int)s;
+  if (s != SGAGG_OK) return s;
+  long long r = h->last_rows;
+  for (int c = 0; c < keys->n_cols; ++c)
+    if (r) CU(cudaMemcpyAsync(out_keys[c], dok[c], (size_t)r * keys->bytes[c], cudaMemcpyDeviceToHost, st));
+  for (int a = 0; a < spec->n_aggs; ++a)
+    if (r) CU(cudaMemcpyAsync(out_aggs[a], doa[a], (size_t)r * 8, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  *rows = r;
+  return SGAGG_OK;
+}
+
+sgagg_status sgagg_result_rows(sgagg_t h, int64_t* rows) {
+  if (!h || !rows) return SGAGG_EINVAL;
+  if (!h->have_call) return fail(h, SGAGG_ESTATE, "no aggregate call yet");
+  if (h->pending_err) return (sgagg_status)h->pending_err;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, SGAGG_ECUDA, "%s", cudaGetErrorString(e));
+  *rows = h->last_rows;
+  return SGAGG_OK;
+}
+
+static long long scratch_in_use(sgagg_t h) {
+  long long s = 0;
+  for (DevBuf* b : h->touched)
+    if (b->gen == h->gen && !b->arena) s += (long long)b->used;
+  return s;
+}
+
+int64_t sgagg_temp_bytes(sgagg_t h) {
+  if (!h) return -1;
+  return h->st.run_bytes_device + h->st.run_bytes_host + scratch_in_use(h);
+}
+
+sgagg_status sgagg_stats(sgagg_t h, sgagg_stats_t* out) {
+  if (!h || !out) return SGAGG_EINVAL;
+  if (h->have_call) cudaStreamSynchronize(h->stream);
+  if (!h->timers_read) {
+    for (int i = 0; i < h->ntimers; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->timers[i].a, h->timers[i].b) == cudaSuccess)
+        h->st.class_ms[h->timers[i].cls] += ms;
+    }
+    h->timers_read = true;
+  }
+  *out = h->st;
+  out->peak_scratch_bytes = scratch_in_use(h);
+  out->out_bytes = h->st.out_rows * (h->key_bytes + 8ll * h->spec_aggs);
+  return SGAGG_OK;
+}
+
+sgagg_status sgagg_aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t count, const sgagg_spec* spec,
+                                     void* stream) {
+  (void)inst; (void)count; (void)spec; (void)stream;
+  if (!h) return SGAGG_EINVAL;
+  return fail(h, SGAGG_EINVAL, "batched mode not built yet");
+}
+
+void sgagg_destroy(sgagg_t h) {
+  if (!h) return;
+  auto fv = [](std::vector<DevBuf>& v) { for (auto& b : v) free_buf(b); };
+  for (int d = 0; d <= kMaxDepth; ++d) {
+    free_buf(h->scatter[d]); free_buf(h->thist[d]); free_buf(h->btot[d]); free_buf(h->bstart[d]);
+    free_buf(h->chunks[d]); free_buf(h->biglist[d]); free_buf(h->copykeys[d]); fv(h->copycols[d]);
+  }
+  free_buf(h->pf[0]); free_buf(h->pf[1]); fv(h->pfcols[0]); fv(h->pfcols[1]);
+  free_buf(h->status); free_buf(h->small); free_buf(h->sample); free_buf(h->arena_keys); fv(h->arena_cols);
+  free_buf(h->offs); free_buf(h->runptrs); free_buf(h->fsizes); free_buf(h->gather_keys); fv(h->gather_cols);
+  free_buf(h->gather_ptrs); free_buf(h->runstarts);
+  for (auto& b : h->in_keys) free_buf(b);
+  fv(h->in_pay);
+  for (auto& b : h->out_keys) free_buf(b);
+  fv(h->out_cols);
+  if (h->harena_keys) cudaFreeHost(h->harena_keys);
+  for (void* p : h->harena_cols) cudaFreeHost(p);
+  if (h->hsmall) cudaFreeHost(h->hsmall);
+  for (auto& t : h->timers) {
+    if (t.a) cudaEventDestroy(t.a);
+    if (t.b) cudaEventDestroy(t.b);
+  }
+  delete h;
+}
+
+const char* sgagg_last_error(sgagg_t h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+"""Python binding of the sgagg C ABI (include/sgagg.h).
+
+Argument marshalling only: every step of the grouping path runs in the CUDA
+library ``libsgagg.so``.  Function names match the C ABI; ``Aggregator`` is a
+small convenience wrapper that takes torch tensors (used only for device
+memory and streams) and returns torch tensors.
+
+There is no CPU fallback: if the library is not built, or no CUDA device is
+present when a call needs one, the call raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsgagg.so")
+
+SGAGG_OK, SGAGG_EINVAL, SGAGG_ENOMEM, SGAGG_ECUDA, SGAGG_ETIMEOUT, SGAGG_ECAPACITY, SGAGG_ESTATE = range(7)
+STATUS_NAMES = {0: "SGAGG_OK", 1: "SGAGG_EINVAL", 2: "SGAGG_ENOMEM", 3: "SGAGG_ECUDA",
+                4: "SGAGG_ETIMEOUT", 5: "SGAGG_ECAPACITY", 6: "SGAGG_ESTATE"}
+SGAGG_COUNT, SGAGG_SUM, SGAGG_MIN, SGAGG_MAX = range(4)
+(SGAGG_OPT_PREFOLD, SGAGG_OPT_ARENA_CAP, SGAGG_OPT_RADIX_BITS, SGAGG_OPT_SPIN_LIMIT,
+ SGAGG_OPT_FANIN_CAP, SGAGG_OPT_FAULT_ALLOC, SGAGG_OPT_TIMING, SGAGG_OPT_TEST_STALL) = range(8)
+
+
+class sgagg_agg(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("col", ctypes.c_int32)]
+
+
+class sgagg_spec(ctypes.Structure):
+    _fields_ = [("n_aggs", ctypes.c_int32), ("aggs", ctypes.POINTER(sgagg_agg))]
+
+
+class sgagg_keys(ctypes.Structure):
+    _fields_ = [("n_cols", ctypes.c_int32), ("bytes", ctypes.POINTER(ctypes.c_int32)),
+                ("cols", ctypes.POINTER(ctypes.c_void_p))]
+
+
+KERNEL_CLASSES = ("probe", "hist", "plan", "scatter", "prefold", "rungen", "merge", "other")
+
+
+class sgagg_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_rows", "batches", "runs", "run_rows", "run_bytes_device", "run_bytes_host",
+        "peak_scratch_bytes", "out_rows", "out_bytes", "prefold_passes", "split_segments",
+        "merge_tiles", "kernel_launches")] + [
+        ("class_launches", ctypes.c_int64 * 8), ("class_bytes", ctypes.c_int64 * 8),
+        ("class_ms", ctypes.c_double * 8)]
+
+    def as_dict(self):
+        d = {n: int(getattr(self, n)) for n, t in self._fields_ if t is ctypes.c_int64}
+        d["kernels"] = {KERNEL_CLASSES[i]: dict(launches=int(self.class_launches[i]),
+                                                bytes=int(self.class_bytes[i]),
+                                                ms=float(self.class_ms[i])) for i in range(8)}
+        return d
+
+
+class sgagg_instance(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("key_bytes", ctypes.c_int32), ("n_payload", ctypes.c_int32),
+                ("payload", ctypes.c_void_p), ("n", ctypes.c_int64), ("out_keys", ctypes.c_void_p),
+                ("out_aggs", ctypes.c_void_p), ("out_capacity", ctypes.c_int64),
+                ("out_rows", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsgagg.so is not built; run __graft_entry__.build() "
+                               "(the grouping path has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.sgagg_create.argtypes = [i64, ctypes.POINTER(vp)]
+        L.sgagg_set_option.argtypes = [vp, i32, i64]
+        L.sgagg_aggregate.argtypes = [vp, ctypes.POINTER(sgagg_keys), vp, i32, i64,
+                                      ctypes.POINTER(sgagg_spec), vp, vp, i64, vp]
+        L.sgagg_aggregate_host.argtypes = [vp, ctypes.POINTER(sgagg_keys), vp, i32, i64,
+                                           ctypes.POINTER(sgagg_spec), vp, vp, i64,
+                                           ctypes.POINTER(i64), vp]
+        L.sgagg_result_rows.argtypes = [vp, ctypes.POINTER(i64)]
+        L.sgagg_temp_bytes.argtypes = [vp]
+        L.sgagg_temp_bytes.restype = i64
+        L.sgagg_stats.argtypes = [vp, ctypes.POINTER(sgagg_stats_t)]
+        L.sgagg_aggregate_batched.argtypes = [vp, ctypes.POINTER(sgagg_instance), i32,
+                                              ctypes.POINTER(sgagg_spec), vp]
+        L.sgagg_destroy.argtypes = [vp]
+        L.sgagg_destroy.restype = None
+        L.sgagg_last_error.argtypes = [vp]
+        L.sgagg_last_error.restype = ctypes.c_char_p
+        for f in ("sgagg_create", "sgagg_set_option", "sgagg_aggregate", "sgagg_aggregate_host",
+                  "sgagg_result_rows", "sgagg_stats", "sgagg_aggregate_batched"):
+            getattr(L, f).restype = i32
+        _lib = L
+    return _lib
+
+
+class SgaggError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+# ---- C ABI, same names --------------------------------------------------
+def sgagg_create(memory_budget_rows):
+    h = ctypes.c_void_p()
+    st = lib().sgagg_create(int(memory_budget_rows), ctypes.byref(h))
+    if st != SGAGG_OK:
+        raise SgaggError(st, "sgagg_create(%d)" % memory_budget_rows)
+    return h
+
+
+def sgagg_last_error(h):
+    m = lib().sgagg_last_error(h)
+    return m.decode() if m else ""
+
+
+def _check(h, st):
+    if st != SGAGG_OK:
+        raise SgaggError(st, sgagg_last_error(h))
+
+
+def sgagg_set_option(h, key, value):
+    _check(h, lib().sgagg_set_option(h, int(key), int(value)))
+
+
+def sgagg_destroy(h):
+    lib().sgagg_destroy(h)
+
+
+def sgagg_temp_bytes(h):
+    return int(lib().sgagg_temp_bytes(h))
+
+
+def sgagg_result_rows(h):
+    r = ctypes.c_int64()
+    _check(h, lib().sgagg_result_rows(h, ctypes.byref(r)))
+    return int(r.value)
+
+
+def sgagg_stats(h):
+    s = sgagg_stats_t()
+    _check(h, lib().sgagg_stats(h, ctypes.byref(s)))
+    return s.as_dict()
+
+
+class _Args:
+    """Keeps ctypes argument structures alive for one call."""
+
+    def __init__(self, key_ptrs, key_bytes, payload_ptrs, aggs, out_key_ptrs, out_agg_ptrs):
+        nk = len(key_ptrs)
+        self.kb = (ctypes.c_int32 * nk)(*key_bytes)
+        self.kc = (ctypes.c_void_p * nk)(*key_ptrs)
+        self.keys = sgagg_keys(nk, self.kb, self.kc)
+        self.pay = (ctypes.c_void_p * max(1, len(payload_ptrs)))(*payload_ptrs)
+        self.aggs = (sgagg_agg * max(1, len(aggs)))(*[sgagg_agg(int(o), int(c)) for o, c in aggs])
+        self.spec = sgagg_spec(len(aggs), self.aggs)
+        self.ok = (ctypes.c_void_p * nk)(*out_key_ptrs)
+        self.oa = (ctypes.c_void_p * max(1, len(out_agg_ptrs)))(*out_agg_ptrs)
+
+
+def sgagg_aggregate(h, key_ptrs, key_bytes, payload_ptrs, n, aggs, out_key_ptrs, out_agg_ptrs,
+                    out_capacity, stream=0):
+    """Raw call with integer device pointers."""
+    a = _Args(key_ptrs, key_bytes, payload_ptrs, aggs, out_key_ptrs, out_agg_ptrs)
+    st = lib().sgagg_aggregate(h, ctypes.byref(a.keys), a.pay, len(payload_ptrs), int(n),
+                               ctypes.byref(a.spec), a.ok, a.oa, int(out_capacity),
+                               ctypes.c_void_p(stream))
+    _check(h, st)
+
+
+def sgagg_aggregate_host(h, key_ptrs, key_bytes, payload_ptrs, n, aggs, out_key_ptrs, out_agg_ptrs,
+                         out_capacity, stream=0):
+    """Raw call with integer HOST pointers; returns the number of rows."""
+    a = _Args(key_ptrs, key_bytes, payload_ptrs, aggs, out_key_ptrs, out_agg_ptrs)
+    rows = ctypes.c_int64()
+    st = lib().sgagg_aggregate_host(h, ctypes.byref(a.keys), a.pay, len(payload_ptrs), int(n),
+                                    ctypes.byref(a.spec), a.ok, a.oa, int(out_capacity),
+                                    ctypes.byref(rows), ctypes.c_void_p(stream))
+    _check(h, st)
+    return int(rows.value)
+
+
+def sgagg_aggregate_batched(h, instances, aggs, stream=0):
+    """instances: list of sgagg_instance (device pointers inside)."""
+    arr = (sgagg_instance * max(1, len(instances)))(*instances)
+    aa = (sgagg_agg * max(1, len(aggs)))(*[sgagg_agg(int(o), int(c)) for o, c in aggs])
+    spec = sgagg_spec(len(aggs), aa)
+    _check(h, lib().sgagg_aggregate_batched(h, arr, len(instances), ctypes.byref(spec),
+                                            ctypes.c_void_p(stream)))
+
+
+# ---- convenience wrapper over torch tensors ------------------------------
+class Aggregator:
+    """One handle.  aggregate() groups device tensors and returns tensors."""
+
+    def __init__(self, memory_budget_rows, **options):
+        self.h = sgagg_create(memory_budget_rows)
+        names = {"prefold": SGAGG_OPT_PREFOLD, "arena_cap": SGAGG_OPT_ARENA_CAP,
+                 "radix_bits": SGAGG_OPT_RADIX_BITS, "spin_limit": SGAGG_OPT_SPIN_LIMIT,
+                 "fanin_cap": SGAGG_OPT_FANIN_CAP, "fault_alloc": SGAGG_OPT_FAULT_ALLOC,
+                 "timing": SGAGG_OPT_TIMING, "test_stall": SGAGG_OPT_TEST_STALL}
+        for k, v in options.items():
+            sgagg_set_option(self.h, names[k], v)
+
+    def close(self):
+        if self.h is not None:
+            sgagg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, key, value):
+        sgagg_set_option(self.h, key, value)
+
+    def aggregate(self, key_cols, payload, aggs, capacity=None, out=None, stream=None, sync=True):
+        """key_cols: list of unsigned CUDA tensors (uint8/16/32/64); payload:
+        list of int64 CUDA tensors; aggs: list of (op, col).  Returns
+        (key column tensors, aggregate tensors) trimmed to the output rows."""
+        import torch
+        n = int(key_cols[0].numel()) if key_cols else 0
+        cap = n if capacity is None else int(capacity)
+        dev = key_cols[0].device
+        if out is None:
+            ok = [torch.empty(max(1, cap), dtype=k.dtype, device=dev) for k in key_cols]
+            oa = [torch.empty(max(1, cap), dtype=torch.int64, device=dev) for _ in aggs]
+        else:
+            ok, oa = out
+        s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+        sgagg_aggregate(self.h, [k.data_ptr() for k in key_cols], [k.element_size() for k in key_cols],
+                        [p.data_ptr() for p in payload], n, aggs, [k.data_ptr() for k in ok],
+                        [a.data_ptr() for a in oa], cap, s)
+        if not sync:
+            return ok, oa
+        rows = sgagg_result_rows(self.h)
+        return [k[:rows] for k in ok], [a[:rows] for a in oa]
+
+    def rows(self):
+        return sgagg_result_rows(self.h)
+
+    def stats(self):
+        return sgagg_stats(self.h)
+
+    def temp_bytes(self):
+        return sgagg_temp_bytes(self.h)
+
+    def aggregate_host(self, key_cols, payload, aggs, capacity=None, stream=0):
+        """Host numpy arrays in, host numpy arrays out (copies inside the call)."""
+        import numpy as np
+        n = len(key_cols[0])
+        cap = n if capacity is None else int(capacity)
+        key_cols = [np.ascontiguousarray(k) for k in key_cols]
+        payload = [np.ascontiguousarray(p, dtype=np.int64) for p in payload]
+        ok = [np.empty(max(1, cap), dtype=k.dtype) for k in key_cols]
+        oa = [np.empty(max(1, cap), dtype=np.int64) for _ in aggs]
+        rows = sgagg_aggregate_host(self.h, [k.ctypes.data for k in key_cols],
+                                    [k.dtype.itemsize for k in key_cols],
+                                    [p.ctypes.data for p in payload], n, aggs,
+                                    [k.ctypes.data for k in ok], [a.ctypes.data for a in oa], cap,
+                                    stream)
+        return [k[:rows] for k in ok], [a[:rows] for a in oa]

@@ -1,0 +1,227 @@
+"""GPU path vs the CPU oracle, element by element (bit-exact: int64 results).
+
+Every case calls the CUDA library through the C ABI (binding in
+paper_2010_00152_gb300/sgagg.py) on seeded inputs and compares keys and every
+aggregate with the oracle.  Sizes span many chunks and ragged tails; edge
+cases cover empty/tiny inputs, tile and budget boundaries, one key, all keys
+distinct, extreme keys and payloads, adversarial key layouts, composite keys,
+every key width, the pre-fold switch, the pinned-host run arena and the
+capacity error.
+"""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+from paper_2010_00152_gb300 import sgagg
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+TILE = 8192
+
+
+def to_np(t):
+    return t.cpu().numpy()
+
+
+def gpu_run(key_cols, payload, aggs, M, capacity=None, **opts):
+    agg = sgagg.Aggregator(M, **opts)
+    try:
+        kc = [k.to(DEV) for k in key_cols]
+        pc = [p.to(DEV) for p in payload]
+        ok, oa = agg.aggregate(kc, pc, aggs, capacity=capacity)
+        st = agg.stats()
+        tb = agg.temp_bytes()
+        return [to_np(k) for k in ok], [to_np(a) for a in oa], st, tb
+    finally:
+        agg.close()
+
+
+def oracle_run(key_cols, payload, aggs):
+    return oracle.aggregate([to_np(k) for k in key_cols], [to_np(p) for p in payload], aggs)
+
+
+def check(key_cols, payload, aggs, M, **opts):
+    gk, ga, st, tb = gpu_run(key_cols, payload, aggs, M, **opts)
+    rk, ra = oracle_run(key_cols, payload, aggs)
+    assert len(gk[0]) == len(rk[0]), (len(gk[0]), len(rk[0]))
+    for c in range(len(rk)):
+        np.testing.assert_array_equal(gk[c], rk[c])
+    for a in range(len(ra)):
+        np.testing.assert_array_equal(ga[a], ra[a], err_msg="aggregate %d" % a)
+    return st, tb
+
+
+AGG4 = [(0, 0), (1, 0), (2, 0), (3, 0)]
+
+
+def u64_case(kind, n, seed=3, npay=1):
+    keys = datagen.edge_keys(kind, n, seed) if kind not in ("c1",) else \
+        datagen.config1(n=n, seed=seed)["key_cols"][0]
+    pay = [datagen.uniform_int(seed, 20 + c, n, -10**12, 10**12) for c in range(npay)]
+    return [keys], pay
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, TILE - 1, TILE, TILE + 1, 3 * TILE + 17, 100_003])
+def test_sizes_single_batch(n):
+    kc, pay = u64_case("c1", n)
+    check(kc, pay, AGG4, M=1 << 30)
+
+
+@pytest.mark.parametrize("M", [TILE - 1, TILE, TILE + 1, 10_000, 65_536, 99_999])
+def test_budget_boundaries(M):
+    kc, pay = u64_case("c1", 200_003)
+    st, _ = check(kc, pay, AGG4, M=M)
+    B = -(-200_003 // M)
+    assert st["batches"] == B
+    assert st["runs"] == (B if B > 1 else 0)
+
+
+def test_budget_one_row():
+    kc, pay = u64_case("c1", 300)
+    st, _ = check(kc, pay, AGG4, M=1)
+    assert st["runs"] == 300 and st["run_rows"] == 300
+
+
+def test_budget_not_dividing_n():
+    kc, pay = u64_case("c1", 123_457)
+    check(kc, pay, AGG4, M=40_000)
+
+
+@pytest.mark.parametrize("kind", ["all_equal", "distinct", "sorted", "reverse", "small_int",
+                                  "extremes", "same_digit", "clustered"])
+@pytest.mark.parametrize("M", [1 << 30, 50_000])
+def test_adversarial_keys(kind, M):
+    kc, pay = u64_case(kind, 150_001, npay=2)
+    aggs = [(0, 0), (1, 0), (2, 1), (3, 1), (1, 1), (2, 0), (3, 0)]
+    check(kc, pay, aggs, M=M)
+
+
+def test_payload_extremes_wraparound():
+    n = 70_000
+    keys = datagen.keys_uniform_over(9, 1, n, 50).view(torch.uint64)
+    r = datagen.uniform_int(9, 2, n, 0, 3)
+    vals = torch.tensor([np.iinfo(np.int64).max, np.iinfo(np.int64).min, -1, 0], dtype=torch.int64)
+    pay = [vals[r]]
+    check([keys], pay, AGG4, M=1 << 30)
+    check([keys], pay, AGG4, M=9_000)
+
+
+def test_c1_full_size_and_run_rows():
+    """Config 1 at full size: 2^20 rows, 10,000 keys, 16 runs + wide merge.
+    The run bookkeeping equals the oracle's run generation exactly."""
+    c = datagen.config1()
+    st, tb = check(c["key_cols"], c["payload"], c["aggs"], M=c["M"])
+    rows, _, _ = oracle.run_generation(to_np(c["key_cols"][0]), [to_np(c["payload"][0])],
+                                       c["aggs"], c["M"])
+    assert st["runs"] == 16 and st["run_rows"] == sum(rows)
+    assert st["out_rows"] == 10_000
+    assert tb >= st["run_rows"] * 8 * (1 + len(c["aggs"]))
+
+
+def test_c2_report_shape_prefold():
+    c = datagen.config2(n=1 << 22, seed=2)
+    st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=c["M"])
+    assert st["out_rows"] == 4 and st["prefold_passes"] >= 1
+
+
+def test_c3_shape_reduced():
+    c = datagen.config3(n=1 << 22, seed=1, D=1 << 21, M=1 << 18)
+    st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=c["M"])
+    rows, _, _ = oracle.run_generation(to_np(c["key_cols"][0]), [to_np(c["payload"][0])],
+                                       c["aggs"], c["M"])
+    assert st["runs"] == 16 and st["run_rows"] == sum(rows)
+
+
+@pytest.mark.parametrize("widths", [[1], [2], [4], [8], [1, 1], [2, 4], [1, 2, 1], [4, 4], [1, 1, 1, 1, 1, 1, 1, 1]])
+def test_composite_keys(widths):
+    n = 120_000
+    dt = {1: torch.uint8, 2: torch.uint16, 4: torch.uint32, 8: torch.uint64}
+    cols = []
+    for i, w in enumerate(widths):
+        hi = min((1 << (8 * w)) - 1, 40 if len(widths) > 1 else (1 << 62))
+        v = datagen.uniform_int(11, 30 + i, n, 0, hi)
+        cols.append(v.to(dt[w]) if w < 8 else v.view(torch.uint64))
+    pay = [datagen.uniform_int(11, 50, n, -100, 100)]
+    check(cols, pay, AGG4, M=1 << 30)
+    check(cols, pay, AGG4, M=30_000)
+
+
+def test_c4_instance_shape():
+    inst = dict(rows=300_000, D=5000, seed=17)
+    c = datagen.config4_instance(inst)
+    check(c["key_cols"], c["payload"], c["aggs"], M=c["M"])
+
+
+def test_c5_request_shape():
+    req = dict(rows=500_000, D=700, seed=23)
+    c = datagen.config5_request(req, M=1 << 17)
+    check(c["key_cols"], c["payload"], c["aggs"], M=c["M"])
+
+
+@pytest.mark.parametrize("prefold", [0, 1])
+def test_prefold_switch_invariant(prefold):
+    c = datagen.config1(n=300_000, seed=8, D=20_000)
+    check(c["key_cols"], c["payload"], c["aggs"], M=100_000, prefold=prefold)
+
+
+@pytest.mark.parametrize("bits", [1, 4, 9, 15])
+def test_radix_bits_invariant(bits):
+    c = datagen.config1(n=300_000, seed=8, D=200_000)
+    check(c["key_cols"], c["payload"], c["aggs"], M=150_000, radix_bits=bits)
+
+
+def test_runs_spill_to_pinned_host():
+    c = datagen.config1(n=400_000, seed=4, D=150_000)
+    st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=50_000, arena_cap=3 * 50_000 * 40)
+    assert st["run_bytes_host"] > 0 and st["run_bytes_device"] > 0
+
+
+def test_permutation_invariance():
+    c = datagen.config1(n=200_000, seed=12, D=30_000)
+    perm = torch.randperm(200_000, generator=torch.Generator().manual_seed(5))
+    a = gpu_run(c["key_cols"], c["payload"], c["aggs"], 60_000)
+    pk = c["key_cols"][0].view(torch.int64)[perm].view(torch.uint64)
+    b = gpu_run([pk], [c["payload"][0][perm]], c["aggs"], 60_000)
+    for x, y in zip(a[0] + a[1], b[0] + b[1]):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_capacity_error():
+    c = datagen.config1(n=50_000, seed=2, D=1000)
+    with pytest.raises(sgagg.SgaggError) as e:
+        gpu_run(c["key_cols"], c["payload"], c["aggs"], 1 << 30, capacity=500)
+    assert e.value.status == sgagg.SGAGG_ECAPACITY
+    with pytest.raises(sgagg.SgaggError) as e:
+        gpu_run(c["key_cols"], c["payload"], c["aggs"], 10_000, capacity=500)
+    assert e.value.status == sgagg.SGAGG_ECAPACITY
+
+
+def test_host_buffers_entry_point():
+    c = datagen.config1(n=150_000, seed=6, D=7_000)
+    agg = sgagg.Aggregator(40_000)
+    try:
+        ok, oa = agg.aggregate_host([to_np(c["key_cols"][0])], [to_np(c["payload"][0])], c["aggs"])
+    finally:
+        agg.close()
+    rk, ra = oracle_run(c["key_cols"], c["payload"], c["aggs"])
+    np.testing.assert_array_equal(ok[0], rk[0])
+    for a in range(len(ra)):
+        np.testing.assert_array_equal(oa[a], ra[a])
+
+
+def test_handle_reuse_across_shapes():
+    agg = sgagg.Aggregator(30_000)
+    try:
+        for seed, n, D in ((1, 100_000, 500), (2, 7, 3), (3, 90_001, 80_000), (4, 0, 1)):
+            c = datagen.config1(n=n, seed=seed, D=D)
+            kc = [c["key_cols"][0].to(DEV)]
+            pc = [c["payload"][0].to(DEV)]
+            ok, oa = agg.aggregate(kc, pc, c["aggs"])
+            rk, ra = oracle_run(c["key_cols"], c["payload"], c["aggs"])
+            np.testing.assert_array_equal(to_np(ok[0]), rk[0])
+            for a in range(len(ra)):
+                np.testing.assert_array_equal(to_np(oa[a]), ra[a])
+    finally:
+        agg.close()
