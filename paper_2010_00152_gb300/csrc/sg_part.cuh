@@ -54,16 +54,34 @@ __device__ __forceinline__ void tile_range(long long n, int ntiles, int t, long 
   *hi = min(n, *lo + per);
 }
 
-// thist[d * ntiles + t] = rows of tile t with coarse digit d.
+// Digit of one partitioning level: bits [dshift, dshift + log2(nb)) of the
+// coarse digit.
+__device__ __forceinline__ unsigned level_digit(const Digit& dig, unsigned long long k, int dshift, int nb) {
+  return (coarse_digit(dig, k) >> dshift) & (unsigned)(nb - 1);
+}
+
+// thist[d * ntiles + t] = rows of tile t with level digit d.
 __global__ void __launch_bounds__(kPartThreads)
-k_hist(RowSrc src, long long n, Digit dig, int nb, int ntiles, unsigned int* thist) {
+k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsigned int* thist) {
   extern __shared__ unsigned int sh_hist[];
   for (int d = threadIdx.x; d < nb; d += blockDim.x) sh_hist[d] = 0;
   __syncthreads();
   long long lo, hi;
   tile_range(n, ntiles, blockIdx.x, &lo, &hi);
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
-    atomicAdd(&sh_hist[coarse_digit(dig, src_key(src, i))], 1u);
+  constexpr int U = 8;  // independent loads in flight per thread
+  for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += (long long)U * blockDim.x) {
+    unsigned long long k[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      long long i = i0 + (long long)u * blockDim.x;
+      if (i < hi) k[u] = src_key(src, i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      long long i = i0 + (long long)u * blockDim.x;
+      if (i < hi) atomicAdd(&sh_hist[level_digit(dig, k[u], dshift, nb)], 1u);
+    }
+  }
   __syncthreads();
   for (int d = threadIdx.x; d < nb; d += blockDim.x) thist[(long long)d * ntiles + blockIdx.x] = sh_hist[d];
 }
@@ -119,35 +137,63 @@ __device__ __forceinline__ bool plan_is_start(long long x, long long big, long l
   return st;
 }
 
+// Exclusive sum over the 1024 threads of k_plan (32 warps); lane 31 of warp 0
+// writes the sum to *total (a shared or local slot of that thread).
+__device__ __forceinline__ long long plan_scan(long long v, long long* total) {
+  __shared__ long long ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    long long t = ws[lane], u = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, u, o);
+      if (lane >= o) u += y;
+    }
+    ws[lane] = u - t;
+    if (lane == 31) *total = u;
+  }
+  __syncthreads();
+  long long r = ws[wid] + x - v;
+  __syncthreads();
+  return r;
+}
+
 __global__ void __launch_bounds__(1024)
 k_plan(const long long* __restrict__ w, int nb, long long target, long long big, int fine_shift,
        long long* bstart, Chunk* chunks, int* big_list, PlanInfo* info) {
   const int T = blockDim.x;
   const int per = (nb + T - 1) / T;
   const int d0 = min(nb, (int)threadIdx.x * per), d1 = min(nb, d0 + per);
-  __shared__ long long sa[1024], sb[1024], sc[1024], sd[1024];
+  __shared__ long long sa[1024];
   __shared__ int s_nc;
+  __shared__ long long s_tot[3];
   long long ta = 0, tb = 0, tc = 0;
   for (int d = d0; d < d1; ++d) {
     long long x = w[d];
     ta += x;
     if (x > big) tc += 1; else tb += x;
   }
-  sa[threadIdx.x] = ta; sb[threadIdx.x] = tb; sc[threadIdx.x] = tc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long A = 0, B = 0, C = 0;
-    for (int t = 0; t < T; ++t) {
-      long long a = sa[t], b = sb[t], c = sc[t];
-      sa[t] = A; sb[t] = B; sc[t] = C;
-      A += a; B += b; C += c;
-    }
-    info->total = A;
-    info->n_big = (int)C;
-    bstart[nb] = A;
+  long long dummy;
+  const long long A0 = plan_scan(ta, &dummy);
+  const long long B0 = plan_scan(tb, &dummy);
+  const long long C0 = plan_scan(tc, &dummy);
+  if (threadIdx.x == T - 1) {
+    s_tot[0] = A0 + ta;
+    s_tot[2] = C0 + tc;
   }
   __syncthreads();
-  const long long A0 = sa[threadIdx.x], B0 = sb[threadIdx.x], C0 = sc[threadIdx.x];
+  if (threadIdx.x == 0) {
+    info->total = s_tot[0];
+    info->n_big = (int)s_tot[2];
+    bstart[nb] = s_tot[0];
+  }
   // state just before d0 (the previous bucket)
   bool pb0 = true;
   long long pq0 = -1;
@@ -166,19 +212,16 @@ k_plan(const long long* __restrict__ w, int nb, long long target, long long big,
       if (x <= big) pB += x;
     }
   }
-  sd[threadIdx.x] = starts;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long S = 0;
-    for (int t = 0; t < T; ++t) { long long c = sd[t]; sd[t] = S; S += c; }
-    s_nc = (int)S;
-    info->n_chunks = (int)S;
+  const long long S0 = plan_scan(starts, &dummy);
+  if (threadIdx.x == T - 1) {
+    s_nc = (int)(S0 + starts);
+    info->n_chunks = (int)(S0 + starts);
   }
   __syncthreads();
   {
     bool pbig = pb0;
     long long pq = pq0, pB = B0, pA = A0, nbig = C0;
-    long long cidx = sd[threadIdx.x] - 1;
+    long long cidx = S0 - 1;
     for (int d = d0; d < d1; ++d) {
       long long x = w[d];
       bstart[d] = pA;
@@ -209,12 +252,13 @@ k_plan(const long long* __restrict__ w, int nb, long long target, long long big,
     chunks[c].f_hi = chunks[c].pad << fine_shift;
     chunks[c].pad = 0;
   }
-  sa[threadIdx.x] = mx;
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sa[threadIdx.x >> 5] = mx;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    long long m = 0;
-    for (int t = 0; t < T; ++t) m = max(m, sa[t]);
-    info->max_chunk = m;
+  if (threadIdx.x < 32) {
+    long long m = sa[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) info->max_chunk = m;
   }
 }
 
@@ -232,28 +276,56 @@ k_scatter(RowSrc src, long long n, Digit dig, int nb, int ntiles, const unsigned
   long long lo, hi;
   tile_range(n, ntiles, blockIdx.x, &lo, &hi);
   const int W = 1 + src.ncols;
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    unsigned long long k = src_key(src, i);
-    unsigned long long pos = atomicAdd(&cursor[coarse_digit(dig, k)], 1u);
-    long long* row = aos + (long long)pos * W;
-    if (W == 2) {
-      // one 16-byte store when the row is key + one column
-      longlong2 v;
-      v.x = (long long)k;
-      v.y = src_col(src, 0, i);
-      *reinterpret_cast<longlong2*>(row) = v;
-    } else {
-      row[0] = (long long)k;
-      for (int c = 0; c < src.ncols; ++c) row[1 + c] = src_col(src, c, i);
+  constexpr int U = 8;  // independent loads in flight per thread
+  if (W == 2) {
+    for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += (long long)U * blockDim.x) {
+      unsigned long long k[U];
+      long long v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        long long i = i0 + (long long)u * blockDim.x;
+        if (i < hi) { k[u] = src_key(src, i); v[u] = src_col(src, 0, i); }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        long long i = i0 + (long long)u * blockDim.x;
+        if (i < hi) {
+          unsigned pos = atomicAdd(&cursor[coarse_digit(dig, k[u])], 1u);
+          // one 16-byte store: key + the one carried column
+          longlong2 r;
+          r.x = (long long)k[u];
+          r.y = v[u];
+          *reinterpret_cast<longlong2*>(aos + (long long)pos * 2) = r;
+        }
+      }
+    }
+    return;
+  }
+  for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += (long long)U * blockDim.x) {
+    unsigned long long k[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      long long i = i0 + (long long)u * blockDim.x;
+      if (i < hi) k[u] = src_key(src, i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      long long i = i0 + (long long)u * blockDim.x;
+      if (i < hi) {
+        unsigned pos = atomicAdd(&cursor[coarse_digit(dig, k[u])], 1u);
+        long long* row = aos + (long long)pos * W;
+        row[0] = (long long)k[u];
+        for (int c = 0; c < src.ncols; ++c) row[1 + c] = src_col(src, c, i);
+      }
     }
   }
 }
 
 // Rows of all runs in each fine bucket: sizes[f] = sum_r offs[r][f+1] - offs[r][f].
-__global__ void k_fine_sizes(const long long* offs, int k, long long stride, int nf, long long* sizes) {
+__global__ void k_fine_sizes(const long long* const* offs, int k, int nf, long long* sizes) {
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
     long long s = 0;
-    for (int r = 0; r < k; ++r) s += offs[(long long)r * stride + f + 1] - offs[(long long)r * stride + f];
+    for (int r = 0; r < k; ++r) s += offs[r][f + 1] - offs[r][f];
     sizes[f] = s;
   }
 }
@@ -262,8 +334,8 @@ __global__ void k_fine_sizes(const long long* offs, int k, long long stride, int
 __global__ void k_gather_runs(RunSet runs, int f_lo, int f_hi, const long long* dst_pre,
                               unsigned long long* dkeys, long long* const* dcols) {
   const int r = blockIdx.y;
-  long long lo = runs.offs[(long long)r * runs.stride + f_lo];
-  long long hi = runs.offs[(long long)r * runs.stride + f_hi];
+  long long lo = runs.offs[r][f_lo];
+  long long hi = runs.offs[r][f_hi];
   long long pre = dst_pre[r];
   const long long* const* p = runs.ptrs + (long long)r * (1 + runs.ncols);
   for (long long i = lo + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hi;
@@ -285,6 +357,231 @@ __global__ void k_offsets_by_search(const unsigned long long* keys, long long n,
     }
     offs[f] = base + lo;
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Two-level partitioning.  Level 1 splits the batch into at most 1024 buckets;
+// level 2 splits every level-1 bucket by the remaining digit bits.  Both
+// levels scatter through a shared-memory stage: a sub-tile of kStage rows is
+// counting-sorted by digit first, so each bucket's rows leave as one
+// contiguous run and every store is coalesced (no partially written sectors
+// for the memory system to read back).
+// ---------------------------------------------------------------------------
+constexpr int kStage = 4096;
+constexpr int kStageCols = 4;        // carried columns the staged scatter handles
+constexpr int kTile2 = 8192;         // rows per level-2 tile
+
+// Exclusive prefix of w[0..nb) into out[0..nb] (single CTA of kPartThreads).
+__global__ void __launch_bounds__(kPartThreads) k_excl_scan(const long long* w, int nb, long long* out) {
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += kPartThreads) {
+    int d = b0 + threadIdx.x;
+    long long v = d < nb ? w[d] : 0;
+    int tot;
+    // values fit int (rows of one batch < 2^31)
+    int ex = block_excl_sum((int)v, &tot);
+    if (d < nb) out[d] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[nb] = carry;
+}
+
+struct Tile2 {
+  long long lo, hi;   // rows of the level-1 output
+  int bucket;         // level-1 bucket
+  int pad;
+};
+
+// Level-2 tiles: bucket b of the level-1 output is cut into ceil(size/kTile2)
+// tiles; tfirst[b] = index of its first tile, tfirst[nb1] = tile count.
+__global__ void __launch_bounds__(kPartThreads)
+k_tiles2(const long long* bstart1, int nb1, Tile2* tiles, int* tfirst) {
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nb1; b0 += kPartThreads) {
+    int b = b0 + threadIdx.x;
+    long long lo = 0, hi = 0;
+    int nt = 0;
+    if (b < nb1) {
+      lo = bstart1[b];
+      hi = bstart1[b + 1];
+      nt = (int)((hi - lo + kTile2 - 1) / kTile2);
+    }
+    int tot;
+    int ex = block_excl_sum(nt, &tot) + carry;
+    if (b < nb1) {
+      tfirst[b] = ex;
+      for (int j = 0; j < nt; ++j) {
+        Tile2 t;
+        t.lo = lo + (long long)j * kTile2;
+        t.hi = min(hi, t.lo + kTile2);
+        t.bucket = b;
+        t.pad = 0;
+        tiles[ex + j] = t;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tfirst[nb1] = carry;
+}
+
+// Level-2 histograms: thist2[t * nb2 + d] = rows of tile t with digit d.
+__global__ void __launch_bounds__(kPartThreads)
+k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, unsigned* thist2) {
+  extern __shared__ unsigned sh2[];
+  const int t = blockIdx.x;
+  if (t >= *ntiles) return;
+  for (int d = threadIdx.x; d < nb2; d += blockDim.x) sh2[d] = 0;
+  __syncthreads();
+  const Tile2 tl = tiles[t];
+  constexpr int U = 8;
+  for (long long i0 = tl.lo + threadIdx.x; i0 < tl.hi; i0 += (long long)U * blockDim.x) {
+    unsigned long long k[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      long long i = i0 + (long long)u * blockDim.x;
+      if (i < tl.hi) k[u] = src_key(src, i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      long long i = i0 + (long long)u * blockDim.x;
+      if (i < tl.hi) atomicAdd(&sh2[level_digit(dig, k[u], 0, nb2)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < nb2; d += blockDim.x) thist2[(long long)t * nb2 + d] = sh2[d];
+}
+
+// One CTA per level-1 bucket: turns the bucket's tile histograms into absolute
+// write positions (thist2, in place) and writes the final bucket totals
+// btot[b * nb2 + d] (fine-grained buckets in key order).
+__global__ void __launch_bounds__(kPartThreads)
+k_scan2(const long long* bstart1, int nb2, const int* tfirst, unsigned* thist2, long long* btot) {
+  const int b = blockIdx.x;
+  const int t0 = tfirst[b], t1 = tfirst[b + 1];
+  const int d = threadIdx.x;
+  int tot = 0;
+  if (d < nb2)
+    for (int t = t0; t < t1; ++t) {
+      unsigned c = thist2[(long long)t * nb2 + d];
+      thist2[(long long)t * nb2 + d] = (unsigned)tot;
+      tot += (int)c;
+    }
+  int all;
+  int ex = block_excl_sum(d < nb2 ? tot : 0, &all);
+  if (d < nb2) {
+    const unsigned start = (unsigned)(bstart1[b] + ex);
+    for (int t = t0; t < t1; ++t) thist2[(long long)t * nb2 + d] += start;
+    btot[(long long)b * nb2 + d] = tot;
+  }
+}
+
+// Staged scatter (both levels).  Level 1 (tiles == nullptr): tile t is an even
+// share of rows [0, n) and bucket d's write cursor starts at
+// bstart[d] + table[d * ntiles + t].  Level 2: tile t is tiles[t] and the
+// cursor starts at table[t * nb + d].  Output: SoA (okeys/ocols) or rows of
+// 1 + ncols words (oaos).
+__global__ void __launch_bounds__(kPartThreads, 2)
+k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, const Tile2* tiles,
+                 const int* ntiles_dev, const unsigned* table, const long long* bstart,
+                 unsigned long long* okeys, long long* const* ocols, long long* oaos) {
+  extern __shared__ __align__(16) unsigned char st_raw[];
+  unsigned* cursor = reinterpret_cast<unsigned*>(st_raw);
+  unsigned* lst = cursor + nb;
+  const int C = src.ncols;
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(lst + nb + (nb & 1));
+  long long* scol = reinterpret_cast<long long*>(skey + kStage);
+  uint16_t* sperm = reinterpret_cast<uint16_t*>(scol + (long long)C * kStage);
+  const int t = blockIdx.x;
+  long long lo, hi;
+  if (tiles) {
+    if (t >= *ntiles_dev) return;
+    lo = tiles[t].lo;
+    hi = tiles[t].hi;
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) cursor[d] = table[(long long)t * nb + d];
+  } else {
+    tile_range(n, ntiles, t, &lo, &hi);
+    for (int d = threadIdx.x; d < nb; d += blockDim.x)
+      cursor[d] = (unsigned)(bstart[d] + table[(long long)d * ntiles + t]);
+  }
+  const int dsh = tiles ? 0 : dshift;
+  constexpr int U = kStage / kPartThreads;  // 8
+  for (long long s0 = lo; s0 < hi; s0 += kStage) {
+    const int m = (int)min((long long)kStage, hi - s0);
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) lst[d] = 0;
+    __syncthreads();
+    unsigned dr[U];  // digit << 16 | rank
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = threadIdx.x + u * kPartThreads;
+      if (i < m) {
+        unsigned long long k = src_key(src, s0 + i);
+        skey[i] = k;
+        for (int c = 0; c < C; ++c) scol[c * kStage + i] = src_col(src, c, s0 + i);
+        unsigned d = level_digit(dig, k, dsh, nb);
+        unsigned r = atomicAdd(&lst[d], 1u);
+        dr[u] = (d << 16) | r;
+      }
+    }
+    __syncthreads();
+    // local starts: exclusive scan of the per-digit counts, two digits per
+    // thread (nb <= 2 * kPartThreads)
+    {
+      const int d0 = 2 * threadIdx.x;
+      const int c0 = d0 < nb ? (int)lst[d0] : 0;
+      const int c1 = d0 + 1 < nb ? (int)lst[d0 + 1] : 0;
+      int tot;
+      const int ex = block_excl_sum(c0 + c1, &tot);
+      if (d0 < nb) lst[d0] = (unsigned)ex;
+      if (d0 + 1 < nb) lst[d0 + 1] = (unsigned)(ex + c0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = threadIdx.x + u * kPartThreads;
+      if (i < m) sperm[lst[dr[u] >> 16] + (dr[u] & 0xFFFFu)] = (uint16_t)i;
+    }
+    __syncthreads();
+    for (int lp = threadIdx.x; lp < m; lp += kPartThreads) {
+      const int i = sperm[lp];
+      const unsigned long long k = skey[i];
+      const unsigned d = level_digit(dig, k, dsh, nb);
+      const long long gp = (long long)cursor[d] + (lp - (int)lst[d]);
+      if (oaos) {
+        long long* row = oaos + gp * (1 + C);
+        if (C == 1) {
+          longlong2 v;
+          v.x = (long long)k;
+          v.y = scol[i];
+          *reinterpret_cast<longlong2*>(row) = v;
+        } else {
+          row[0] = (long long)k;
+          for (int c = 0; c < C; ++c) row[1 + c] = scol[c * kStage + i];
+        }
+      } else {
+        okeys[gp] = k;
+        for (int c = 0; c < C; ++c) ocols[c][gp] = scol[c * kStage + i];
+      }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) {
+      const unsigned next = (d + 1 < nb) ? lst[d + 1] : (unsigned)m;
+      cursor[d] += next - lst[d];
+    }
+    __syncthreads();
+  }
+}
+
+inline size_t staged_smem_bytes(int nb, int ncols) {
+  return (size_t)(2 * nb + (nb & 1)) * 4 + (size_t)kStage * 8 * (1 + ncols) + (size_t)kStage * 2 + 16;
 }
 
 }  // namespace sg

@@ -4,30 +4,35 @@
 //
 // One CTA takes one chunk (ticket order) of at most kTileCap rows:
 //   1. load the chunk's keys into shared memory (a row range of one source,
-//      or one slice from each of k sorted runs);
+//      or one slice from each of k sorted runs, all loads in flight at once;
+//      the runs' aggregate columns are prefetched into L2 meanwhile);
 //   2. sort a permutation of the chunk by key: a counting sort on the top
-//      kBinBits bits of (key - chunk min); bins are then finished by insertion
+//      kBinBits bits of (key - chunk min); bins are finished by insertion
 //      sort, or -- when some bin is large -- the chunk is sorted by a stable
-//      LSD radix sort (8-bit digits, warp-ballot ranking) over all bits that
-//      vary inside the chunk;
-//   3. mark segment heads (first row of every distinct key) and number the
-//      segments; the segment count is the chunk's output row count;
-//   4. get the chunk's output offset by decoupled look-back;
-//   5. write the distinct keys and, per aggregate, the segmented reduction of
-//      its source column, staged in shared memory so every global store is
-//      coalesced.
+//      LSD radix sort (8-bit digits, warp-ballot ranking) over every bit that
+//      varies inside the chunk;
+//   3. fold equal keys, choosing by the shape of the chunk:
+//        lane per row     key groups of at most 32 rows (uniform keys: the
+//                         common case);
+//        CTA per group    few distinct keys (at most kFewGroups);
+//        warp ranges      anything else: segmented scans over warp ranges;
+//      the chunk's distinct-key count gives its output offset by decoupled
+//      look-back, and aggregate values are gathered by row index from the
+//      source (L2-resident) while the sorted keys stay in shared memory.
 #pragma once
 #include "sg_common.cuh"
 
 namespace sg {
 
-constexpr int kTileCap = 8192;          // rows per chunk
+constexpr int kTileCap = 8192;             // rows per chunk
 constexpr int kThreads = 512;
-constexpr int kEPT = kTileCap / kThreads;  // rows per thread (16)
+constexpr int kWarps = kThreads / 32;
 constexpr int kBinBits = 12;
 constexpr int kBins = 1 << kBinBits;
-constexpr int kMaxFanIn = 512;          // runs one merge chunk can read
-constexpr int kWarps = kThreads / 32;
+constexpr int kBinsPerThread = kBins / kThreads;  // 8
+constexpr int kMaxFanIn = 256;             // runs one merge chunk can read
+constexpr int kFewGroups = 16;             // CTA-per-group fold below this many keys
+constexpr int kAccBlock = 8;               // state columns folded per pass
 
 enum : int { CH_NORMAL = 0, CH_COPY = 1 };
 enum : int { MODE_RANGE = 0, MODE_RUNS = 1, MODE_TILES = 2 };
@@ -40,14 +45,13 @@ struct Chunk {
 };
 
 // k sorted runs of state rows in SoA form, for the wide merge.  Run r's rows
-// with fine digit in [f_lo, f_hi) are rows offs[r*stride + f_lo] ..
-// offs[r*stride + f_hi] - 1 of its arrays.
+// with fine digit in [f_lo, f_hi) are rows offs[r][f_lo] .. offs[r][f_hi] - 1
+// of its arrays (offs[r] is the run's sparse index over fine buckets).
 struct RunSet {
   int k;
   int ncols;
   const long long* const* ptrs;   // [k * (1 + ncols)]: keys, then state columns
-  const long long* offs;
-  long long stride;
+  const long long* const* offs;   // [k] fine-bucket offsets of each run
 };
 
 // Sorted, folded state rows to copy verbatim (key ranges solved elsewhere).
@@ -68,25 +72,23 @@ struct OutSink {
 
 struct SortSmem {
   unsigned long long* keys;   // [kTileCap]
-  long long* work;            // [kTileCap] column buffer / output staging
-  uint16_t* idxA;             // [kTileCap]
-  uint16_t* idxB;             // [kTileCap]
-  uint32_t* bins;             // [kBins / 2] packed 16-bit counters
+  uint16_t* idx;              // [kTileCap] sorted permutation
+  uint16_t* aux;              // [kTileCap] LSD ping-pong, then per-bin distinct prefix
+  uint32_t* bins;             // [kBins / 2] packed 16-bit bin starts / LSD warp histograms
   long long* slo;             // [kMaxFanIn] merge: slice start per run
   long long* spre;            // [kMaxFanIn + 1] merge: slice prefix
 };
 
 constexpr size_t kSortSmemBytes =
-    kTileCap * 8 * 2 + kTileCap * 2 * 2 + (kBins / 2) * 4 + kMaxFanIn * 8 + (kMaxFanIn + 1) * 8 + 64;
+    kTileCap * 8 + kTileCap * 2 * 2 + (kBins / 2) * 4 + kMaxFanIn * 8 + (kMaxFanIn + 1) * 8 + 64;
 
 __device__ __forceinline__ SortSmem carve(unsigned char* base) {
   SortSmem s;
   s.keys = reinterpret_cast<unsigned long long*>(base);
-  s.work = reinterpret_cast<long long*>(base + kTileCap * 8);
-  s.idxA = reinterpret_cast<uint16_t*>(base + kTileCap * 16);
-  s.idxB = reinterpret_cast<uint16_t*>(base + kTileCap * 18);
-  s.bins = reinterpret_cast<uint32_t*>(base + kTileCap * 20);
-  s.slo = reinterpret_cast<long long*>(base + kTileCap * 20 + (kBins / 2) * 4);
+  s.idx = reinterpret_cast<uint16_t*>(base + kTileCap * 8);
+  s.aux = reinterpret_cast<uint16_t*>(base + kTileCap * 10);
+  s.bins = reinterpret_cast<uint32_t*>(base + kTileCap * 12);
+  s.slo = reinterpret_cast<long long*>(base + kTileCap * 12 + (kBins / 2) * 4);
   s.spre = s.slo + kMaxFanIn;
   return s;
 }
@@ -171,82 +173,128 @@ __device__ __forceinline__ int block_max_int(int v) {
   return r;
 }
 
-// Inclusive segmented scan over threads of (flag, value): a set flag starts a
-// new segment.  Returns the exclusive result (the combined value of the
-// thread's segment over all earlier threads), valid when the earlier threads
-// carry part of that segment.
-__device__ __forceinline__ long long block_seg_carry(int op, bool flag, long long val) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  bool f = flag;
-  long long a = val;
-  for (int o = 1; o < 32; o <<= 1) {
-    long long ya = __shfl_up_sync(0xffffffffu, a, o);
-    int yf = __shfl_up_sync(0xffffffffu, (int)f, o);
-    if (lane >= o) {
-      if (!f) a = op_combine(op, ya, a);
-      f = f || yf;
-    }
-  }
-  // a, f: inclusive within the warp
-  __syncthreads();
-  if (lane == 31) { g_red[w] = a; g_redu[w] = f; }
-  __syncthreads();
-  if (w == 0) {
-    long long ta = lane < kWarps ? g_red[lane] : op_identity(op);
-    bool tf = lane < kWarps ? (g_redu[lane] != 0) : false;
-    long long sa = ta;
-    bool sf = tf;
-    for (int o = 1; o < 32; o <<= 1) {
-      long long ya = __shfl_up_sync(0xffffffffu, sa, o);
-      int yf = __shfl_up_sync(0xffffffffu, (int)sf, o);
-      if (lane >= o) {
-        if (!sf) sa = op_combine(op, ya, sa);
-        sf = sf || yf;
-      }
-    }
-    // exclusive across warps
-    long long ea = __shfl_up_sync(0xffffffffu, sa, 1);
-    if (lane == 0) ea = op_identity(op);
-    if (lane < kWarps) g_red[lane] = ea;
-  }
-  __syncthreads();
-  long long wcarry = g_red[w];
-  // exclusive within warp: previous lane's inclusive
-  long long pa = __shfl_up_sync(0xffffffffu, a, 1);
-  int pf = __shfl_up_sync(0xffffffffu, (int)f, 1);
-  long long carry;
-  if (lane == 0) carry = wcarry;
-  else carry = pf ? pa : op_combine(op, wcarry, pa);
-  __syncthreads();
-  return carry;
+__device__ __forceinline__ long long warp_reduce(int op, long long v) {
+  for (int o = 16; o > 0; o >>= 1) v = op_combine(op, v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
 // ---------------------------------------------------------------------------
-// Sort helpers.
+// Row access.
+// ---------------------------------------------------------------------------
+struct ChunkView {
+  long long lo;     // first source row (MODE_RANGE / MODE_TILES)
+  int n;
+  int k;            // MODE_RUNS: runs
+};
+
+// Run holding chunk position i (MODE_RUNS): largest r with spre[r] <= i.
+__device__ __forceinline__ int run_of(const SortSmem& s, int k, int i) {
+  int lo = 0, hi = k - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (s.spre[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Source value of column c (< 0: the constant 1 of count(*)) for chunk row i.
+template <int MODE>
+__device__ __forceinline__ long long row_value(const SortSmem& s, const RowSrc& src, const RunSet& runs,
+                                               const ChunkView& cv, int c, int i) {
+  if (c < 0) return 1;
+  if (MODE == MODE_RUNS) {
+    int r = run_of(s, cv.k, i);
+    const long long* p = runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c];
+    return p[s.slo[r] + (i - s.spre[r])];
+  }
+  if (MODE == MODE_RANGE) return src.aos[(cv.lo + i) * (1 + src.ncols) + 1 + c];  // leaf: rows of the scatter
+  return src_col(src, c, cv.lo + i);
+}
+
+// Where chunk row i's columns live: one address computation per row.
+struct RowAt {
+  const long long* aos;      // MODE_RANGE: the row's first column
+  long long off;             // MODE_RUNS: row inside the run; MODE_TILES: source row
+  int run;                   // MODE_RUNS
+};
+
+template <int MODE>
+__device__ __forceinline__ RowAt row_at(const SortSmem& s, const RowSrc& src, const ChunkView& cv, int i) {
+  RowAt a;
+  a.aos = nullptr;
+  a.run = 0;
+  a.off = 0;
+  if (MODE == MODE_RUNS) {
+    a.run = run_of(s, cv.k, i);
+    a.off = s.slo[a.run] + (i - s.spre[a.run]);
+  } else if (MODE == MODE_RANGE) {
+    a.aos = src.aos + (cv.lo + i) * (1 + src.ncols) + 1;
+  } else {
+    a.off = cv.lo + i;
+  }
+  return a;
+}
+
+template <int MODE>
+__device__ __forceinline__ long long col_at(const RowSrc& src, const RunSet& runs, const RowAt& a, int c) {
+  if (c < 0) return 1;
+  if (MODE == MODE_RUNS) return runs.ptrs[(long long)a.run * (1 + runs.ncols) + 1 + c][a.off];
+  if (MODE == MODE_RANGE) return a.aos[c];
+  return src_col(src, c, a.off);
+}
+
+template <int MODE>
+__device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, const RunSet& runs,
+                                          const ChunkView& cv) {
+  constexpr int U = 8;  // loads in flight per thread
+  for (int base = threadIdx.x; base < cv.n; base += U * kThreads) {
+    unsigned long long v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int i = base + u * kThreads;
+      if (i < cv.n) {
+        if (MODE == MODE_RUNS) {
+          int r = run_of(s, cv.k, i);
+          const long long* p = runs.ptrs[(long long)r * (1 + runs.ncols)];
+          v[u] = (unsigned long long)__ldg(p + s.slo[r] + (i - s.spre[r]));
+        } else {
+          v[u] = src_key(src, cv.lo + i);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int i = base + u * kThreads;
+      if (i < cv.n) s.keys[i] = v[u];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sort.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t bin_get(const uint32_t* bins, int b) {
   return (bins[b >> 1] >> ((b & 1) * 16)) & 0xFFFFu;
 }
 
-// Stable LSD radix sort of idx by (keys[idx] - kmin) over bits [0, vb).
-// Positions are warp-striped so that ranking in (step, lane) order is the
-// input order.  Returns the buffer that holds the result.
-__device__ uint16_t* lsd_sort(const SortSmem& s, int n, unsigned long long kmin, int vb) {
+// Stable LSD radix sort of s.idx by (keys[idx] - kmin) over bits [0, vb);
+// positions are warp-striped so that ranking in (step, lane) order is the
+// input order.  The result is left in s.idx.
+__device__ void lsd_sort(const SortSmem& s, int n, unsigned long long kmin, int vb) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint16_t* in = s.idxA;
-  uint16_t* out = s.idxB;
+  constexpr int EPT = kTileCap / kThreads;
+  uint16_t* in = s.idx;
+  uint16_t* out = s.aux;
   for (int i = threadIdx.x; i < n; i += kThreads) in[i] = (uint16_t)i;
   uint16_t* whist = reinterpret_cast<uint16_t*>(s.bins);  // [kWarps][256]
   const unsigned lt = (1u << lane) - 1;
   for (int p = 0; p < vb; p += 8) {
     for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) whist[i] = 0;
     __syncthreads();
-    uint16_t myidx[kEPT];
-    uint16_t rank[kEPT];
-    uint8_t dg[kEPT];
+    uint32_t packed[EPT];  // rank (16 bits) | digit (8 bits) << 16
 #pragma unroll
-    for (int j = 0; j < kEPT; ++j) {
-      int pos = w * (kEPT * 32) + j * 32 + lane;
+    for (int j = 0; j < EPT; ++j) {
+      int pos = w * (EPT * 32) + j * 32 + lane;
       bool act = pos < n;
       uint16_t id = act ? in[pos] : 0;
       unsigned d = act ? (unsigned)(((s.keys[id] - kmin) >> p) & 0xFFu) : 0u;
@@ -266,12 +314,9 @@ __device__ uint16_t* lsd_sort(const SortSmem& s, int n, unsigned long long kmin,
       }
       unsigned srcl = act ? (unsigned)(__ffs(peers) - 1) : (unsigned)lane;
       base = __shfl_sync(0xffffffffu, base, srcl);
-      myidx[j] = id;
-      rank[j] = (uint16_t)(base + __popc(peers & lt));
-      dg[j] = (uint8_t)d;
+      packed[j] = ((base + __popc(peers & lt)) & 0xFFFFu) | (d << 16);
     }
     __syncthreads();
-    // exclusive scan over (digit, warp)
     {
       int d = threadIdx.x;  // kThreads >= 256
       int tot = 0;
@@ -290,18 +335,24 @@ __device__ uint16_t* lsd_sort(const SortSmem& s, int n, unsigned long long kmin,
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kEPT; ++j) {
-      int pos = w * (kEPT * 32) + j * 32 + lane;
-      if (pos < n) out[whist[w * 256 + dg[j]] + rank[j]] = myidx[j];
+    for (int j = 0; j < EPT; ++j) {
+      int pos = w * (EPT * 32) + j * 32 + lane;
+      if (pos < n) out[whist[w * 256 + (packed[j] >> 16)] + (packed[j] & 0xFFFFu)] = in[pos];
     }
     __syncthreads();
     uint16_t* t = in; in = out; out = t;
   }
-  return in;
+  if (in != s.idx) {
+    for (int i = threadIdx.x; i < n; i += kThreads) s.idx[i] = in[i];
+    __syncthreads();
+  }
 }
 
-// Sort s.idx by key.  Returns the buffer holding the sorted permutation.
-__device__ uint16_t* chunk_sort(const SortSmem& s, int n) {
+enum : int { FOLD_BINS = 0, FOLD_WARPS = 1 };
+
+// Sort s.idx by key; returns FOLD_BINS when s.bins holds bin starts whose bins
+// contain whole key groups of at most 32 rows, else FOLD_WARPS.
+__device__ int chunk_sort(const SortSmem& s, int n) {
   unsigned long long lmin = ~0ull, lmax = 0ull;
   for (int i = threadIdx.x; i < n; i += kThreads) {
     unsigned long long k = s.keys[i];
@@ -310,112 +361,83 @@ __device__ uint16_t* chunk_sort(const SortSmem& s, int n) {
   }
   unsigned long long kmin, kmax;
   block_minmax(lmin, lmax, &kmin, &kmax);
-  if (n == 0) return s.idxA;
+  if (n == 0) {
+    for (int i = threadIdx.x; i < kBins / 2; i += kThreads) s.bins[i] = 0;
+    __syncthreads();
+    return FOLD_BINS;
+  }
   const unsigned long long range = kmax - kmin;
   const int vb = range == 0 ? 0 : 64 - __clzll((long long)range);
   const int sh = vb > kBinBits ? vb - kBinBits : 0;
-  // counting sort on the top bits
   for (int i = threadIdx.x; i < kBins / 2; i += kThreads) s.bins[i] = 0;
   __syncthreads();
-  uint16_t rb[kEPT], rr[kEPT];
-#pragma unroll
-  for (int j = 0; j < kEPT; ++j) {
-    int i = threadIdx.x + j * kThreads;
-    if (i < n) {
-      int b = (int)((s.keys[i] - kmin) >> sh);
-      unsigned sft = (b & 1) * 16;
-      unsigned old = atomicAdd(&s.bins[b >> 1], 1u << sft);
-      rb[j] = (uint16_t)b;
-      rr[j] = (uint16_t)((old >> sft) & 0xFFFFu);
-    }
+  // counting sort on the top bits: rank inside the bin from the atomic
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    int b = (int)((s.keys[i] - kmin) >> sh);
+    unsigned sft = (b & 1) * 16;
+    unsigned old = atomicAdd(&s.bins[b >> 1], 1u << sft);
+    s.aux[i] = (uint16_t)((old >> sft) & 0xFFFFu);
   }
   __syncthreads();
-  // exclusive scan of the bin counts (kBins / kThreads = 8 per thread)
-  constexpr int BPT = kBins / kThreads;
-  int cnt[BPT];
+  int cnt[kBinsPerThread];
   int loc = 0, mx = 0;
 #pragma unroll
-  for (int q = 0; q < BPT; ++q) {
-    cnt[q] = (int)bin_get(s.bins, threadIdx.x * BPT + q);
+  for (int q = 0; q < kBinsPerThread; ++q) {
+    cnt[q] = (int)bin_get(s.bins, threadIdx.x * kBinsPerThread + q);
     loc += cnt[q];
     mx = max(mx, cnt[q]);
   }
   int total;
   int start = block_excl_sum(loc, &total);
-  int maxbin = block_max_int(mx);
-  // write starts back (packed 16-bit; starts <= kTileCap fit)
+  const int maxbin = block_max_int(mx);
 #pragma unroll
-  for (int q = 0; q < BPT; q += 2) {
+  for (int q = 0; q < kBinsPerThread; q += 2) {
     unsigned lo = (unsigned)start;
     start += cnt[q];
     unsigned hi = (unsigned)start;
     start += cnt[q + 1];
-    s.bins[(threadIdx.x * BPT + q) >> 1] = lo | (hi << 16);
+    s.bins[(threadIdx.x * kBinsPerThread + q) >> 1] = lo | (hi << 16);
   }
   __syncthreads();
-#pragma unroll
-  for (int j = 0; j < kEPT; ++j) {
-    int i = threadIdx.x + j * kThreads;
-    if (i < n) s.idxA[bin_get(s.bins, rb[j]) + rr[j]] = (uint16_t)i;
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    int b = (int)((s.keys[i] - kmin) >> sh);
+    s.idx[bin_get(s.bins, b) + s.aux[i]] = (uint16_t)i;
   }
   __syncthreads();
-  if (sh == 0) return s.idxA;  // every bin holds one key value
+  if (sh == 0) return maxbin <= 32 ? FOLD_BINS : FOLD_WARPS;  // every bin is one key value
   if (maxbin <= 32) {
     for (int b = threadIdx.x; b < kBins; b += kThreads) {
       int st = (int)bin_get(s.bins, b);
       int en = (b + 1 < kBins) ? (int)bin_get(s.bins, b + 1) : n;
       for (int i = st + 1; i < en; ++i) {
-        uint16_t v = s.idxA[i];
+        uint16_t v = s.idx[i];
         unsigned long long kv = s.keys[v];
         int j = i - 1;
-        while (j >= st && s.keys[s.idxA[j]] > kv) {
-          s.idxA[j + 1] = s.idxA[j];
+        while (j >= st && s.keys[s.idx[j]] > kv) {
+          s.idx[j + 1] = s.idx[j];
           --j;
         }
-        s.idxA[j + 1] = v;
+        s.idx[j + 1] = v;
       }
     }
     __syncthreads();
-    return s.idxA;
+    return FOLD_BINS;
   }
-  return lsd_sort(s, n, kmin, vb);
+  lsd_sort(s, n, kmin, vb);
+  return FOLD_WARPS;
 }
 
 // ---------------------------------------------------------------------------
-// The kernel.
+// Output helpers.
 // ---------------------------------------------------------------------------
-template <int MODE>
-__device__ __forceinline__ void load_chunk_column(const SortSmem& s, const RowSrc& src,
-                                                  const RunSet& runs, const Chunk& ch, int n,
-                                                  int col, long long* dst_ll,
-                                                  unsigned long long* dst_key) {
-  if (MODE == MODE_RUNS) {
-    for (int r = 0; r < runs.k; ++r) {
-      long long lo = s.slo[r], pre = s.spre[r];
-      int len = (int)(s.spre[r + 1] - pre);
-      const long long* p = runs.ptrs[(long long)r * (1 + runs.ncols) + (col < 0 ? 0 : 1 + col)];
-      for (int i = threadIdx.x; i < len; i += kThreads) {
-        long long v = __ldg(p + lo + i);
-        if (col < 0) dst_key[pre + i] = (unsigned long long)v;
-        else dst_ll[pre + i] = v;
-      }
-    }
-  } else {
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-      if (col < 0) dst_key[i] = src_key(src, ch.lo + i);
-      else dst_ll[i] = src_col(src, col, ch.lo + i);
-    }
-  }
-}
-
 __device__ __forceinline__ void write_fine_offsets(const OutSink& out, const Chunk& ch, long long base,
                                                    long long g, long long count, unsigned long long key,
-                                                   unsigned long long prev_key) {
+                                                   bool has_prev, unsigned long long prev_key) {
   // offs[f] = absolute position of the first row with fine digit >= f; the
   // entry at f_hi (start of the next chunk's range) is written by both
   // neighbours with the same value.
   int f = (int)fine_digit(out.dig, key);
-  int fp = (g == 0) ? ch.f_lo - 1 : (int)fine_digit(out.dig, prev_key);
+  int fp = has_prev ? (int)fine_digit(out.dig, prev_key) : ch.f_lo - 1;
   for (int ff = fp + 1; ff <= f; ++ff) out.offs[ff] = base + g;
   if (g == count - 1)
     for (int ff = f + 1; ff <= ch.f_hi; ++ff) out.offs[ff] = base + count;
@@ -427,18 +449,292 @@ __device__ __forceinline__ void sink_key(const OutSink& out, long long pos, unsi
   else out.keys[pos] = key;
 }
 
+__device__ __forceinline__ void sink_val(const OutSink& out, int st, long long pos, long long v) {
+  if (pos < out.capacity) out.cols[st][pos] = v;
+}
+
+// Publishes `count` for the chunk and returns its base (or -1: stop).
+__device__ __forceinline__ long long chunk_base(const LookBack& lb, const OutSink& out, int cid,
+                                                long long count, long long* s_base) {
+  if (threadIdx.x < 32) {
+    long long b = lookback_warp(lb, cid, count);
+    if (threadIdx.x == 0) {
+      *s_base = b;
+      if (b >= 0 && lb.total_out && cid == lb.n_chunks - 1) *lb.total_out = b + count;
+      if (b >= 0 && b + count > out.capacity) err_raise(lb.err, ERR_CAPACITY);
+    }
+  }
+  __syncthreads();
+  return *s_base;
+}
+
+// ---------------------------------------------------------------------------
+// Fold for small key groups (every group within one bin of <= 32 rows): each
+// warp takes a contiguous range of sorted positions, a lane per position; a
+// lane holding the first row of a group folds the group's rows and writes one
+// output row.  Heads come from a ballot, output positions from popc and one
+// scan over warps, so consecutive lanes write consecutive rows.
+// ---------------------------------------------------------------------------
+__shared__ int g_lcnt[kWarps + 1];
+
+template <int MODE, int KS>
+__device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& runs, const ChunkView& cv,
+                           const FoldDesc& fd, const OutSink& out, const LookBack& lb, const Chunk& ch,
+                           int cid, long long* s_base) {
+  const int n = cv.n;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1;
+  const int Q = ((n + kWarps - 1) / kWarps + 31) & ~31;
+  const int wb = min(n, w * Q), we = min(n, wb + Q);
+  int hc = 0;
+  for (int b = wb; b < we; b += 32) {
+    const int p = b + lane;
+    bool h = false;
+    if (p < we) h = (p == 0) || s.keys[s.idx[p]] != s.keys[s.idx[p - 1]];
+    hc += __popc(__ballot_sync(0xffffffffu, h));
+  }
+  if (lane == 0) g_lcnt[w] = hc;
+  __syncthreads();
+  if (w == 0) {
+    int v = lane < kWarps ? g_lcnt[lane] : 0, x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < kWarps) g_lcnt[lane] = x - v;
+    if (lane == kWarps - 1) g_lcnt[kWarps] = x;
+  }
+  __syncthreads();
+  const int count = g_lcnt[kWarps];
+  const long long base = chunk_base(lb, out, cid, count, s_base);
+  if (base < 0) return;
+  if (out.offs && count == 0 && threadIdx.x == 0)
+    for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
+  int opv[KS], srv[KS];
+#pragma unroll
+  for (int a = 0; a < KS; ++a) {
+    opv[a] = a < fd.n_state ? fd.op[a] : OP_SUM;
+    srv[a] = a < fd.n_state ? fd.src[a] : -1;
+  }
+  const int ns = fd.n_state;
+  int run = g_lcnt[w];
+  for (int b = wb; b < we; b += 32) {
+    const int p = b + lane;
+    unsigned long long key = 0, prev = 0;
+    bool h = false;
+    if (p < we) {
+      key = s.keys[s.idx[p]];
+      if (p > 0) prev = s.keys[s.idx[p - 1]];
+      h = (p == 0) || key != prev;
+    }
+    const unsigned hb = __ballot_sync(0xffffffffu, h);
+    if (h) {
+      const long long g = run + __popc(hb & lt);
+      const long long pos = base + g;
+      long long acc[KS];
+      {
+        RowAt ra = row_at<MODE>(s, src, cv, s.idx[p]);
+#pragma unroll
+        for (int a = 0; a < KS; ++a)
+          if (a < ns) acc[a] = col_at<MODE>(src, runs, ra, srv[a]);
+      }
+      for (int q = p + 1; q < n; ++q) {
+        const int i = s.idx[q];
+        if (s.keys[i] != key) break;
+        RowAt ra = row_at<MODE>(s, src, cv, i);
+#pragma unroll
+        for (int a = 0; a < KS; ++a)
+          if (a < ns) acc[a] = op_combine(opv[a], acc[a], col_at<MODE>(src, runs, ra, srv[a]));
+      }
+      sink_key(out, pos, key);
+      if (out.offs) write_fine_offsets(out, ch, base, g, count, key, p > 0, prev);
+#pragma unroll
+      for (int a = 0; a < KS; ++a)
+        if (a < ns) sink_val(out, a, pos, acc[a]);
+    }
+    run += __popc(hb);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fold: warp ranges over sorted positions with segmented warp scans, or --
+// with few distinct keys -- the whole CTA reducing one key group at a time.
+// ---------------------------------------------------------------------------
+__shared__ int g_wcnt[kWarps + 1];
+__shared__ long long g_wtail[kWarps];
+__shared__ int g_whead[kWarps];
+__shared__ int g_gstart[kFewGroups + 1];
+__shared__ long long g_gacc[kWarps * kAccBlock];
+
+__device__ __forceinline__ bool is_head(const SortSmem& s, int p) {
+  return p == 0 || s.keys[s.idx[p]] != s.keys[s.idx[p - 1]];
+}
+
+// Inclusive segmented scan across the warp: flag starts a segment.
+__device__ __forceinline__ long long warp_seg_scan(int op, bool flag, long long v) {
+  const int lane = threadIdx.x & 31;
+  unsigned fl = __ballot_sync(0xffffffffu, flag);
+  // first lane of my segment within this warp step
+  unsigned upto = fl & ((lane == 31) ? 0xffffffffu : ((2u << lane) - 1));
+  int seg_start = upto ? 31 - __clz(upto) : 0;
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane - o >= seg_start) v = op_combine(op, y, v);
+  }
+  return v;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+__device__ void fold_warps(const SortSmem& s, const RowSrc& src, const RunSet& runs, const ChunkView& cv,
+                           const FoldDesc& fd, const OutSink& out, const LookBack& lb, const Chunk& ch,
+                           int cid, long long* s_base) {
+  const int n = cv.n;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1);
+  const int Q = ((n + kWarps - 1) / kWarps + 31) & ~31;
+  const int wb = min(n, w * Q), we = min(n, wb + Q);
+  // heads per warp range
+  int hc = 0;
+  for (int b = wb; b < we; b += 32) {
+    int p = b + lane;
+    bool h = p < we && is_head(s, p);
+    hc += __popc(__ballot_sync(0xffffffffu, h));
+  }
+  if (lane == 0) g_wcnt[w] = hc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int i = 0; i < kWarps; ++i) { int c = g_wcnt[i]; g_wcnt[i] = acc; acc += c; }
+    g_wcnt[kWarps] = acc;
+  }
+  __syncthreads();
+  const int count = g_wcnt[kWarps];
+  const long long base = chunk_base(lb, out, cid, count, s_base);
+  if (base < 0) return;
+  if (out.offs && count == 0 && threadIdx.x == 0)
+    for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
+
+  // keys (and run offsets)
+  {
+    int run = g_wcnt[w];
+    for (int b = wb; b < we; b += 32) {
+      int p = b + lane;
+      bool h = p < we && is_head(s, p);
+      unsigned hb = __ballot_sync(0xffffffffu, h);
+      if (h) {
+        long long g = run + __popc(hb & le) - 1;
+        unsigned long long key = s.keys[s.idx[p]];
+        if (count <= kFewGroups) g_gstart[g] = p;
+        sink_key(out, base + g, key);
+        if (out.offs) write_fine_offsets(out, ch, base, g, count, key, p > 0, p > 0 ? s.keys[s.idx[p - 1]] : 0ull);
+      }
+      run += __popc(hb);
+    }
+  }
+
+  if (count <= kFewGroups) {
+    // few key groups: the CTA reduces one group at a time, kAccBlock
+    // aggregates per sweep
+    if (threadIdx.x == 0) g_gstart[count] = n;
+    __syncthreads();
+    for (int g = 0; g < count; ++g) {
+      const int gs = g_gstart[g], ge = g_gstart[g + 1];
+      for (int s0 = 0; s0 < fd.n_state; s0 += kAccBlock) {
+        long long acc[kAccBlock];
+#pragma unroll
+        for (int a = 0; a < kAccBlock; ++a)
+          if (s0 + a < fd.n_state) acc[a] = op_identity(fd.op[s0 + a]);
+        for (int p = gs + threadIdx.x; p < ge; p += kThreads) {
+          const int i = s.idx[p];
+#pragma unroll
+          for (int a = 0; a < kAccBlock; ++a)
+            if (s0 + a < fd.n_state)
+              acc[a] = op_combine(fd.op[s0 + a], acc[a], row_value<MODE>(s, src, runs, cv, fd.src[s0 + a], i));
+        }
+#pragma unroll
+        for (int a = 0; a < kAccBlock; ++a)
+          if (s0 + a < fd.n_state) {
+            long long v = warp_reduce(fd.op[s0 + a], acc[a]);
+            if (lane == 0) g_gacc[w * kAccBlock + a] = v;
+          }
+        __syncthreads();
+        if (threadIdx.x < kAccBlock && s0 + (int)threadIdx.x < fd.n_state) {
+          const int a = threadIdx.x, op = fd.op[s0 + a];
+          long long v = op_identity(op);
+          for (int ww = 0; ww < kWarps; ++ww) v = op_combine(op, v, g_gacc[ww * kAccBlock + a]);
+          sink_val(out, s0 + a, base + g, v);
+        }
+        __syncthreads();
+      }
+    }
+    return;
+  }
+
+  for (int st = 0; st < fd.n_state; ++st) {
+    const int op = fd.op[st];
+    const int c = fd.src[st];
+    // pass A: partial of the segment open at the end of this warp's range
+    long long carry = op_identity(op);
+    bool any_head = false;
+    for (int b = wb; b < we; b += 32) {
+      int p = b + lane;
+      bool valid = p < we;
+      bool h = valid && is_head(s, p);
+      long long v = valid ? row_value<MODE>(s, src, runs, cv, c, s.idx[p]) : op_identity(op);
+      bool f = h || lane == 0;
+      if (lane == 0 && !h) v = op_combine(op, carry, v);
+      long long x = warp_seg_scan(op, f, v);
+      carry = __shfl_sync(0xffffffffu, x, 31);
+      any_head |= __ballot_sync(0xffffffffu, h) != 0;
+    }
+    if (lane == 0) { g_wtail[w] = carry; g_whead[w] = any_head; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // exclusive segmented scan over warps (in place)
+      long long acc = op_identity(op);
+      for (int i = 0; i < kWarps; ++i) {
+        long long t = g_wtail[i];
+        int hh = g_whead[i];
+        g_wtail[i] = acc;
+        acc = hh ? t : op_combine(op, acc, t);
+      }
+    }
+    __syncthreads();
+    // pass B: complete segments
+    carry = g_wtail[w];
+    int run = g_wcnt[w];
+    for (int b = wb; b < we; b += 32) {
+      int p = b + lane;
+      bool valid = p < we;
+      bool h = valid && is_head(s, p);
+      long long v = valid ? row_value<MODE>(s, src, runs, cv, c, s.idx[p]) : op_identity(op);
+      bool f = h || lane == 0;
+      if (lane == 0 && !h) v = op_combine(op, carry, v);
+      long long x = warp_seg_scan(op, f, v);
+      unsigned hb = __ballot_sync(0xffffffffu, h);
+      bool ends = valid && (p + 1 >= n || is_head(s, p + 1));
+      if (ends) sink_val(out, st, base + run + __popc(hb & le) - 1, x);
+      run += __popc(hb);
+      carry = __shfl_sync(0xffffffffu, x, 31);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.
+// ---------------------------------------------------------------------------
+template <int MODE, int KS>
+__global__ void __launch_bounds__(kThreads, 2)
 k_sortfold(const Chunk* __restrict__ chunks, RowSrc src, RunSet runs, CopySrc copy, FoldDesc fd,
            OutSink out, LookBack lb, long long tile_n, int tile_f_hi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem s = carve(smem_raw);
   __shared__ int s_cid;
+  __shared__ int s_err;
   __shared__ long long s_base;
   __shared__ int s_n;
-  __shared__ int s_count;
 
-  __shared__ int s_err;
   if (threadIdx.x == 0) {
     s_cid = (int)atomicAdd(lb.ticket, 1u);
     s_err = err_load(lb.err);
@@ -458,188 +754,76 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src, RunSet runs, CopySrc co
 
   if (ch.kind == CH_COPY) {
     const long long n = ch.hi - ch.lo;
-    if (threadIdx.x < 32) {
-      long long b = lookback_warp(lb, cid, n);
-      if (threadIdx.x == 0) {
-        s_base = b;
-        if (b >= 0 && lb.total_out && cid == lb.n_chunks - 1) *lb.total_out = b + n;
-        if (b >= 0 && b + n > out.capacity) err_raise(lb.err, ERR_CAPACITY);
-      }
-    }
-    __syncthreads();
-    const long long base = s_base;
+    const long long base = chunk_base(lb, out, cid, n, &s_base);
     if (base < 0) return;
     for (long long g = threadIdx.x; g < n; g += kThreads) {
       unsigned long long key = copy.keys[ch.lo + g];
       sink_key(out, base + g, key);
-      if (out.offs) {
-        unsigned long long pk = g > 0 ? copy.keys[ch.lo + g - 1] : 0ull;
-        write_fine_offsets(out, ch, base, g, n, key, pk);
-      }
-      if (base + g < out.capacity)
-        for (int st = 0; st < fd.n_state; ++st) out.cols[st][base + g] = copy.cols[st][ch.lo + g];
+      if (out.offs)
+        write_fine_offsets(out, ch, base, g, n, key, g > 0, g > 0 ? copy.keys[ch.lo + g - 1] : 0ull);
+      for (int st = 0; st < fd.n_state; ++st) sink_val(out, st, base + g, copy.cols[st][ch.lo + g]);
     }
     if (out.offs && n == 0 && threadIdx.x == 0)
       for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
     return;
   }
 
-  // ---- 1. keys ----
+  ChunkView cv;
+  cv.lo = ch.lo;
+  cv.k = 0;
   if (MODE == MODE_RUNS) {
     const int k = runs.k;
+    cv.k = k;
     for (int r = threadIdx.x; r < k; r += kThreads) {
-      long long lo = runs.offs[(long long)r * runs.stride + ch.f_lo];
-      long long hi = runs.offs[(long long)r * runs.stride + ch.f_hi];
+      long long lo = runs.offs[r][ch.f_lo];
+      long long hi = runs.offs[r][ch.f_hi];
       s.slo[r] = lo;
       s.spre[r + 1] = hi - lo;
+      // pull the slice's aggregate columns into L2 while the keys sort
+      for (int c = 0; c < runs.ncols; ++c) {
+        const long long* p = runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c] + lo;
+        unsigned long long a0 = reinterpret_cast<unsigned long long>(p) & ~15ull;
+        unsigned long long a1 = (reinterpret_cast<unsigned long long>(p + (hi - lo)) + 15ull) & ~15ull;
+        if (a1 > a0)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((unsigned)(a1 - a0))
+                       : "memory");
+      }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      long long acc = 0;
-      s.spre[0] = 0;
-      for (int r = 0; r < k; ++r) { acc += s.spre[r + 1]; s.spre[r + 1] = acc; }
-      s_n = (int)min(acc, (long long)kTileCap + 1);
+    if (threadIdx.x < 32) {
+      // prefix over k <= kMaxFanIn slice lengths
+      long long run = 0;
+      for (int b = 0; b < k; b += 32) {
+        int r = b + threadIdx.x;
+        long long v = r < k ? s.spre[r + 1] : 0;
+        long long x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+          long long y = __shfl_up_sync(0xffffffffu, x, o);
+          if ((int)threadIdx.x >= o) x += y;
+        }
+        if (r < k) s.spre[r + 1] = run + x;
+        run += __shfl_sync(0xffffffffu, x, 31);
+      }
+      if (threadIdx.x == 0) {
+        s.spre[0] = 0;
+        s_n = (int)min(run, (long long)kTileCap + 1);
+      }
     }
     __syncthreads();
   } else {
     if (threadIdx.x == 0) s_n = (int)(ch.hi - ch.lo);
     __syncthreads();
   }
-  const int n = s_n;
-  if (n > kTileCap) {  // the planner never makes such chunks
+  cv.n = s_n;
+  if (cv.n > kTileCap) {  // the planner never makes such chunks
     if (threadIdx.x == 0) err_raise(lb.err, ERR_INTERNAL);
     return;
   }
-  load_chunk_column<MODE>(s, src, runs, ch, n, -1, nullptr, s.keys);
+  load_keys<MODE>(s, src, runs, cv);
   __syncthreads();
-
-  // ---- 2. sort ----
-  uint16_t* sidx = chunk_sort(s, n);
-  uint16_t* segid = (sidx == s.idxA) ? s.idxB : s.idxA;
-
-  // ---- 3. segment heads / ids over contiguous strips ----
-  const int s0 = threadIdx.x * kEPT;
-  unsigned hmask = 0;
-  int hc = 0;
-#pragma unroll
-  for (int j = 0; j < kEPT; ++j) {
-    int p = s0 + j;
-    if (p < n) {
-      bool h = (p == 0) || (s.keys[sidx[p]] != s.keys[sidx[p - 1]]);
-      hmask |= (unsigned)h << j;
-      hc += h;
-    }
-  }
-  int count;
-  int g0 = block_excl_sum(hc, &count);
-  {
-    int g = g0 - 1;
-#pragma unroll
-    for (int j = 0; j < kEPT; ++j) {
-      int p = s0 + j;
-      if (p < n) {
-        g += (hmask >> j) & 1u;
-        segid[p] = (uint16_t)g;
-      }
-    }
-  }
-  // is the first row of the next strip a head (ends my last segment)?
-  const bool next_head = (s0 + kEPT >= n) || (s0 + kEPT < n && (s.keys[sidx[s0 + kEPT]] != s.keys[sidx[s0 + kEPT - 1]]));
-
-  // ---- 4. output offset ----
-  if (threadIdx.x < 32) {
-    long long b = lookback_warp(lb, cid, count);
-    if (threadIdx.x == 0) {
-      s_base = b;
-      s_count = count;
-      if (b >= 0 && lb.total_out && cid == lb.n_chunks - 1) *lb.total_out = b + count;
-      if (b >= 0 && b + count > out.capacity) err_raise(lb.err, ERR_CAPACITY);
-    }
-  }
-  __syncthreads();
-  const long long base = s_base;
-  if (base < 0) return;
-
-  // ---- 5a. distinct keys, staged in work[] ----
-  {
-    unsigned long long kr[kEPT];
-#pragma unroll
-    for (int j = 0; j < kEPT; ++j) {
-      int p = s0 + j;
-      kr[j] = p < n ? s.keys[sidx[p]] : 0ull;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kEPT; ++j) {
-      int p = s0 + j;
-      if (p < n && ((hmask >> j) & 1u)) s.work[segid[p]] = (long long)kr[j];
-    }
-  }
-  __syncthreads();
-  for (int g = threadIdx.x; g < count; g += kThreads) {
-    unsigned long long key = (unsigned long long)s.work[g];
-    sink_key(out, base + g, key);
-    if (out.offs) write_fine_offsets(out, ch, base, g, count,
-                                     key, g > 0 ? (unsigned long long)s.work[g - 1] : 0ull);
-  }
-  if (out.offs && count == 0 && threadIdx.x == 0)
-    for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
-  __syncthreads();
-
-  // ---- 5b. aggregates, one source column at a time ----
-  const int ncols_src = (MODE == MODE_RUNS) ? runs.ncols : src.ncols;
-  for (int c = -1; c < ncols_src; ++c) {
-    bool used = false;
-    for (int st = 0; st < fd.n_state; ++st) used |= (fd.src[st] == c);
-    if (!used) continue;
-    long long v[kEPT];
-    if (c >= 0) {
-      load_chunk_column<MODE>(s, src, runs, ch, n, c, s.work, nullptr);
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < kEPT; ++j) {
-        int p = s0 + j;
-        v[j] = p < n ? s.work[sidx[p]] : 0;
-      }
-      __syncthreads();
-    } else {
-#pragma unroll
-      for (int j = 0; j < kEPT; ++j) v[j] = 1;
-    }
-    for (int st = 0; st < fd.n_state; ++st) {
-      if (fd.src[st] != c) continue;
-      const int op = fd.op[st];
-      // pass 1: partial of the strip's last segment
-      long long acc = op_identity(op);
-      bool hh = false;
-#pragma unroll
-      for (int j = 0; j < kEPT; ++j) {
-        int p = s0 + j;
-        if (p < n) {
-          if ((hmask >> j) & 1u) { acc = v[j]; hh = true; }
-          else acc = op_combine(op, acc, v[j]);
-        }
-      }
-      long long carry = block_seg_carry(op, hh, acc);
-      // pass 2: complete segments, staged by segment id (a strip that starts
-      // with a head overwrites the carry at once)
-      acc = carry;
-#pragma unroll
-      for (int j = 0; j < kEPT; ++j) {
-        int p = s0 + j;
-        if (p < n) {
-          if ((hmask >> j) & 1u) acc = v[j];
-          else acc = op_combine(op, acc, v[j]);
-          bool ends = (j == kEPT - 1) ? next_head : (((hmask >> (j + 1)) & 1u) != 0 || p + 1 >= n);
-          if (ends) s.work[segid[p]] = acc;
-        }
-      }
-      __syncthreads();
-      for (int g = threadIdx.x; g < count; g += kThreads)
-        if (base + g < out.capacity) out.cols[st][base + g] = s.work[g];
-      __syncthreads();
-    }
-  }
+  const int how = chunk_sort(s, cv.n);
+  if (how == FOLD_BINS) fold_lanes<MODE, KS>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
+  else fold_warps<MODE>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
 }
 
 }  // namespace sg

@@ -50,6 +50,14 @@ struct Run {
   int host;          // 1: pinned host arena
 };
 
+// A sorted run of state rows as the merge sees it (device-accessible pointers).
+struct RunRef {
+  const long long* keys;
+  const long long* cols[sg::kMaxCols];
+  long long* offs;   // nf + 1 fine-bucket offsets (absolute rows of its arrays)
+  long long rows;
+};
+
 }  // namespace
 
 struct sgagg_ctx {
@@ -94,6 +102,9 @@ struct sgagg_ctx {
   std::vector<DevBuf> gather_cols;
   DevBuf gather_ptrs;
   DevBuf runstarts;              // batches + 1 device scalars
+  DevBuf marena_keys;            // runs written by preliminary merges
+  std::vector<DevBuf> marena_cols;
+  DevBuf moffs;
   // host arena (pinned, mapped)
   void* harena_keys = nullptr;
   std::vector<void*> harena_cols;
@@ -269,14 +280,24 @@ bool want_prefold(sgagg_t h, long long sample_n, long long distinct) {
   return per_tile * 2.0 <= (double)kTileCap;
 }
 
-template <int MODE>
+template <int MODE, int KS>
 void set_smem_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_sortfold<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_sortfold<MODE, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kSortSmemBytes);
     done = true;
   }
+}
+
+// Launch the sort+fold kernel specialized for the number of aggregates.
+template <int MODE, int KS>
+void launch_ks(int grid, cudaStream_t st, const Chunk* dchunks, const RowSrc& src, const RunSet& runs,
+               const CopySrc& copy, const FoldDesc& fd, const OutSink& out, const LookBack& lb,
+               long long tile_n, int tile_f_hi) {
+  set_smem_attr<MODE, KS>();
+  k_sortfold<MODE, KS><<<grid, kThreads, kSortSmemBytes, st>>>(dchunks, src, runs, copy, fd, out, lb, tile_n,
+                                                              tile_f_hi);
 }
 
 constexpr int kMaxCoarseBits = 15;  // per-tile histogram / cursors: 2^15 x 4 B of shared memory
@@ -328,10 +349,17 @@ sgagg_status launch_sortfold(sgagg_t h, int cls, const Chunk* dchunks, int n_chu
   lb.n_chunks = n_chunks;
   lb.stall = h->test_stall;
   h->test_stall = 0;
-  set_smem_attr<MODE>();
   kbegin(h, cls);
-  k_sortfold<MODE><<<n_chunks, kThreads, kSortSmemBytes, h->stream>>>(dchunks, src, runs, copy, fd, out,
-                                                                      lb, tile_n, tile_f_hi);
+  if (fd.n_state <= 2)
+    launch_ks<MODE, 2>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
+  else if (fd.n_state <= 4)
+    launch_ks<MODE, 4>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
+  else if (fd.n_state <= 8)
+    launch_ks<MODE, 8>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
+  else if (fd.n_state <= 16)
+    launch_ks<MODE, 16>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
+  else
+    launch_ks<MODE, 32>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
   kend(h);
   CU(cudaGetLastError());
   return SGAGG_OK;
@@ -671,6 +699,130 @@ T* host_dev_ptr(sgagg_t h, void* p) {
   return reinterpret_cast<T*>(d);
 }
 
+// One wide merge (Sec. 4): every run is cut by the same fine-bucket
+// boundaries (their sparse indexes); the planner groups fine buckets into
+// merge tiles of at most kTileCap rows over all runs, and one CTA per tile
+// folds equal keys across runs.  A tile bigger than that (a key range dense
+// in many runs) is gathered and solved on its own first, then copied.
+sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const FoldDesc& fid, int nf,
+                        const OutSink& out, const long long* base_in, long long* total_out, long long* end,
+                        bool final_merge) {
+  cudaStream_t stream = h->stream;
+  Small* ds = dsmall(h);
+  HostSmall* hs = hsmall(h);
+  const int K = (int)rr.size();
+  const long long row_bytes = 8ll * (1 + S);
+  std::vector<const long long*> hp((size_t)K * (1 + S) + K);
+  long long in_rows = 0;
+  for (int r = 0; r < K; ++r) {
+    hp[(size_t)r * (1 + S)] = rr[r].keys;
+    for (int s = 0; s < S; ++s) hp[(size_t)r * (1 + S) + 1 + s] = rr[r].cols[s];
+    hp[(size_t)K * (1 + S) + r] = rr[r].offs;
+    in_rows += rr[r].rows;
+  }
+  TRY(grow(h, h->runptrs, hp.size() * 8));
+  CU(cudaMemcpyAsync(h->runptrs.p, hp.data(), hp.size() * 8, cudaMemcpyHostToDevice, stream));
+  RunSet rset{};
+  rset.k = K;
+  rset.ncols = S;
+  rset.ptrs = reinterpret_cast<const long long* const*>(h->runptrs.p);
+  rset.offs = reinterpret_cast<const long long* const*>(h->runptrs.p) + (size_t)K * (1 + S);
+
+  TRY(grow(h, h->fsizes, (size_t)nf * 8));
+  kbegin(h, SGAGG_K_PLAN);
+  k_fine_sizes<<<std::max(1, std::min(4 * h->num_sms, (nf + 255) / 256)), 256, 0, stream>>>(
+      rset.offs, K, nf, P<long long>(h->fsizes));
+  kend(h);
+  kbytes(h, SGAGG_K_PLAN, (long long)K * (nf + 1) * 8 + nf * 8ll);
+  TRY(grow(h, h->bstart[0], (size_t)(nf + 1) * 8));
+  TRY(grow(h, h->chunks[0], (size_t)nf * sizeof(Chunk)));
+  TRY(grow(h, h->biglist[0], (size_t)nf * 4));
+  kbegin(h, SGAGG_K_PLAN);
+  k_plan<<<1, 1024, 0, stream>>>(P<long long>(h->fsizes), nf, kChunkTarget, kBigBucket, 0,
+                                 P<long long>(h->bstart[0]), P<Chunk>(h->chunks[0]), P<int>(h->biglist[0]),
+                                 &ds->info);
+  kend(h);
+  CU(cudaGetLastError());
+  TRY(sync_read(h, &hs->info, &ds->info, sizeof(PlanInfo)));
+  PlanInfo info = hs->info;
+  if (final_merge) h->st.merge_tiles = info.n_chunks;
+  CopySrc copy{};
+  if (info.n_big > 0) {
+    std::vector<int> big(info.n_big);
+    TRY(sync_read(h, big.data(), h->biglist[0].p, (size_t)info.n_big * 4));
+    std::vector<Chunk> bch(info.n_big);
+    long long tot = 0;
+    for (int i = 0; i < info.n_big; ++i) {
+      CU(cudaMemcpy(&bch[i], P<Chunk>(h->chunks[0]) + big[i], sizeof(Chunk), cudaMemcpyDeviceToHost));
+      tot += bch[i].hi - bch[i].lo;
+    }
+    TRY(grow(h, h->copykeys[0], (size_t)tot * 8));
+    TRY(grow_cols(h, h->copycols[0], S, (size_t)tot * 8));
+    OutSink co{};
+    co.user = 0;
+    co.keys = P<unsigned long long>(h->copykeys[0]);
+    for (int s = 0; s < S; ++s) co.cols[s] = P<long long>(h->copycols[0][s]);
+    co.capacity = tot;
+    long long at = 0;
+    for (int i = 0; i < info.n_big; ++i) {
+      // gather the tile's rows from every run into one SoA buffer
+      long long m = bch[i].hi - bch[i].lo;
+      std::vector<long long> lo(K), hi(K), pre(K + 1, 0);
+      for (int r = 0; r < K; ++r) {
+        CU(cudaMemcpy(&lo[r], rr[r].offs + bch[i].f_lo, 8, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(&hi[r], rr[r].offs + bch[i].f_hi, 8, cudaMemcpyDeviceToHost));
+        pre[r + 1] = pre[r] + (hi[r] - lo[r]);
+      }
+      TRY(grow(h, h->gather_keys, (size_t)m * 8));
+      TRY(grow_cols(h, h->gather_cols, S, (size_t)m * 8));
+      std::vector<long long*> gcols(std::max(1, S));
+      for (int s = 0; s < S; ++s) gcols[s] = P<long long>(h->gather_cols[s]);
+      TRY(grow(h, h->gather_ptrs, (size_t)(std::max(1, S) + K + 1) * 8));
+      long long* dpre = P<long long>(h->gather_ptrs);
+      long long** dcols = reinterpret_cast<long long**>(dpre + K + 1);
+      CU(cudaMemcpy(dpre, pre.data(), (size_t)(K + 1) * 8, cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(dcols, gcols.data(), (size_t)std::max(1, S) * 8, cudaMemcpyHostToDevice));
+      dim3 grid(std::max(1, std::min(64, (int)((m / K + 255) / 256))), K);
+      kbegin(h, SGAGG_K_OTHER);
+      k_gather_runs<<<grid, 256, 0, stream>>>(rset, bch[i].f_lo, bch[i].f_hi, dpre,
+                                              P<unsigned long long>(h->gather_keys), dcols);
+      kend(h);
+      kbytes(h, SGAGG_K_OTHER, m * 16ll * (1 + S));
+      RowSrc gs{};
+      gs.kind = SRC_SOA;
+      gs.ncols = S;
+      gs.keys = P<unsigned long long>(h->gather_keys);
+      for (int s = 0; s < S; ++s) gs.cols[s] = gcols[s];
+      long long* tdev = &ds->dtot[kMaxDepth + 1];
+      hs->v[0] = at;
+      CU(cudaMemcpyAsync(tdev, &hs->v[0], 8, cudaMemcpyHostToDevice, stream));
+      CU(cudaStreamSynchronize(stream));
+      TRY(solve(h, gs, m, fid, co, tdev, tdev, nullptr, 1));
+      ++h->st.split_segments;
+      TRY(sync_read(h, &hs->v[1], tdev, 8));
+      TRY(check_device_err(h));
+      long long e = hs->v[1];
+      bch[i].lo = at;
+      bch[i].hi = e;
+      at = e;
+      CU(cudaMemcpy(P<Chunk>(h->chunks[0]) + big[i], &bch[i], sizeof(Chunk), cudaMemcpyHostToDevice));
+    }
+    copy.keys = co.keys;
+    for (int s = 0; s < S; ++s) copy.cols[s] = co.cols[s];
+  }
+  RowSrc nosrc{};
+  nosrc.ncols = 0;
+  TRY(launch_sortfold<MODE_RUNS>(h, SGAGG_K_MERGE, P<Chunk>(h->chunks[0]), info.n_chunks, 0, nosrc, rset, copy,
+                                 fid, out, base_in, total_out));
+  TRY(sync_read(h, &hs->v[0], total_out, 8));
+  TRY(check_device_err(h));
+  *end = hs->v[0];
+  const long long out_row_bytes = out.user ? (h->key_bytes + 8ll * S) : row_bytes;
+  kbytes(h, SGAGG_K_MERGE, in_rows * row_bytes);
+  kbytes(h, SGAGG_K_MERGE, (final_merge ? *end : 0) * out_row_bytes);
+  return SGAGG_OK;
+}
+
 // The whole operation on device-resident inputs.
 sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* const* payload_cols,
                               int32_t n_payload, int64_t n, const sgagg_spec* spec, void* const* out_keys,
@@ -865,122 +1017,81 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
   h->st.runs = B;
 
   // ---- wide merge ----
-  int K = (int)B;
-  std::vector<long long> hptrs((size_t)K * (1 + S));
-  for (int r = 0; r < K; ++r) {
-    if (runs[r].host) {
-      hptrs[(size_t)r * (1 + S)] = (long long)host_dev_ptr<long long>(h, h->harena_keys);
-      for (int s = 0; s < S; ++s) hptrs[(size_t)r * (1 + S) + 1 + s] = (long long)host_dev_ptr<long long>(h, h->harena_cols[s]);
+  std::vector<RunRef> rr(B);
+  for (long long b2 = 0; b2 < B; ++b2) {
+    RunRef& r = rr[b2];
+    if (runs[b2].host) {
+      r.keys = host_dev_ptr<long long>(h, h->harena_keys);
+      for (int s = 0; s < S; ++s) r.cols[s] = host_dev_ptr<long long>(h, h->harena_cols[s]);
     } else {
-      hptrs[(size_t)r * (1 + S)] = (long long)h->arena_keys.p;
-      for (int s = 0; s < S; ++s) hptrs[(size_t)r * (1 + S) + 1 + s] = (long long)h->arena_cols[s].p;
+      r.keys = P<long long>(h->arena_keys);
+      for (int s = 0; s < S; ++s) r.cols[s] = P<long long>(h->arena_cols[s]);
     }
+    r.offs = P<long long>(h->offs) + b2 * stride;
+    r.rows = runs[b2].rows;
   }
-  if (K > kMaxFanIn || (h->fanin_cap > 0 && K > h->fanin_cap))
-    return fail(h, SGAGG_EINVAL, "too many runs for one wide merge (raise memory_budget_rows)");
-  TRY(grow(h, h->runptrs, hptrs.size() * 8));
-  CU(cudaMemcpyAsync(h->runptrs.p, hptrs.data(), hptrs.size() * 8, cudaMemcpyHostToDevice, stream));
-  RunSet rset{};
-  rset.k = K;
-  rset.ncols = S;
-  rset.ptrs = reinterpret_cast<const long long* const*>(h->runptrs.p);
-  rset.offs = P<long long>(h->offs);
-  rset.stride = stride;
   FoldDesc fid = identity_fold(fd);
-
-  TRY(grow(h, h->fsizes, (size_t)nf * 8));
-  kbegin(h, SGAGG_K_PLAN);
-  k_fine_sizes<<<std::max(1, std::min(4 * h->num_sms, (nf + 255) / 256)), 256, 0, stream>>>(
-      rset.offs, K, stride, nf, P<long long>(h->fsizes));
-  kend(h);
-  kbytes(h, SGAGG_K_PLAN, (long long)K * stride * 8 + nf * 8ll);
-  TRY(ensure_depth(h, 0));
-  TRY(grow(h, h->bstart[0], (size_t)(nf + 1) * 8));
-  TRY(grow(h, h->chunks[0], (size_t)nf * sizeof(Chunk)));
-  TRY(grow(h, h->biglist[0], (size_t)nf * 4));
-  kbegin(h, SGAGG_K_PLAN);
-  k_plan<<<1, 1024, 0, stream>>>(P<long long>(h->fsizes), nf, kChunkTarget, kBigBucket, 0,
-                                 P<long long>(h->bstart[0]), P<Chunk>(h->chunks[0]), P<int>(h->biglist[0]),
-                                 &ds->info);
-  kend(h);
-  CU(cudaGetLastError());
-  TRY(sync_read(h, &hs->info, &ds->info, sizeof(PlanInfo)));
-  PlanInfo info = hs->info;
-  h->st.merge_tiles = info.n_chunks;
-  CopySrc copy{};
-  if (info.n_big > 0) {
-    std::vector<int> big(info.n_big);
-    TRY(sync_read(h, big.data(), h->biglist[0].p, (size_t)info.n_big * 4));
-    std::vector<Chunk> bch(info.n_big);
-    long long tot = 0;
-    for (int i = 0; i < info.n_big; ++i) {
-      CU(cudaMemcpy(&bch[i], P<Chunk>(h->chunks[0]) + big[i], sizeof(Chunk), cudaMemcpyDeviceToHost));
-      tot += bch[i].hi - bch[i].lo;
-    }
-    TRY(grow(h, h->copykeys[0], (size_t)tot * 8));
-    TRY(grow_cols(h, h->copycols[0], S, (size_t)tot * 8));
-    OutSink co{};
-    co.user = 0;
-    co.keys = P<unsigned long long>(h->copykeys[0]);
-    for (int s = 0; s < S; ++s) co.cols[s] = P<long long>(h->copycols[0][s]);
-    co.capacity = tot;
-    long long at = 0;
-    for (int i = 0; i < info.n_big; ++i) {
-      // gather the tile's rows from every run into one SoA buffer
-      long long m = bch[i].hi - bch[i].lo;
-      std::vector<long long> lo(K), hi(K), pre(K + 1, 0);
-      for (int r = 0; r < K; ++r) {
-        CU(cudaMemcpy(&lo[r], P<long long>(h->offs) + (long long)r * stride + bch[i].f_lo, 8, cudaMemcpyDeviceToHost));
-        CU(cudaMemcpy(&hi[r], P<long long>(h->offs) + (long long)r * stride + bch[i].f_hi, 8, cudaMemcpyDeviceToHost));
-        pre[r + 1] = pre[r] + (hi[r] - lo[r]);
+  const int cap = (h->fanin_cap > 0) ? std::min(h->fanin_cap, kMaxFanIn) : kMaxFanIn;
+  if ((int)rr.size() > cap) {
+    // preliminary merges of the smallest runs until one wide merge can take
+    // every run (Sec. 4.3); each writes a new run into the merge arena
+    // rows all preliminary merges may write: replay the schedule with each
+    // merged run as large as its inputs (an upper bound)
+    long long need = 0;
+    int extra = 0;
+    {
+      std::vector<long long> sz;
+      for (auto& r : rr) sz.push_back(r.rows);
+      while ((int)sz.size() > cap) {
+        const int g = std::min<int>(cap, (int)sz.size() - cap + 1);
+        std::stable_sort(sz.begin(), sz.end());
+        long long m = 0;
+        for (int i = 0; i < g; ++i) m += sz[i];
+        sz.erase(sz.begin(), sz.begin() + g);
+        sz.push_back(m);
+        need += m;
+        ++extra;
       }
-      TRY(grow(h, h->gather_keys, (size_t)m * 8));
-      TRY(grow_cols(h, h->gather_cols, S, (size_t)m * 8));
-      std::vector<long long*> gcols(std::max(1, S));
-      for (int s = 0; s < S; ++s) gcols[s] = P<long long>(h->gather_cols[s]);
-      TRY(grow(h, h->gather_ptrs, (size_t)(std::max(1, S) + K + 1) * 8));
-      long long* dpre = P<long long>(h->gather_ptrs);
-      long long** dcols = reinterpret_cast<long long**>(dpre + K + 1);
-      CU(cudaMemcpy(dpre, pre.data(), (size_t)(K + 1) * 8, cudaMemcpyHostToDevice));
-      CU(cudaMemcpy(dcols, gcols.data(), (size_t)std::max(1, S) * 8, cudaMemcpyHostToDevice));
-      dim3 grid(std::max(1, std::min(64, (int)((m / K + 255) / 256))), K);
-      kbegin(h, SGAGG_K_OTHER);
-      k_gather_runs<<<grid, 256, 0, stream>>>(rset, bch[i].f_lo, bch[i].f_hi, dpre,
-                                              P<unsigned long long>(h->gather_keys), dcols);
-      kend(h);
-      kbytes(h, SGAGG_K_OTHER, m * 16ll * (1 + S));
-      RowSrc gs{};
-      gs.kind = SRC_SOA;
-      gs.ncols = S;
-      gs.keys = P<unsigned long long>(h->gather_keys);
-      for (int s = 0; s < S; ++s) gs.cols[s] = gcols[s];
-      long long* tdev = &ds->dtot[kMaxDepth + 1];
-      hs->v[0] = at;
-      CU(cudaMemcpyAsync(tdev, &hs->v[0], 8, cudaMemcpyHostToDevice, stream));
-      CU(cudaStreamSynchronize(stream));
-      TRY(solve(h, gs, m, fid, co, tdev, tdev, nullptr, 1));
-      ++h->st.split_segments;
-      TRY(sync_read(h, &hs->v[1], tdev, 8));
-      TRY(check_device_err(h));
-      long long end = hs->v[1];
-      bch[i].lo = at;
-      bch[i].hi = end;
-      at = end;
-      CU(cudaMemcpy(P<Chunk>(h->chunks[0]) + big[i], &bch[i], sizeof(Chunk), cudaMemcpyHostToDevice));
     }
-    copy.keys = co.keys;
-    for (int s = 0; s < S; ++s) copy.cols[s] = co.cols[s];
+    TRY(grow(h, h->marena_keys, (size_t)std::max(1ll, need) * 8));
+    TRY(grow_cols(h, h->marena_cols, S, (size_t)std::max(1ll, need) * 8));
+    TRY(grow(h, h->moffs, (size_t)extra * stride * 8));
+    long long used = 0;
+    int made = 0;
+    while ((int)rr.size() > cap) {
+      const int g = std::min<int>(cap, (int)rr.size() - cap + 1);
+      std::stable_sort(rr.begin(), rr.end(), [](const RunRef& x, const RunRef& y) { return x.rows < y.rows; });
+      std::vector<RunRef> part(rr.begin(), rr.begin() + g);
+      OutSink o{};
+      o.user = 0;
+      o.keys = P<unsigned long long>(h->marena_keys);
+      for (int s = 0; s < S; ++s) o.cols[s] = P<long long>(h->marena_cols[s]);
+      o.capacity = need;
+      o.offs = P<long long>(h->moffs) + (long long)made * stride;
+      o.dig = gd;
+      long long* slot = &ds->dtot[kMaxDepth];
+      hs->v[0] = used;
+      CU(cudaMemcpyAsync(slot, &hs->v[0], 8, cudaMemcpyHostToDevice, stream));
+      long long end = 0;
+      TRY(merge_runs(h, part, S, fid, nf, o, slot, slot, &end, false));
+      RunRef nr;
+      nr.keys = P<long long>(h->marena_keys);
+      for (int s = 0; s < S; ++s) nr.cols[s] = P<long long>(h->marena_cols[s]);
+      nr.offs = o.offs;
+      nr.rows = end - used;
+      used = end;
+      ++made;
+      h->st.run_rows += nr.rows;
+      h->st.run_bytes_device += nr.rows * row_bytes;
+      ++h->st.runs;
+      rr.erase(rr.begin(), rr.begin() + g);
+      rr.push_back(nr);
+    }
   }
-  RowSrc nosrc{};
-  nosrc.ncols = 0;
-  long long* tot = &ds->total;
-  TRY(launch_sortfold<MODE_RUNS>(h, SGAGG_K_MERGE, P<Chunk>(h->chunks[0]), info.n_chunks, 0, nosrc, rset, copy,
-                                 fid, user, nullptr, tot));
-  TRY(sync_read(h, &hs->v[0], tot, 8));
-  TRY(check_device_err(h));
-  h->last_rows = hs->v[0];
-  h->st.out_rows = h->last_rows;
-  kbytes(h, SGAGG_K_MERGE, h->st.run_rows * row_bytes + h->last_rows * (h->key_bytes + 8ll * S));
+  long long rows = 0;
+  TRY(merge_runs(h, rr, S, fid, nf, user, nullptr, &ds->total, &rows, true));
+  h->last_rows = rows;
+  h->st.out_rows = rows;
   return SGAGG_OK;
 }
 
@@ -1153,6 +1264,7 @@ void sgagg_destroy(sgagg_t h) {
   free_buf(h->status); free_buf(h->small); free_buf(h->sample); free_buf(h->arena_keys); fv(h->arena_cols);
   free_buf(h->offs); free_buf(h->runptrs); free_buf(h->fsizes); free_buf(h->gather_keys); fv(h->gather_cols);
   free_buf(h->gather_ptrs); free_buf(h->runstarts);
+  free_buf(h->marena_keys); fv(h->marena_cols); free_buf(h->moffs);
   for (auto& b : h->in_keys) free_buf(b);
   fv(h->in_pay);
   for (auto& b : h->out_keys) free_buf(b);

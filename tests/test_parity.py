@@ -79,9 +79,11 @@ def test_budget_boundaries(M):
 
 
 def test_budget_one_row():
+    """300 one-row runs exceed one merge's fan-in (256): one preliminary merge
+    of the 45 smallest runs writes one more run (counted in the spill)."""
     kc, pay = u64_case("c1", 300)
     st, _ = check(kc, pay, AGG4, M=1)
-    assert st["runs"] == 300 and st["run_rows"] == 300
+    assert st["batches"] == 300 and st["runs"] == 301 and st["run_rows"] == 300 + 45
 
 
 def test_budget_not_dividing_n():
@@ -225,3 +227,12 @@ def test_handle_reuse_across_shapes():
                 np.testing.assert_array_equal(to_np(oa[a]), ra[a])
     finally:
         agg.close()
+
+
+@pytest.mark.parametrize("cap", [2, 3, 7])
+def test_preliminary_merges(cap):
+    """More runs than one wide merge may take: the smallest runs are merged
+    first (Sec. 4.3) until the final merge takes them all."""
+    c = datagen.config1(n=60_000, seed=13, D=9000)
+    st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=1000, fanin_cap=cap)
+    assert st["runs"] > 60
