@@ -497,7 +497,8 @@ k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int nti
   unsigned* cursor = reinterpret_cast<unsigned*>(st_raw);
   unsigned* lst = cursor + nb;
   const int C = src.ncols;
-  unsigned long long* skey = reinterpret_cast<unsigned long long*>(lst + nb + (nb & 1));
+  // header (cursor, lst) padded to 16 bytes so the 8-byte stage stays aligned
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(st_raw + (((size_t)2 * nb * 4 + 15) & ~(size_t)15));
   long long* scol = reinterpret_cast<long long*>(skey + kStage);
   uint16_t* sperm = reinterpret_cast<uint16_t*>(scol + (long long)C * kStage);
   const int t = blockIdx.x;
@@ -519,14 +520,47 @@ k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int nti
     for (int d = threadIdx.x; d < nb; d += blockDim.x) lst[d] = 0;
     __syncthreads();
     unsigned dr[U];  // digit << 16 | rank
+    unsigned long long kk[U];
+    // all loads of the sub-tile first (independent, in flight together) ...
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = threadIdx.x + u * kPartThreads;
+      if (i < m) kk[u] = src_key(src, s0 + i);
+    }
+    if (C == 1) {
+      long long cv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = threadIdx.x + u * kPartThreads;
+        if (i < m) cv[u] = src_col(src, 0, s0 + i);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = threadIdx.x + u * kPartThreads;
+        if (i < m) scol[i] = cv[u];
+      }
+    } else {
+      for (int c = 0; c < C; ++c) {
+        long long cv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = threadIdx.x + u * kPartThreads;
+          if (i < m) cv[u] = src_col(src, c, s0 + i);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = threadIdx.x + u * kPartThreads;
+          if (i < m) scol[c * kStage + i] = cv[u];
+        }
+      }
+    }
+    // ... then the stage writes and the per-digit ranks
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = threadIdx.x + u * kPartThreads;
       if (i < m) {
-        unsigned long long k = src_key(src, s0 + i);
-        skey[i] = k;
-        for (int c = 0; c < C; ++c) scol[c * kStage + i] = src_col(src, c, s0 + i);
-        unsigned d = level_digit(dig, k, dsh, nb);
+        skey[i] = kk[u];
+        unsigned d = level_digit(dig, kk[u], dsh, nb);
         unsigned r = atomicAdd(&lst[d], 1u);
         dr[u] = (d << 16) | r;
       }
@@ -581,7 +615,7 @@ k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int nti
 }
 
 inline size_t staged_smem_bytes(int nb, int ncols) {
-  return (size_t)(2 * nb + (nb & 1)) * 4 + (size_t)kStage * 8 * (1 + ncols) + (size_t)kStage * 2 + 16;
+  return (((size_t)2 * nb * 4 + 15) & ~(size_t)15) + (size_t)kStage * 8 * (1 + ncols) + (size_t)kStage * 2 + 16;
 }
 
 }  // namespace sg

@@ -406,20 +406,24 @@ __device__ int chunk_sort(const SortSmem& s, int n) {
   __syncthreads();
   if (sh == 0) return maxbin <= 32 ? FOLD_BINS : FOLD_WARPS;  // every bin is one key value
   if (maxbin <= 32) {
-    for (int b = threadIdx.x; b < kBins; b += kThreads) {
-      int st = (int)bin_get(s.bins, b);
-      int en = (b + 1 < kBins) ? (int)bin_get(s.bins, b + 1) : n;
-      for (int i = st + 1; i < en; ++i) {
-        uint16_t v = s.idx[i];
-        unsigned long long kv = s.keys[v];
-        int j = i - 1;
-        while (j >= st && s.keys[s.idx[j]] > kv) {
-          s.idx[j + 1] = s.idx[j];
-          --j;
-        }
-        s.idx[j + 1] = v;
+    // finish each bin by ranking: an element's place in its bin is the number
+    // of bin members with a smaller key (ties broken by position), so every
+    // position is handled by its own lane and the loop runs over one bin
+    for (int p = threadIdx.x; p < n; p += kThreads) {
+      const int i = s.idx[p];
+      const unsigned long long k = s.keys[i];
+      const int b = (int)((k - kmin) >> sh);
+      const int st = (int)bin_get(s.bins, b);
+      const int en = (b + 1 < kBins) ? (int)bin_get(s.bins, b + 1) : n;
+      int r = st;
+      for (int q = st; q < en; ++q) {
+        const unsigned long long kq = s.keys[s.idx[q]];
+        r += (kq < k) || (kq == k && q < p);
       }
+      s.aux[r] = (uint16_t)i;
     }
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += kThreads) s.idx[p] = s.aux[p];
     __syncthreads();
     return FOLD_BINS;
   }
@@ -477,6 +481,49 @@ __device__ __forceinline__ long long chunk_base(const LookBack& lb, const OutSin
 // ---------------------------------------------------------------------------
 __shared__ int g_lcnt[kWarps + 1];
 
+// Stage source column c of every chunk row (chunk order) into dst: one
+// coalesced pass with kU loads in flight per thread.
+template <int MODE>
+__device__ __forceinline__ void stage_column(const SortSmem& s, const RowSrc& src, const RunSet& runs,
+                                             const ChunkView& cv, int c, long long* dst) {
+  constexpr int U = 8;
+  for (int base = threadIdx.x; base < cv.n; base += U * kThreads) {
+    long long v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * kThreads;
+      if (i < cv.n) {
+        if (MODE == MODE_RUNS) {
+          const int r = run_of(s, cv.k, i);
+          v[u] = __ldg(runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c] + s.slo[r] + (i - s.spre[r]));
+        } else if (MODE == MODE_RANGE) {
+          v[u] = src.aos[(cv.lo + i) * (1 + src.ncols) + 1 + c];
+        } else {
+          v[u] = src_col(src, c, cv.lo + i);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * kThreads;
+      if (i < cv.n) dst[i] = v[u];
+    }
+  }
+}
+
+__device__ __forceinline__ bool head_bit(const uint32_t* hm, int p) { return (hm[p >> 5] >> (p & 31)) & 1u; }
+
+// End (exclusive) of the key group starting at head position p.
+__device__ __forceinline__ int group_end(const uint32_t* hm, int p, int n) {
+  int q = p + 1;
+  while (q < n) {
+    const uint32_t w = hm[q >> 5] >> (q & 31);
+    if (w) return q + __ffs(w) - 1;
+    q = (q | 31) + 1;
+  }
+  return n;
+}
+
 template <int MODE, int KS>
 __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& runs, const ChunkView& cv,
                            const FoldDesc& fd, const OutSink& out, const LookBack& lb, const Chunk& ch,
@@ -486,12 +533,16 @@ __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& r
   const unsigned lt = (1u << lane) - 1;
   const int Q = ((n + kWarps - 1) / kWarps + 31) & ~31;
   const int wb = min(n, w * Q), we = min(n, wb + Q);
+  uint32_t* hm = s.bins;  // head bitmask (the bins are done with)
+  // pass 1: heads -> bitmask, per-warp counts (warp ranges are 32-aligned)
   int hc = 0;
   for (int b = wb; b < we; b += 32) {
     const int p = b + lane;
     bool h = false;
     if (p < we) h = (p == 0) || s.keys[s.idx[p]] != s.keys[s.idx[p - 1]];
-    hc += __popc(__ballot_sync(0xffffffffu, h));
+    const unsigned hb = __ballot_sync(0xffffffffu, h);
+    if (lane == 0) hm[b >> 5] = hb;
+    hc += __popc(hb);
   }
   if (lane == 0) g_lcnt[w] = hc;
   __syncthreads();
@@ -510,49 +561,58 @@ __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& r
   if (base < 0) return;
   if (out.offs && count == 0 && threadIdx.x == 0)
     for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
-  int opv[KS], srv[KS];
-#pragma unroll
-  for (int a = 0; a < KS; ++a) {
-    opv[a] = a < fd.n_state ? fd.op[a] : OP_SUM;
-    srv[a] = a < fd.n_state ? fd.src[a] : -1;
+  // keys (and the run's sparse index)
+  {
+    int run = g_lcnt[w];
+    for (int b = wb; b < we; b += 32) {
+      const int p = b + lane;
+      const unsigned hb = hm[b >> 5];
+      if ((hb >> lane) & 1u) {
+        const long long g = run + __popc(hb & lt);
+        const unsigned long long key = s.keys[s.idx[p]];
+        sink_key(out, base + g, key);
+        if (out.offs) write_fine_offsets(out, ch, base, g, count, key, p > 0, p > 0 ? s.keys[s.idx[p - 1]] : 0ull);
+      }
+      run += __popc(hb);
+    }
   }
+  // aggregates, one source column at a time, staged where the keys were
+  long long* col = reinterpret_cast<long long*>(s.keys);
   const int ns = fd.n_state;
-  int run = g_lcnt[w];
-  for (int b = wb; b < we; b += 32) {
-    const int p = b + lane;
-    unsigned long long key = 0, prev = 0;
-    bool h = false;
-    if (p < we) {
-      key = s.keys[s.idx[p]];
-      if (p > 0) prev = s.keys[s.idx[p - 1]];
-      h = (p == 0) || key != prev;
+  const int ncols = (MODE == MODE_RUNS) ? runs.ncols : src.ncols;
+  for (int c = -1; c < ncols; ++c) {
+    bool used = false;
+    for (int a = 0; a < ns; ++a) used |= (fd.src[a] == c);
+    if (!used) continue;
+    if (c >= 0) {
+      __syncthreads();  // everyone is done with the previous contents
+      stage_column<MODE>(s, src, runs, cv, c, col);
+      __syncthreads();
     }
-    const unsigned hb = __ballot_sync(0xffffffffu, h);
-    if (h) {
-      const long long g = run + __popc(hb & lt);
-      const long long pos = base + g;
-      long long acc[KS];
-      {
-        RowAt ra = row_at<MODE>(s, src, cv, s.idx[p]);
+    int run = g_lcnt[w];
+    for (int b = wb; b < we; b += 32) {
+      const int p = b + lane;
+      const unsigned hb = hm[b >> 5];
+      if ((hb >> lane) & 1u) {
+        const long long pos = base + run + __popc(hb & lt);
+        const int e = group_end(hm, p, n);
 #pragma unroll
-        for (int a = 0; a < KS; ++a)
-          if (a < ns) acc[a] = col_at<MODE>(src, runs, ra, srv[a]);
+        for (int a = 0; a < KS; ++a) {
+          if (a < ns && fd.src[a] == c) {
+            const int op = fd.op[a];
+            long long acc;
+            if (c < 0) {
+              acc = op == OP_SUM ? (long long)(e - p) : 1;  // count(*) of raw rows
+            } else {
+              acc = col[s.idx[p]];
+              for (int q = p + 1; q < e; ++q) acc = op_combine(op, acc, col[s.idx[q]]);
+            }
+            sink_val(out, a, pos, acc);
+          }
+        }
       }
-      for (int q = p + 1; q < n; ++q) {
-        const int i = s.idx[q];
-        if (s.keys[i] != key) break;
-        RowAt ra = row_at<MODE>(s, src, cv, i);
-#pragma unroll
-        for (int a = 0; a < KS; ++a)
-          if (a < ns) acc[a] = op_combine(opv[a], acc[a], col_at<MODE>(src, runs, ra, srv[a]));
-      }
-      sink_key(out, pos, key);
-      if (out.offs) write_fine_offsets(out, ch, base, g, count, key, p > 0, prev);
-#pragma unroll
-      for (int a = 0; a < KS; ++a)
-        if (a < ns) sink_val(out, a, pos, acc[a]);
+      run += __popc(hb);
     }
-    run += __popc(hb);
   }
 }
 
