@@ -221,11 +221,44 @@ typedef struct {
 sgagg_status sgagg_aggregate_batched(sgagg_t h, const sgagg_instance *inst, int32_t count,
                                      const sgagg_spec *spec, void *stream);
 
+/*
+ * Group at most SGAGG_NOALLOC_MAX_ROWS rows without allocating any memory.
+ * The paper has no counterpart; this exists for callers that cannot allocate
+ * device memory at all, e.g. code running inside a memory pool or allocator
+ * callback, or a process whose allocations are reserved by a framework up
+ * front: this call makes no cudaMalloc/cudaFree and no allocating library
+ * call, and needs no handle.
+ *
+ * Same arguments as sgagg_aggregate except that there is no handle and
+ * out_rows is a DEVICE pointer to one int64 that receives the number of
+ * output rows, or -1 when out_capacity was too small (nothing past
+ * out_capacity is written).  Asynchronous on `stream`.
+ *
+ * Scratch: a fixed 256-byte array in the library's device memory
+ * (SGAGG_NOALLOC_SCRATCH_BYTES), held by every GPU that loads the library
+ * until the process exits.  Every call shares it and overwrites it, so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race:
+ * serialize them.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.
+ *
+ * Errors: n > SGAGG_NOALLOC_MAX_ROWS, or any argument error of
+ * sgagg_aggregate, returns SGAGG_EINVAL before any GPU work;
+ * sgagg_last_error(NULL) then gives the message.
+ */
+#define SGAGG_NOALLOC_MAX_ROWS 8192
+#define SGAGG_NOALLOC_SCRATCH_BYTES 256
+sgagg_status sgagg_aggregate_noalloc(const sgagg_keys *keys, const int64_t *const *payload_cols,
+                                     int32_t n_payload, int64_t n, const sgagg_spec *spec,
+                                     void *const *out_keys, int64_t *const *out_aggs,
+                                     int64_t out_capacity, int64_t *out_rows, void *stream);
+
 /* Free the handle and everything it owns.  NULL is ignored. */
 void sgagg_destroy(sgagg_t h);
 
 /* Message of the last error on this handle ("" if none).  Valid until the
- * next call on the handle. */
+ * next call on the handle.  With h == NULL: the last message of
+ * sgagg_aggregate_noalloc on this host thread. */
 const char *sgagg_last_error(sgagg_t h);
 
 #ifdef __cplusplus

@@ -712,44 +712,57 @@ void build_keycols(const sgagg_keys* keys, KeyCols* kc, KeyOut* ko, void* const*
   }
 }
 
+// Argument checks shared by every entry point; *msg gets a static message.
+sgagg_status check_args(const sgagg_keys* keys, const int64_t* const* payload, int32_t n_payload, int64_t n,
+                        const sgagg_spec* spec, void* const* out_keys, int64_t* const* out_aggs,
+                        int64_t out_capacity, const char** msg) {
+#define BAD(m) do { *msg = m; return SGAGG_EINVAL; } while (0)
+  if (!keys || !spec) BAD("null keys or spec");
+  if (n < 0) BAD("n < 0");
+  if (out_capacity < 0) BAD("out_capacity < 0");
+  if (keys->n_cols < 1 || keys->n_cols > kMaxKeyCols || !keys->bytes || !keys->cols)
+    BAD("bad key columns");
+  int bits = 0;
+  for (int c = 0; c < keys->n_cols; ++c) {
+    int b = keys->bytes[c];
+    if (b != 1 && b != 2 && b != 4 && b != 8) BAD("key column width must be 1, 2, 4 or 8 bytes");
+    bits += 8 * b;
+    if (n > 0 && !keys->cols[c]) BAD("null key column");
+  }
+  if (bits > 64) BAD("key columns wider than 64 bits");
+  if (spec->n_aggs < 0 || spec->n_aggs > kMaxCols || (spec->n_aggs > 0 && !spec->aggs))
+    BAD("bad aggregate spec");
+  if (n_payload < 0 || n_payload > 1024 || (n_payload > 0 && !payload))
+    BAD("bad payload columns");
+  for (int a = 0; a < spec->n_aggs; ++a) {
+    int op = spec->aggs[a].op;
+    if (op < SGAGG_COUNT || op > SGAGG_MAX) BAD("bad aggregate op");
+    if (op != SGAGG_COUNT) {
+      int c = spec->aggs[a].col;
+      if (c < 0 || c >= n_payload) BAD("aggregate column out of range");
+      if (n > 0 && !payload[c]) BAD("null payload column");
+    }
+  }
+  if (out_capacity > 0 || n > 0) {
+    if (!out_keys) BAD("null out_keys");
+    for (int c = 0; c < keys->n_cols; ++c)
+      if (!out_keys[c] && out_capacity > 0) BAD("null output key column");
+    if (spec->n_aggs > 0 && !out_aggs) BAD("null out_aggs");
+    for (int a = 0; a < spec->n_aggs; ++a)
+      if (!out_aggs[a] && out_capacity > 0) BAD("null output aggregate column");
+  }
+  *msg = "";
+  return SGAGG_OK;
+#undef BAD
+}
+
 sgagg_status validate(sgagg_t h, const sgagg_keys* keys, const int64_t* const* payload, int32_t n_payload,
                       int64_t n, const sgagg_spec* spec, void* const* out_keys, int64_t* const* out_aggs,
                       int64_t out_capacity) {
   if (!h) return SGAGG_EINVAL;
-  if (!keys || !spec) return fail(h, SGAGG_EINVAL, "null keys or spec");
-  if (n < 0) return fail(h, SGAGG_EINVAL, "n < 0");
-  if (out_capacity < 0) return fail(h, SGAGG_EINVAL, "out_capacity < 0");
-  if (keys->n_cols < 1 || keys->n_cols > kMaxKeyCols || !keys->bytes || !keys->cols)
-    return fail(h, SGAGG_EINVAL, "bad key columns");
-  int bits = 0;
-  for (int c = 0; c < keys->n_cols; ++c) {
-    int b = keys->bytes[c];
-    if (b != 1 && b != 2 && b != 4 && b != 8) return fail(h, SGAGG_EINVAL, "key column width must be 1, 2, 4 or 8 bytes");
-    bits += 8 * b;
-    if (n > 0 && !keys->cols[c]) return fail(h, SGAGG_EINVAL, "null key column");
-  }
-  if (bits > 64) return fail(h, SGAGG_EINVAL, "key columns wider than 64 bits");
-  if (spec->n_aggs < 0 || spec->n_aggs > kMaxCols || (spec->n_aggs > 0 && !spec->aggs))
-    return fail(h, SGAGG_EINVAL, "bad aggregate spec");
-  if (n_payload < 0 || n_payload > 1024 || (n_payload > 0 && !payload))
-    return fail(h, SGAGG_EINVAL, "bad payload columns");
-  for (int a = 0; a < spec->n_aggs; ++a) {
-    int op = spec->aggs[a].op;
-    if (op < SGAGG_COUNT || op > SGAGG_MAX) return fail(h, SGAGG_EINVAL, "bad aggregate op");
-    if (op != SGAGG_COUNT) {
-      int c = spec->aggs[a].col;
-      if (c < 0 || c >= n_payload) return fail(h, SGAGG_EINVAL, "aggregate column out of range");
-      if (n > 0 && !payload[c]) return fail(h, SGAGG_EINVAL, "null payload column");
-    }
-  }
-  if (out_capacity > 0 || n > 0) {
-    if (!out_keys) return fail(h, SGAGG_EINVAL, "null out_keys");
-    for (int c = 0; c < keys->n_cols; ++c)
-      if (!out_keys[c] && out_capacity > 0) return fail(h, SGAGG_EINVAL, "null output key column");
-    if (spec->n_aggs > 0 && !out_aggs) return fail(h, SGAGG_EINVAL, "null out_aggs");
-    for (int a = 0; a < spec->n_aggs; ++a)
-      if (!out_aggs[a] && out_capacity > 0) return fail(h, SGAGG_EINVAL, "null output aggregate column");
-  }
+  const char* msg = "";
+  sgagg_status st = check_args(keys, payload, n_payload, n, spec, out_keys, out_aggs, out_capacity, &msg);
+  if (st != SGAGG_OK) return fail(h, st, "%s", msg);
   return SGAGG_OK;
 }
 
@@ -1188,6 +1201,127 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
 }  // namespace
 
 // ===========================================================================
+// Grouping without allocation (sgagg_aggregate_noalloc).
+//
+// One chunk of at most kTileCap rows is sorted and folded by the same kernel
+// as every other chunk; its look-back status, ticket, error word and row
+// count live in this fixed array instead of handle-owned buffers.  Host code
+// must not pass the symbol itself to a kernel (on the host it names a
+// stand-in, not device memory): the device address is looked up once per
+// device with cudaGetSymbolAddress.
+// ===========================================================================
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SGAGG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// byte offsets inside g_noalloc_scratch
+constexpr int kNaTicket = 0, kNaStatus = 8, kNaErr = 16, kNaTotal = 24, kNaZeroBytes = 24;
+
+constexpr int kNaMaxDevices = 64;
+unsigned char* g_na_ptr[kNaMaxDevices];   // device address of the array, per device
+thread_local char g_na_msg[256];
+
+__global__ void k_noalloc_finish(const int* err, const long long* total, long long* out_rows) {
+  *out_rows = *err ? -1 : *total;
+}
+
+sgagg_status na_fail(sgagg_status st, const char* msg) {
+  snprintf(g_na_msg, sizeof g_na_msg, "%s", msg);
+  return st;
+}
+
+}  // namespace
+
+extern "C" sgagg_status sgagg_aggregate_noalloc(const sgagg_keys* keys, const int64_t* const* payload_cols,
+                                                int32_t n_payload, int64_t n, const sgagg_spec* spec,
+                                                void* const* out_keys, int64_t* const* out_aggs,
+                                                int64_t out_capacity, int64_t* out_rows, void* stream) {
+  g_na_msg[0] = 0;
+  if (n > SGAGG_NOALLOC_MAX_ROWS)
+    return na_fail(SGAGG_EINVAL, "sgagg_aggregate_noalloc: n exceeds SGAGG_NOALLOC_MAX_ROWS (8192)");
+  if (!out_rows) return na_fail(SGAGG_EINVAL, "sgagg_aggregate_noalloc: null out_rows");
+  const char* msg = "";
+  sgagg_status vs = check_args(keys, payload_cols, n_payload, n, spec, out_keys, out_aggs, out_capacity, &msg);
+  if (vs != SGAGG_OK) return na_fail(vs, msg);
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
+    return na_fail(SGAGG_ECUDA, "sgagg_aggregate_noalloc: no usable current device");
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return na_fail(SGAGG_ECUDA, cudaGetErrorString(e));
+    g_na_ptr[dev] = reinterpret_cast<unsigned char*>(p);
+  }
+  unsigned char* base = g_na_ptr[dev];
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // ticket, status word and error word must start at zero; the count is written
+  if (cudaMemsetAsync(base, 0, kNaZeroBytes, st) != cudaSuccess)
+    return na_fail(SGAGG_ECUDA, "sgagg_aggregate_noalloc: cudaMemsetAsync failed");
+  if (n == 0) {
+    if (cudaMemsetAsync(base + kNaTotal, 0, 8, st) != cudaSuccess)
+      return na_fail(SGAGG_ECUDA, "sgagg_aggregate_noalloc: cudaMemsetAsync failed");
+  } else {
+    RowSrc raw{};
+    raw.kind = SRC_RAW;
+    KeyOut kout{};
+    build_keycols(keys, &raw.key, &kout, out_keys);
+    FoldDesc fd{};
+    fd.n_state = spec->n_aggs;
+    int colmap[1024];
+    for (int c = 0; c < n_payload && c < 1024; ++c) colmap[c] = -1;
+    int C = 0;
+    for (int a = 0; a < spec->n_aggs; ++a) {
+      const int op = spec->aggs[a].op;
+      if (op == SGAGG_COUNT) {
+        fd.src[a] = -1;
+        fd.op[a] = OP_SUM;
+      } else {
+        const int c = spec->aggs[a].col;
+        if (colmap[c] < 0) {
+          if (C >= kMaxCols) return na_fail(SGAGG_EINVAL, "sgagg_aggregate_noalloc: too many payload columns");
+          colmap[c] = C;
+          raw.cols[C++] = reinterpret_cast<const long long*>(payload_cols[c]);
+        }
+        fd.src[a] = (int8_t)colmap[c];
+        fd.op[a] = op == SGAGG_SUM ? OP_SUM : (op == SGAGG_MIN ? OP_MIN : OP_MAX);
+      }
+    }
+    raw.ncols = C;
+    OutSink o{};
+    o.user = 1;
+    o.kout = kout;
+    for (int a = 0; a < spec->n_aggs; ++a) o.cols[a] = reinterpret_cast<long long*>(out_aggs[a]);
+    o.capacity = out_capacity;
+    LookBack lb{};
+    lb.ticket = reinterpret_cast<unsigned int*>(base + kNaTicket);
+    lb.status = reinterpret_cast<unsigned long long*>(base + kNaStatus);
+    lb.err = reinterpret_cast<int*>(base + kNaErr);
+    lb.total_out = reinterpret_cast<long long*>(base + kNaTotal);
+    lb.base_in = nullptr;
+    lb.spin_limit = 1ll << 26;
+    lb.n_chunks = 1;
+    RunSet norun{};
+    CopySrc nocopy{};
+    if (fd.n_state <= 2)
+      launch_ks<MODE_TILES, 2>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+    else if (fd.n_state <= 4)
+      launch_ks<MODE_TILES, 4>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+    else if (fd.n_state <= 8)
+      launch_ks<MODE_TILES, 8>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+    else if (fd.n_state <= 16)
+      launch_ks<MODE_TILES, 16>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+    else
+      launch_ks<MODE_TILES, 32>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+    if (cudaGetLastError() != cudaSuccess) return na_fail(SGAGG_ECUDA, "sgagg_aggregate_noalloc: launch failed");
+  }
+  k_noalloc_finish<<<1, 1, 0, st>>>(reinterpret_cast<const int*>(base + kNaErr),
+                                    reinterpret_cast<const long long*>(base + kNaTotal),
+                                    reinterpret_cast<long long*>(out_rows));
+  if (cudaGetLastError() != cudaSuccess) return na_fail(SGAGG_ECUDA, "sgagg_aggregate_noalloc: launch failed");
+  return SGAGG_OK;
+}
+
+// ===========================================================================
 // C ABI
 // ===========================================================================
 extern "C" {
@@ -1373,7 +1507,7 @@ void sgagg_destroy(sgagg_t h) {
 }
 
 const char* sgagg_last_error(sgagg_t h) {
-  if (!h) return "null handle";
+  if (!h) return g_na_msg;
   return h->err.c_str();
 }
 

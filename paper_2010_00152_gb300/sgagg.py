@@ -86,6 +86,9 @@ def lib():
         L.sgagg_stats.argtypes = [vp, ctypes.POINTER(sgagg_stats_t)]
         L.sgagg_aggregate_batched.argtypes = [vp, ctypes.POINTER(sgagg_instance), i32,
                                               ctypes.POINTER(sgagg_spec), vp]
+        L.sgagg_aggregate_noalloc.argtypes = [ctypes.POINTER(sgagg_keys), vp, i32, i64,
+                                              ctypes.POINTER(sgagg_spec), vp, vp, i64, vp, vp]
+        L.sgagg_aggregate_noalloc.restype = i32
         L.sgagg_destroy.argtypes = [vp]
         L.sgagg_destroy.restype = None
         L.sgagg_last_error.argtypes = [vp]
@@ -181,6 +184,22 @@ def sgagg_aggregate_host(h, key_ptrs, key_bytes, payload_ptrs, n, aggs, out_key_
                                     ctypes.byref(rows), ctypes.c_void_p(stream))
     _check(h, st)
     return int(rows.value)
+
+
+NOALLOC_MAX_ROWS = 8192
+
+
+def sgagg_aggregate_noalloc(key_ptrs, key_bytes, payload_ptrs, n, aggs, out_key_ptrs, out_agg_ptrs,
+                            out_capacity, out_rows_ptr, stream=0):
+    """Handle-free grouping of at most NOALLOC_MAX_ROWS rows that allocates no
+    memory (device pointers in and out; the row count lands in the device
+    int64 at out_rows_ptr, -1 if out_capacity was too small)."""
+    a = _Args(key_ptrs, key_bytes, payload_ptrs, aggs, out_key_ptrs, out_agg_ptrs)
+    st = lib().sgagg_aggregate_noalloc(ctypes.byref(a.keys), a.pay, len(payload_ptrs), int(n),
+                                       ctypes.byref(a.spec), a.ok, a.oa, int(out_capacity),
+                                       ctypes.c_void_p(out_rows_ptr), ctypes.c_void_p(stream))
+    if st != SGAGG_OK:
+        raise SgaggError(st, sgagg_last_error(None))
 
 
 def sgagg_aggregate_batched(h, instances, aggs, stream=0):
