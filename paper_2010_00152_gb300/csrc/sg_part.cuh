@@ -18,6 +18,7 @@
 namespace sg {
 
 constexpr int kPartThreads = 512;
+constexpr int kPrivBuckets = 256;   // per-warp private histograms up to this many buckets
 
 // Keys of `count` rows spread evenly over [0, n), for the planner's probe.
 __global__ void k_sample(RowSrc src, long long n, int count, unsigned long long* out) {
@@ -64,7 +65,12 @@ __device__ __forceinline__ unsigned level_digit(const Digit& dig, unsigned long 
 __global__ void __launch_bounds__(kPartThreads)
 k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsigned int* thist) {
   extern __shared__ unsigned int sh_hist[];
-  for (int d = threadIdx.x; d < nb; d += blockDim.x) sh_hist[d] = 0;
+  // up to 256 buckets: one private histogram per warp (no cross-warp atomic
+  // contention), summed at the end; more buckets: one shared histogram
+  const bool priv = nb <= kPrivBuckets;
+  unsigned* mine = priv ? sh_hist + (threadIdx.x >> 5) * nb : sh_hist;
+  const int nh = priv ? nb * (blockDim.x >> 5) : nb;
+  for (int d = threadIdx.x; d < nh; d += blockDim.x) sh_hist[d] = 0;
   __syncthreads();
   long long lo, hi;
   tile_range(n, ntiles, blockIdx.x, &lo, &hi);
@@ -79,11 +85,20 @@ k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsig
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       long long i = i0 + (long long)u * blockDim.x;
-      if (i < hi) atomicAdd(&sh_hist[level_digit(dig, k[u], dshift, nb)], 1u);
+      if (i < hi) atomicAdd(&mine[level_digit(dig, k[u], dshift, nb)], 1u);
     }
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < nb; d += blockDim.x) thist[(long long)d * ntiles + blockIdx.x] = sh_hist[d];
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) {
+    unsigned v = sh_hist[d];
+    if (priv)
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v += sh_hist[w * nb + d];
+    thist[(long long)d * ntiles + blockIdx.x] = v;
+  }
+}
+
+inline size_t hist_smem_bytes(int nb, int threads) {
+  return (size_t)(nb <= 256 ? nb * (threads / 32) : nb) * 4;
 }
 
 // One warp per bucket: exclusive scan of thist over tiles (in place), total.
@@ -439,7 +454,10 @@ k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, u
   extern __shared__ unsigned sh2[];
   const int t = blockIdx.x;
   if (t >= *ntiles) return;
-  for (int d = threadIdx.x; d < nb2; d += blockDim.x) sh2[d] = 0;
+  const bool priv = nb2 <= kPrivBuckets;
+  unsigned* mine = priv ? sh2 + (threadIdx.x >> 5) * nb2 : sh2;
+  const int nh = priv ? nb2 * (blockDim.x >> 5) : nb2;
+  for (int d = threadIdx.x; d < nh; d += blockDim.x) sh2[d] = 0;
   __syncthreads();
   const Tile2 tl = tiles[t];
   constexpr int U = 8;
@@ -453,11 +471,16 @@ k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, u
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       long long i = i0 + (long long)u * blockDim.x;
-      if (i < tl.hi) atomicAdd(&sh2[level_digit(dig, k[u], 0, nb2)], 1u);
+      if (i < tl.hi) atomicAdd(&mine[level_digit(dig, k[u], 0, nb2)], 1u);
     }
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < nb2; d += blockDim.x) thist2[(long long)t * nb2 + d] = sh2[d];
+  for (int d = threadIdx.x; d < nb2; d += blockDim.x) {
+    unsigned v = sh2[d];
+    if (priv)
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v += sh2[w * nb2 + d];
+    thist2[(long long)t * nb2 + d] = v;
+  }
 }
 
 // One CTA per level-1 bucket: turns the bucket's tile histograms into absolute

@@ -27,9 +27,9 @@ namespace sg {
 constexpr int kTileCap = 8192;             // rows per chunk
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kBinBits = 12;
+constexpr int kBinBits = 13;
 constexpr int kBins = 1 << kBinBits;
-constexpr int kBinsPerThread = kBins / kThreads;  // 8
+constexpr int kBinsPerThread = kBins / kThreads;  // 16
 constexpr int kMaxFanIn = 256;             // runs one merge chunk can read
 constexpr int kFewGroups = 16;             // CTA-per-group fold below this many keys
 constexpr int kAccBlock = 8;               // state columns folded per pass
@@ -73,22 +73,24 @@ struct OutSink {
 struct SortSmem {
   unsigned long long* keys;   // [kTileCap]
   uint16_t* idx;              // [kTileCap] sorted permutation
-  uint16_t* aux;              // [kTileCap] LSD ping-pong, then per-bin distinct prefix
-  uint32_t* bins;             // [kBins / 2] packed 16-bit bin starts / LSD warp histograms
+  uint32_t* bins;             // [kBins / 2] packed 16-bit bin starts; LSD ping-pong buffer;
+                              // then the head bitmask and its word prefix
+  uint16_t* whist;            // [kWarps * 256] LSD per-warp digit counts
   long long* slo;             // [kMaxFanIn] merge: slice start per run
   long long* spre;            // [kMaxFanIn + 1] merge: slice prefix
 };
 
 constexpr size_t kSortSmemBytes =
-    kTileCap * 8 + kTileCap * 2 * 2 + (kBins / 2) * 4 + kMaxFanIn * 8 + (kMaxFanIn + 1) * 8 + 64;
+    kTileCap * 8 + kTileCap * 2 + (kBins / 2) * 4 + kWarps * 256 * 2 + kMaxFanIn * 8 + (kMaxFanIn + 1) * 8 + 64;
+static_assert(kBins >= kTileCap, "the LSD ping-pong buffer lives in the bins area");
 
 __device__ __forceinline__ SortSmem carve(unsigned char* base) {
   SortSmem s;
   s.keys = reinterpret_cast<unsigned long long*>(base);
   s.idx = reinterpret_cast<uint16_t*>(base + kTileCap * 8);
-  s.aux = reinterpret_cast<uint16_t*>(base + kTileCap * 10);
-  s.bins = reinterpret_cast<uint32_t*>(base + kTileCap * 12);
-  s.slo = reinterpret_cast<long long*>(base + kTileCap * 12 + (kBins / 2) * 4);
+  s.bins = reinterpret_cast<uint32_t*>(base + kTileCap * 10);
+  s.whist = reinterpret_cast<uint16_t*>(base + kTileCap * 10 + (kBins / 2) * 4);
+  s.slo = reinterpret_cast<long long*>(base + kTileCap * 10 + (kBins / 2) * 4 + kWarps * 256 * 2);
   s.spre = s.slo + kMaxFanIn;
   return s;
 }
@@ -243,10 +245,17 @@ __device__ __forceinline__ long long col_at(const RowSrc& src, const RunSet& run
   return src_col(src, c, a.off);
 }
 
+// Advance a run cursor r (MODE_RUNS) to the run holding position i >= its start.
+__device__ __forceinline__ int run_advance(const SortSmem& s, int k, int r, int i) {
+  while (r + 1 < k && s.spre[r + 1] <= i) ++r;
+  return r;
+}
+
 template <int MODE>
 __device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, const RunSet& runs,
                                           const ChunkView& cv) {
   constexpr int U = 8;  // loads in flight per thread
+  int r = 0;            // a thread's positions only grow: the run cursor only advances
   for (int base = threadIdx.x; base < cv.n; base += U * kThreads) {
     unsigned long long v[U];
 #pragma unroll
@@ -254,7 +263,7 @@ __device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, 
       int i = base + u * kThreads;
       if (i < cv.n) {
         if (MODE == MODE_RUNS) {
-          int r = run_of(s, cv.k, i);
+          r = run_advance(s, cv.k, r, i);
           const long long* p = runs.ptrs[(long long)r * (1 + runs.ncols)];
           v[u] = (unsigned long long)__ldg(p + s.slo[r] + (i - s.spre[r]));
         } else {
@@ -284,9 +293,9 @@ __device__ void lsd_sort(const SortSmem& s, int n, unsigned long long kmin, int 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int EPT = kTileCap / kThreads;
   uint16_t* in = s.idx;
-  uint16_t* out = s.aux;
+  uint16_t* out = reinterpret_cast<uint16_t*>(s.bins);  // ping-pong in the bins area
   for (int i = threadIdx.x; i < n; i += kThreads) in[i] = (uint16_t)i;
-  uint16_t* whist = reinterpret_cast<uint16_t*>(s.bins);  // [kWarps][256]
+  uint16_t* whist = s.whist;  // [kWarps][256]
   const unsigned lt = (1u << lane) - 1;
   for (int p = 0; p < vb; p += 8) {
     for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) whist[i] = 0;
@@ -371,12 +380,19 @@ __device__ int chunk_sort(const SortSmem& s, int n) {
   const int sh = vb > kBinBits ? vb - kBinBits : 0;
   for (int i = threadIdx.x; i < kBins / 2; i += kThreads) s.bins[i] = 0;
   __syncthreads();
-  // counting sort on the top bits: rank inside the bin from the atomic
-  for (int i = threadIdx.x; i < n; i += kThreads) {
-    int b = (int)((s.keys[i] - kmin) >> sh);
-    unsigned sft = (b & 1) * 16;
-    unsigned old = atomicAdd(&s.bins[b >> 1], 1u << sft);
-    s.aux[i] = (uint16_t)((old >> sft) & 0xFFFFu);
+  // counting sort on the top bits: rank inside the bin from the atomic, kept
+  // in registers (a thread's rows are i = threadIdx.x + j * kThreads)
+  constexpr int EPT = kTileCap / kThreads;
+  uint32_t br[EPT];  // bin << 16 | rank in bin
+#pragma unroll
+  for (int j = 0; j < EPT; ++j) {
+    const int i = threadIdx.x + j * kThreads;
+    if (i < n) {
+      const int b = (int)((s.keys[i] - kmin) >> sh);
+      const unsigned sft = (b & 1) * 16;
+      const unsigned old = atomicAdd(&s.bins[b >> 1], 1u << sft);
+      br[j] = ((unsigned)b << 16) | ((old >> sft) & 0xFFFFu);
+    }
   }
   __syncthreads();
   int cnt[kBinsPerThread];
@@ -399,31 +415,33 @@ __device__ int chunk_sort(const SortSmem& s, int n) {
     s.bins[(threadIdx.x * kBinsPerThread + q) >> 1] = lo | (hi << 16);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += kThreads) {
-    int b = (int)((s.keys[i] - kmin) >> sh);
-    s.idx[bin_get(s.bins, b) + s.aux[i]] = (uint16_t)i;
+  // place
+#pragma unroll
+  for (int j = 0; j < EPT; ++j) {
+    const int i = threadIdx.x + j * kThreads;
+    if (i < n) s.idx[(int)bin_get(s.bins, (int)(br[j] >> 16)) + (int)(br[j] & 0xFFFFu)] = (uint16_t)i;
   }
   __syncthreads();
   if (sh == 0) return maxbin <= 32 ? FOLD_BINS : FOLD_WARPS;  // every bin is one key value
   if (maxbin <= 32) {
-    // finish each bin by ranking: an element's place in its bin is the number
-    // of bin members with a smaller key (ties broken by position), so every
-    // position is handled by its own lane and the loop runs over one bin
-    for (int p = threadIdx.x; p < n; p += kThreads) {
-      const int i = s.idx[p];
-      const unsigned long long k = s.keys[i];
-      const int b = (int)((k - kmin) >> sh);
+    // with about one row per bin, only the few bins holding two or more rows
+    // need work: insertion sort in place, a thread per bin
+    for (int b = threadIdx.x; b < kBins; b += kThreads) {
       const int st = (int)bin_get(s.bins, b);
       const int en = (b + 1 < kBins) ? (int)bin_get(s.bins, b + 1) : n;
-      int r = st;
-      for (int q = st; q < en; ++q) {
-        const unsigned long long kq = s.keys[s.idx[q]];
-        r += (kq < k) || (kq == k && q < p);
+      for (int i = st + 1; i < en; ++i) {
+        const uint16_t v = s.idx[i];
+        const unsigned long long kv = s.keys[v];
+        int j = i - 1;
+        while (j >= st) {
+          const uint16_t u = s.idx[j];
+          if (s.keys[u] <= kv) break;
+          s.idx[j + 1] = u;
+          --j;
+        }
+        s.idx[j + 1] = v;
       }
-      s.aux[r] = (uint16_t)i;
     }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += kThreads) s.idx[p] = s.aux[p];
     __syncthreads();
     return FOLD_BINS;
   }
@@ -487,6 +505,7 @@ template <int MODE>
 __device__ __forceinline__ void stage_column(const SortSmem& s, const RowSrc& src, const RunSet& runs,
                                              const ChunkView& cv, int c, long long* dst) {
   constexpr int U = 8;
+  int r = 0;
   for (int base = threadIdx.x; base < cv.n; base += U * kThreads) {
     long long v[U];
 #pragma unroll
@@ -494,7 +513,7 @@ __device__ __forceinline__ void stage_column(const SortSmem& s, const RowSrc& sr
       const int i = base + u * kThreads;
       if (i < cv.n) {
         if (MODE == MODE_RUNS) {
-          const int r = run_of(s, cv.k, i);
+          r = run_advance(s, cv.k, r, i);
           v[u] = __ldg(runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c] + s.slo[r] + (i - s.spre[r]));
         } else if (MODE == MODE_RANGE) {
           v[u] = src.aos[(cv.lo + i) * (1 + src.ncols) + 1 + c];
@@ -535,13 +554,17 @@ __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& r
   const int wb = min(n, w * Q), we = min(n, wb + Q);
   uint32_t* hm = s.bins;  // head bitmask (the bins are done with)
   // pass 1: heads -> bitmask, per-warp counts (warp ranges are 32-aligned)
+  uint16_t* hpre = reinterpret_cast<uint16_t*>(s.bins + kTileCap / 32);  // heads before each word
   int hc = 0;
   for (int b = wb; b < we; b += 32) {
     const int p = b + lane;
     bool h = false;
     if (p < we) h = (p == 0) || s.keys[s.idx[p]] != s.keys[s.idx[p - 1]];
     const unsigned hb = __ballot_sync(0xffffffffu, h);
-    if (lane == 0) hm[b >> 5] = hb;
+    if (lane == 0) {
+      hm[b >> 5] = hb;
+      hpre[b >> 5] = (uint16_t)hc;  // warp-local; the warp's prefix is added below
+    }
     hc += __popc(hb);
   }
   if (lane == 0) g_lcnt[w] = hc;
@@ -557,38 +580,54 @@ __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& r
   }
   __syncthreads();
   const int count = g_lcnt[kWarps];
+  for (int b = wb + 32 * lane; b < we; b += 32 * 32) hpre[b >> 5] += (uint16_t)g_lcnt[w];
   const long long base = chunk_base(lb, out, cid, count, s_base);
   if (base < 0) return;
-  if (out.offs && count == 0 && threadIdx.x == 0)
-    for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
-  // keys (and the run's sparse index)
+  const int ns = fd.n_state;
+  // keys and count(*) of raw rows (no column to stage)
   {
     int run = g_lcnt[w];
     for (int b = wb; b < we; b += 32) {
       const int p = b + lane;
       const unsigned hb = hm[b >> 5];
       if ((hb >> lane) & 1u) {
-        const long long g = run + __popc(hb & lt);
-        const unsigned long long key = s.keys[s.idx[p]];
-        sink_key(out, base + g, key);
-        if (out.offs) write_fine_offsets(out, ch, base, g, count, key, p > 0, p > 0 ? s.keys[s.idx[p - 1]] : 0ull);
+        const long long pos = base + run + __popc(hb & lt);
+        sink_key(out, pos, s.keys[s.idx[p]]);
+        int e = -1;
+#pragma unroll
+        for (int a = 0; a < KS; ++a)
+          if (a < ns && fd.src[a] < 0) {
+            if (e < 0) e = group_end(hm, p, n);
+            sink_val(out, a, pos, fd.op[a] == OP_SUM ? (long long)(e - p) : 1);
+          }
       }
       run += __popc(hb);
     }
   }
+  // the run's sparse index: offs[f] = rows of this run before the first key
+  // with fine digit >= f, for every fine bucket of the chunk's key range
+  if (out.offs) {
+    for (int f = ch.f_lo + (int)threadIdx.x; f <= ch.f_hi; f += kThreads) {
+      int lo = 0, hi = n;  // first sorted position whose fine digit is >= f
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)fine_digit(out.dig, s.keys[s.idx[mid]]) < f) lo = mid + 1; else hi = mid;
+      }
+      const int heads = lo >= n ? count
+                                : (int)hpre[lo >> 5] + __popc(hm[lo >> 5] & ((1u << (lo & 31)) - 1u));
+      out.offs[f] = base + heads;
+    }
+  }
   // aggregates, one source column at a time, staged where the keys were
   long long* col = reinterpret_cast<long long*>(s.keys);
-  const int ns = fd.n_state;
   const int ncols = (MODE == MODE_RUNS) ? runs.ncols : src.ncols;
-  for (int c = -1; c < ncols; ++c) {
+  for (int c = 0; c < ncols; ++c) {
     bool used = false;
     for (int a = 0; a < ns; ++a) used |= (fd.src[a] == c);
     if (!used) continue;
-    if (c >= 0) {
-      __syncthreads();  // everyone is done with the previous contents
-      stage_column<MODE>(s, src, runs, cv, c, col);
-      __syncthreads();
-    }
+    __syncthreads();  // everyone is done with the previous contents (keys, offsets)
+    stage_column<MODE>(s, src, runs, cv, c, col);
+    __syncthreads();
     int run = g_lcnt[w];
     for (int b = wb; b < we; b += 32) {
       const int p = b + lane;
@@ -600,13 +639,8 @@ __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& r
         for (int a = 0; a < KS; ++a) {
           if (a < ns && fd.src[a] == c) {
             const int op = fd.op[a];
-            long long acc;
-            if (c < 0) {
-              acc = op == OP_SUM ? (long long)(e - p) : 1;  // count(*) of raw rows
-            } else {
-              acc = col[s.idx[p]];
-              for (int q = p + 1; q < e; ++q) acc = op_combine(op, acc, col[s.idx[q]]);
-            }
+            long long acc = col[s.idx[p]];
+            for (int q = p + 1; q < e; ++q) acc = op_combine(op, acc, col[s.idx[q]]);
             sink_val(out, a, pos, acc);
           }
         }
