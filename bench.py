@@ -44,6 +44,9 @@ def load_peaks():
 
 
 WORKLOADS = {
+    "c4": dict(desc="batched: 4,096 independent instances, rows log-uniform 1K-4M, uint32 keys Zipf(1.1) "
+                    "over a per-instance domain log-uniform 16-1M, 1 int64 payload, count/sum/min/max",
+               n=4096),
     "c3": dict(desc="512M rows, uint64 keys uniform over 2^28 values, 1 int64 payload, count/sum, "
                     "memory budget 2^25 rows (16 runs + wide merge)",
                n=1 << 29, D=1 << 28, M=1 << 25),
@@ -202,6 +205,84 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(args, dev):
+    """Config 4: the batched call against the plain loop of one call per
+    instance over the same instances (both through the C ABI)."""
+    import torch
+    import datagen
+    from paper_2010_00152_gb300 import sgagg
+    count = args.instances or WORKLOADS["c4"]["n"]
+    specs = datagen.config4_instances(count=count, seed=1)
+    insts = [datagen.config4_instance(sp, device=dev) for sp in specs]
+    aggs = insts[0]["aggs"]
+    n_total = sum(sp["rows"] for sp in specs)
+    outs, descs, keep = [], [], []
+    rows_dev = torch.zeros(count, dtype=torch.int64, device=dev)
+    for i, c in enumerate(insts):
+        k, p = c["key_cols"][0], c["payload"][0]
+        n = k.numel()
+        ok = torch.empty(n, dtype=k.dtype, device=dev)
+        oa = [torch.empty(n, dtype=torch.int64, device=dev) for _ in aggs]
+        pp = torch.tensor([p.data_ptr()], dtype=torch.int64, device=dev)
+        op = torch.tensor([a.data_ptr() for a in oa], dtype=torch.int64, device=dev)
+        keep += [pp, op]
+        descs.append(sgagg.sgagg_instance(k.data_ptr(), 4, 1, pp.data_ptr(), n, ok.data_ptr(), op.data_ptr(), n,
+                                          rows_dev.data_ptr() + 8 * i))
+        outs.append((ok, oa))
+    torch.cuda.synchronize()
+    agg = sgagg.Aggregator(1 << 22, timing=1)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+
+    def batched():
+        sgagg.sgagg_aggregate_batched(agg.h, descs, aggs, s)
+        return agg.rows()
+
+    def plain():
+        r = 0
+        for i, c in enumerate(insts):
+            k, p = c["key_cols"][0], c["payload"][0]
+            ok, oa = outs[i]
+            sgagg.sgagg_aggregate(agg.h, [k.data_ptr()], [4], [p.data_ptr()], k.numel(), aggs, [ok.data_ptr()],
+                                  [a.data_ptr() for a in oa], k.numel(), s)
+            r += agg.rows()
+        return r
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, r
+
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    ms_b, rows_b = timed(batched, args.steps, args.warmup)
+    clk = clocks.stop()
+    st = agg.stats()
+    ms_p, rows_p = timed(plain, max(1, args.steps // 2), 1)
+    assert rows_b == rows_p, (rows_b, rows_p)
+    line = {"metric": "rows/s grouped (batched)", "value": n_total / (ms_b / 1e3), "unit": "rows/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOADS["c4"]["desc"], "instances": count, "rows": n_total},
+            "plain": {"value": n_total / (ms_p / 1e3), "ms_per_step": ms_p,
+                      "note": "one sgagg_aggregate call per instance, same instances"},
+            "speedup_vs_plain": ms_p / ms_b, "out_rows": rows_b, "clocks": clk,
+            "kernels": {k: v for k, v in st["kernels"].items() if v["launches"]},
+            "gpu_launches": st["kernel_launches"] * args.steps}
+    print(json.dumps(line))
+    agg.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,6 +294,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--instances", type=int, default=None, help="c4: instance count")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -232,6 +314,8 @@ def main():
     build.build()
 
     name = args.config
+    if name == "c4":
+        return bench_batched(args, dev)
     w = make_workload(name, dev, args.rows)
     n = int(w["key_cols"][0].numel())
     M = int(w["M"])

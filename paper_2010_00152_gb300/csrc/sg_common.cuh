@@ -76,6 +76,7 @@ struct RowSrc {
   int kind;
   int ncols;                        // columns carried (payload or state)
   int64_t offset;                   // added to every row index
+  unsigned long long key_or;        // SRC_RAW: OR-ed into every key (instance id of a batch)
   KeyCols key;                          // SRC_RAW
   const unsigned long long* keys;       // SRC_SOA
   const long long* cols[kMaxCols];      // SRC_RAW payload / SRC_SOA state columns
@@ -86,7 +87,7 @@ __device__ __forceinline__ uint64_t src_key(const RowSrc& s, int64_t i) {
   int64_t r = s.offset + i;
   if (s.kind == SRC_AOS) return (uint64_t)s.aos[r * (1 + s.ncols)];
   if (s.kind == SRC_SOA) return __ldg(s.keys + r);
-  return load_key(s.key, r);
+  return load_key(s.key, r) | s.key_or;
 }
 
 __device__ __forceinline__ long long src_col(const RowSrc& s, int c, int64_t i) {

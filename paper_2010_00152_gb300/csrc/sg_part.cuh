@@ -641,4 +641,45 @@ inline size_t staged_smem_bytes(int nb, int ncols) {
   return (((size_t)2 * nb * 4 + 15) & ~(size_t)15) + (size_t)kStage * 8 * (1 + ncols) + (size_t)kStage * 2 + 16;
 }
 
+
+// Batched call, last step: the grouped rows are sorted by (instance, key), so
+// each instance's rows are one contiguous range; one CTA per instance finds
+// it (binary search on the instance bits) and copies it to the instance's own
+// outputs.  *out_rows = the range's length, or -1 when it exceeds the
+// instance's out_capacity (then nothing is written).
+__global__ void __launch_bounds__(256)
+k_distribute(const unsigned long long* keys, CopySrc states, long long total, int n_state,
+             const InstDesc* inst, int key_bits, int first) {
+  const int i = first + blockIdx.x;
+  __shared__ long long s_lo, s_hi;
+  if (threadIdx.x < 2) {
+    const unsigned long long target = (unsigned long long)(i + threadIdx.x) << key_bits;
+    long long lo = 0, hi = total;
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if (keys[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    if (threadIdx.x == 0) s_lo = lo; else s_hi = lo;
+  }
+  __syncthreads();
+  const InstDesc d = inst[i];
+  const long long lo = s_lo, rows = s_hi - s_lo;
+  if (rows > d.out_capacity) {
+    if (threadIdx.x == 0) *d.out_rows = -1;
+    return;
+  }
+  const unsigned long long mask = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1);
+  for (long long j = threadIdx.x; j < rows; j += blockDim.x) {
+    const unsigned long long k = keys[lo + j] & mask;
+    switch (d.key_bytes) {
+      case 1: reinterpret_cast<uint8_t*>(d.out_keys)[j] = (uint8_t)k; break;
+      case 2: reinterpret_cast<uint16_t*>(d.out_keys)[j] = (uint16_t)k; break;
+      case 4: reinterpret_cast<uint32_t*>(d.out_keys)[j] = (uint32_t)k; break;
+      default: reinterpret_cast<unsigned long long*>(d.out_keys)[j] = k; break;
+    }
+    for (int a = 0; a < n_state; ++a) d.out_aggs[a][j] = states.cols[a][lo + j];
+  }
+  if (threadIdx.x == 0) *d.out_rows = rows;
+}
+
 }  // namespace sg

@@ -35,7 +35,28 @@ constexpr int kFewGroups = 16;             // CTA-per-group fold below this many
 constexpr int kAccBlock = 8;               // state columns folded per pass
 
 enum : int { CH_NORMAL = 0, CH_COPY = 1 };
-enum : int { MODE_RANGE = 0, MODE_RUNS = 1, MODE_TILES = 2 };
+enum : int { MODE_RANGE = 0, MODE_RUNS = 1, MODE_TILES = 2, MODE_INST = 3 };
+
+// One instance of a batched call (same layout as sgagg_instance).
+struct InstDesc {
+  const void* keys;
+  int key_bytes;
+  int n_payload;
+  const long long* const* payload;   // device array of n_payload device pointers
+  long long n;
+  void* out_keys;
+  long long* const* out_aggs;        // device array
+  long long out_capacity;
+  long long* out_rows;               // device
+};
+
+// Batched tiles: chunk.pad = instance; the tile's rows are read from that
+// instance's columns, its keys OR-ed with instance << key_bits.
+struct InstSet {
+  const InstDesc* inst;
+  int key_bits;
+  int8_t colsel[kMaxCols];   // carried column c -> the instance's payload column
+};
 
 struct Chunk {
   long long lo, hi;   // MODE_RANGE: source rows; CH_COPY: rows of the copy source
@@ -210,7 +231,7 @@ __device__ __forceinline__ long long row_value(const SortSmem& s, const RowSrc& 
     return p[s.slo[r] + (i - s.spre[r])];
   }
   if (MODE == MODE_RANGE) return src.aos[(cv.lo + i) * (1 + src.ncols) + 1 + c];  // leaf: rows of the scatter
-  return src_col(src, c, cv.lo + i);
+  return src_col(src, c, cv.lo + i);  // MODE_TILES / MODE_INST: the raw (or state) source
 }
 
 // Where chunk row i's columns live: one address computation per row.
@@ -820,10 +841,11 @@ __device__ void fold_warps(const SortSmem& s, const RowSrc& src, const RunSet& r
 // ---------------------------------------------------------------------------
 template <int MODE, int KS>
 __global__ void __launch_bounds__(kThreads, 2)
-k_sortfold(const Chunk* __restrict__ chunks, RowSrc src, RunSet runs, CopySrc copy, FoldDesc fd,
-           OutSink out, LookBack lb, long long tile_n, int tile_f_hi) {
+k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, CopySrc copy, FoldDesc fd,
+           OutSink out, LookBack lb, long long tile_n, int tile_f_hi, InstSet is) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem s = carve(smem_raw);
+  __shared__ RowSrc s_src;  // MODE_INST: the chunk's instance as a source
   __shared__ int s_cid;
   __shared__ int s_err;
   __shared__ long long s_base;
@@ -845,6 +867,22 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src, RunSet runs, CopySrc co
   } else {
     ch = chunks[cid];
   }
+  if (MODE == MODE_INST) {
+    if (threadIdx.x == 0) {
+      const InstDesc d = is.inst[ch.pad];
+      s_src = src_param;
+      s_src.kind = SRC_RAW;
+      s_src.offset = 0;
+      s_src.key.n_cols = 1;
+      s_src.key.bytes[0] = d.key_bytes;
+      s_src.key.shift[0] = 0;
+      s_src.key.cols[0] = d.keys;
+      s_src.key_or = (unsigned long long)ch.pad << is.key_bits;
+      for (int c = 0; c < src_param.ncols; ++c) s_src.cols[c] = d.payload[is.colsel[c]];
+    }
+    __syncthreads();
+  }
+  const RowSrc& src = (MODE == MODE_INST) ? s_src : src_param;
 
   if (ch.kind == CH_COPY) {
     const long long n = ch.hi - ch.lo;

@@ -39,6 +39,7 @@ constexpr long long kBucketRows = 1024;
 constexpr int kMaxDepth = 70;
 constexpr long long kMaxBatch = 1ll << 30;
 constexpr int kSample = 16384;
+constexpr long long kBatchGroupRows = 1ll << 28;   // rows per group of a batched call
 
 struct DevBuf {
   void* p = nullptr;
@@ -110,6 +111,8 @@ struct sgagg_ctx {
   std::vector<DevBuf> gather_cols;
   DevBuf gather_ptrs;
   DevBuf runstarts;              // batches + 1 device scalars
+  DevBuf binst, bchunks, bkeys, bout_keys;   // batched call: instances, tiles, partial rows, output
+  std::vector<DevBuf> bcols, bout_cols;
   DevBuf marena_keys;            // runs written by preliminary merges
   std::vector<DevBuf> marena_cols;
   DevBuf moffs;
@@ -302,10 +305,10 @@ void set_smem_attr() {
 template <int MODE, int KS>
 void launch_ks(int grid, cudaStream_t st, const Chunk* dchunks, const RowSrc& src, const RunSet& runs,
                const CopySrc& copy, const FoldDesc& fd, const OutSink& out, const LookBack& lb,
-               long long tile_n, int tile_f_hi) {
+               long long tile_n, int tile_f_hi, const InstSet& is = InstSet{}) {
   set_smem_attr<MODE, KS>();
   k_sortfold<MODE, KS><<<grid, kThreads, kSortSmemBytes, st>>>(dchunks, src, runs, copy, fd, out, lb, tile_n,
-                                                              tile_f_hi);
+                                                              tile_f_hi, is);
 }
 
 constexpr int kMaxCoarseBits = 15;  // per-tile histogram / cursors: 2^15 x 4 B of shared memory
@@ -344,7 +347,7 @@ template <int MODE>
 sgagg_status launch_sortfold(sgagg_t h, int cls, const Chunk* dchunks, int n_chunks, long long tile_n,
                              const RowSrc& src, const RunSet& runs, const CopySrc& copy,
                              const FoldDesc& fd, const OutSink& out, const long long* base_in,
-                             long long* total_out, int tile_f_hi = 0) {
+                             long long* total_out, int tile_f_hi = 0, const InstSet& is = InstSet{}) {
   if (n_chunks <= 0) {
     // still publish the running total
     if (total_out) {
@@ -367,15 +370,15 @@ sgagg_status launch_sortfold(sgagg_t h, int cls, const Chunk* dchunks, int n_chu
   h->test_stall = 0;
   kbegin(h, cls);
   if (fd.n_state <= 2)
-    launch_ks<MODE, 2>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
+    launch_ks<MODE, 2>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
   else if (fd.n_state <= 4)
-    launch_ks<MODE, 4>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
+    launch_ks<MODE, 4>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
   else if (fd.n_state <= 8)
-    launch_ks<MODE, 8>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
+    launch_ks<MODE, 8>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
   else if (fd.n_state <= 16)
-    launch_ks<MODE, 16>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
+    launch_ks<MODE, 16>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
   else
-    launch_ks<MODE, 32>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi);
+    launch_ks<MODE, 32>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
   kend(h);
   CU(cudaGetLastError());
   return SGAGG_OK;
@@ -1203,6 +1206,250 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
 }  // namespace
 
 // ===========================================================================
+// Batched call: many independent instances as one grouping on the composite
+// normalized key (instance, key) -- instance id in the bits above the widest
+// key.  Three steps, whatever the instance count:
+//   1. one launch pre-aggregates instance-aligned tiles (a tile never spans
+//      two instances) straight from every instance's columns;
+//   2. the partial-aggregate rows are grouped by the ordinary path (partition,
+//      chunk sort+fold; several batches and a wide merge when they are many);
+//   3. one launch copies each instance's rows -- contiguous, since the output
+//      is sorted by instance first -- into that instance's outputs.
+// Composite keys need key bits + instance bits <= 64; beyond that the
+// instances are grouped one by one.
+// ===========================================================================
+namespace {
+
+// adds the CUDA-event times of the call's launches to the class totals
+// (the call's stream must have completed)
+void read_timers(sgagg_t h) {
+  if (h->timers_read) return;
+  for (int i = 0; i < h->ntimers; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->timers[i].a, h->timers[i].b) == cudaSuccess)
+      h->st.class_ms[h->timers[i].cls] += ms;
+  }
+  h->timers_read = true;
+}
+
+sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t count, const sgagg_spec* spec,
+                               cudaStream_t stream) {
+  if (count < 0 || (count > 0 && !inst) || !spec) return fail(h, SGAGG_EINVAL, "bad batched arguments");
+  if (spec->n_aggs < 0 || spec->n_aggs > kMaxCols || (spec->n_aggs > 0 && !spec->aggs))
+    return fail(h, SGAGG_EINVAL, "bad aggregate spec");
+  int maxkb = 1, maxcol = -1;
+  long long total = 0;
+  for (int i = 0; i < count; ++i) {
+    const sgagg_instance& d = inst[i];
+    const int kb = d.key_bytes;
+    if (kb != 1 && kb != 2 && kb != 4 && kb != 8) return fail(h, SGAGG_EINVAL, "instance key width must be 1, 2, 4 or 8");
+    if (d.n < 0 || d.out_capacity < 0 || !d.out_rows) return fail(h, SGAGG_EINVAL, "bad instance sizes or null out_rows");
+    if (d.n > 0 && !d.keys) return fail(h, SGAGG_EINVAL, "null instance keys");
+    if (d.n_payload < 0 || d.n_payload > 1024) return fail(h, SGAGG_EINVAL, "bad instance payload count");
+    maxkb = std::max(maxkb, kb);
+    total += d.n;
+  }
+  for (int a = 0; a < spec->n_aggs; ++a) {
+    const int op = spec->aggs[a].op;
+    if (op < SGAGG_COUNT || op > SGAGG_MAX) return fail(h, SGAGG_EINVAL, "bad aggregate op");
+    if (op != SGAGG_COUNT) {
+      maxcol = std::max(maxcol, (int)spec->aggs[a].col);
+      if (spec->aggs[a].col < 0) return fail(h, SGAGG_EINVAL, "aggregate column out of range");
+    }
+  }
+  for (int i = 0; i < count; ++i)
+    if (maxcol >= inst[i].n_payload || (maxcol >= 0 && inst[i].n > 0 && !inst[i].payload))
+      return fail(h, SGAGG_EINVAL, "aggregate column out of range for an instance");
+  const int S = spec->n_aggs;
+  const int key_bits = 8 * maxkb;
+  const int inst_bits = ilog2_ceil(std::max(1, count));
+  h->stream = stream;
+  h->have_call = true;
+  h->st = sgagg_stats_t{};
+  h->st.n_rows = total;
+  ++h->gen;
+  h->touched.clear();
+  h->ntimers = 0;
+  h->timers_read = true;
+  h->key_bytes = maxkb;
+  h->spec_aggs = S;
+  h->last_rows = 0;
+  TRY(ensure_ctx_device(h));
+  Small* ds = dsmall(h);
+  HostSmall* hs = hsmall(h);
+  CU(cudaMemsetAsync(ds, 0, sizeof(Small), stream));
+  if (count == 0) return SGAGG_OK;
+
+  if (key_bits + inst_bits > 64) {
+    // composite key too wide: one instance at a time through the ordinary
+    // path; the counters of the calls are summed
+    long long rows_all = 0;
+    sgagg_stats_t acc{};
+    for (int i = 0; i < count; ++i) {
+      const sgagg_instance& d = inst[i];
+      std::vector<const int64_t*> pay(std::max(1, d.n_payload), nullptr);
+      std::vector<int64_t*> oa(std::max(1, S), nullptr);
+      if (d.n_payload > 0) CU(cudaMemcpy(pay.data(), d.payload, (size_t)d.n_payload * 8, cudaMemcpyDeviceToHost));
+      if (S > 0) CU(cudaMemcpy(oa.data(), d.out_aggs, (size_t)S * 8, cudaMemcpyDeviceToHost));
+      int32_t kb = d.key_bytes;
+      const void* kc = d.keys;
+      sgagg_keys k{1, &kb, &kc};
+      void* ok = d.out_keys;
+      sgagg_status st = aggregate_device(h, &k, pay.data(), d.n_payload, d.n, spec, &ok, oa.data(),
+                                         d.out_capacity, stream);
+      long long r = st == SGAGG_OK ? h->last_rows : -1;
+      if (st != SGAGG_OK && st != SGAGG_ECAPACITY) return st;
+      CU(cudaMemcpyAsync(d.out_rows, &r, 8, cudaMemcpyHostToDevice, stream));
+      CU(cudaStreamSynchronize(stream));
+      rows_all += std::max(0ll, r);
+      read_timers(h);
+      const sgagg_stats_t& c = h->st;
+      acc.batches += c.batches; acc.runs += c.runs; acc.run_rows += c.run_rows;
+      acc.run_bytes_device += c.run_bytes_device; acc.run_bytes_host += c.run_bytes_host;
+      acc.out_rows += c.out_rows; acc.prefold_passes += c.prefold_passes;
+      acc.split_segments += c.split_segments; acc.merge_tiles += c.merge_tiles;
+      acc.kernel_launches += c.kernel_launches;
+      for (int k = 0; k < 8; ++k) {
+        acc.class_launches[k] += c.class_launches[k];
+        acc.class_bytes[k] += c.class_bytes[k];
+        acc.class_ms[k] += c.class_ms[k];
+      }
+    }
+    acc.n_rows = total;
+    h->st = acc;
+    h->key_bytes = maxkb;
+    h->last_rows = rows_all;
+    return SGAGG_OK;
+  }
+
+  // instance table (all instances); groups of consecutive instances of at
+  // most kBatchGroupRows rows bound the scratch
+  TRY(grow(h, h->binst, (size_t)count * sizeof(InstDesc)));
+  static_assert(sizeof(InstDesc) == sizeof(sgagg_instance), "instance layouts differ");
+  CU(cudaMemcpyAsync(h->binst.p, inst, (size_t)count * sizeof(InstDesc), cudaMemcpyHostToDevice, stream));
+  InstSet is{};
+  is.inst = P<InstDesc>(h->binst);
+  is.key_bits = key_bits;
+  FoldDesc fd{};
+  fd.n_state = S;
+  int colmap[1024];
+  for (int c = 0; c < 1024; ++c) colmap[c] = -1;
+  int C = 0;
+  for (int a = 0; a < S; ++a) {
+    const int op = spec->aggs[a].op;
+    if (op == SGAGG_COUNT) {
+      fd.src[a] = -1;
+      fd.op[a] = OP_SUM;
+    } else {
+      const int c = spec->aggs[a].col;
+      if (colmap[c] < 0) {
+        colmap[c] = C;
+        is.colsel[C] = (int8_t)c;
+        ++C;
+      }
+      fd.src[a] = (int8_t)colmap[c];
+      fd.op[a] = op == SGAGG_SUM ? OP_SUM : (op == SGAGG_MIN ? OP_MIN : OP_MAX);
+    }
+  }
+  RowSrc raw{};
+  raw.kind = SRC_RAW;
+  raw.ncols = C;
+  const FoldDesc fid = identity_fold(fd);
+  long long rows_all = 0;
+  int i0 = 0;
+  while (i0 < count) {
+    int i1 = i0;
+    long long grows = 0;
+    while (i1 < count && (i1 == i0 || grows + inst[i1].n <= kBatchGroupRows)) grows += inst[i1++].n;
+    std::vector<Chunk> tiles;
+    for (int i = i0; i < i1; ++i)
+      for (long long lo = 0; lo < inst[i].n; lo += kTileCap) {
+        Chunk c{};
+        c.lo = lo;
+        c.hi = std::min<long long>(inst[i].n, lo + kTileCap);
+        c.kind = CH_NORMAL;
+        c.pad = i;
+        tiles.push_back(c);
+      }
+    const long long ntiles = (long long)tiles.size();
+    TRY(grow(h, h->bchunks, (size_t)std::max(1ll, ntiles) * sizeof(Chunk)));
+    if (ntiles)
+      CU(cudaMemcpyAsync(h->bchunks.p, tiles.data(), tiles.size() * sizeof(Chunk), cudaMemcpyHostToDevice, stream));
+    // 1. tile pre-aggregation over the group's instances
+    TRY(grow(h, h->bkeys, (size_t)std::max(1ll, grows) * 8));
+    TRY(grow_cols(h, h->bcols, S, (size_t)std::max(1ll, grows) * 8));
+    OutSink o{};
+    o.user = 0;
+    o.keys = P<unsigned long long>(h->bkeys);
+    for (int a = 0; a < S; ++a) o.cols[a] = P<long long>(h->bcols[a]);
+    o.capacity = grows;
+    RunSet norun{};
+    CopySrc nocopy{};
+    long long n1 = 0;
+    if (ntiles) {
+      TRY(launch_sortfold<MODE_INST>(h, SGAGG_K_PREFOLD, P<Chunk>(h->bchunks), (int)ntiles, 0, raw, norun, nocopy,
+                                     fd, o, nullptr, &ds->pftot, 0, is));
+      TRY(sync_read(h, &hs->v[0], &ds->pftot, 8));
+      TRY(check_device_err(h));
+      n1 = hs->v[0];
+    }
+    ++h->st.prefold_passes;
+    kbytes(h, SGAGG_K_PREFOLD, grows * (maxkb + 8ll * C) + n1 * 8ll * (1 + S));
+    // 2. group the partial rows on (instance, key)
+    RowSrc part{};
+    part.kind = SRC_SOA;
+    part.ncols = S;
+    part.keys = P<unsigned long long>(h->bkeys);
+    for (int a = 0; a < S; ++a) part.cols[a] = P<long long>(h->bcols[a]);
+    TRY(grow(h, h->bout_keys, (size_t)std::max(1ll, n1) * 8));
+    TRY(grow_cols(h, h->bout_cols, S, (size_t)std::max(1ll, n1) * 8));
+    OutSink g{};
+    g.user = 0;
+    g.keys = P<unsigned long long>(h->bout_keys);
+    for (int a = 0; a < S; ++a) g.cols[a] = P<long long>(h->bout_cols[a]);
+    g.capacity = n1;
+    long long rows = 0;
+    if (n1 > 0) {
+      h->top_prefold = false;
+      if (n1 > kTileCap) {
+        int cnt = (int)std::min<long long>(n1, 4096);
+        TRY(grow(h, h->sample, (size_t)kSample * 8));
+        kbegin(h, SGAGG_K_PROBE);
+        k_sample<<<8, 256, 0, stream>>>(part, n1, cnt, P<unsigned long long>(h->sample));
+        kend(h);
+        TRY(sync_read(h, hs->sample, h->sample.p, (size_t)cnt * 8));
+        std::sort(hs->sample, hs->sample + cnt);
+        long long dist = std::unique(hs->sample, hs->sample + cnt) - hs->sample;
+        h->top_prefold = want_prefold(h, cnt, dist);
+      }
+      CU(cudaMemsetAsync(&ds->total, 0, 8, stream));
+      TRY(solve(h, part, n1, fid, g, nullptr, &ds->total, nullptr, 0));
+      TRY(sync_read(h, &hs->v[1], &ds->total, 8));
+      TRY(check_device_err(h));
+      rows = hs->v[1];
+    }
+    // 3. every instance's rows to its outputs
+    CopySrc gs{};
+    gs.keys = g.keys;
+    for (int a = 0; a < S; ++a) gs.cols[a] = g.cols[a];
+    kbegin(h, SGAGG_K_OTHER);
+    k_distribute<<<i1 - i0, 256, 0, stream>>>(g.keys, gs, rows, S, P<InstDesc>(h->binst), key_bits, i0);
+    kend(h);
+    kbytes(h, SGAGG_K_OTHER, rows * (8ll * (1 + S) + maxkb + 8ll * S));
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(stream));  // the group's scratch is reused by the next group
+    rows_all += rows;
+    i0 = i1;
+  }
+  const long long rows = rows_all;
+  h->last_rows = rows;
+  h->st.out_rows = rows;
+  return SGAGG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
 // Grouping without allocation (sgagg_aggregate_noalloc).
 //
 // One chunk of at most kTileCap rows is sorted and folded by the same kernel
@@ -1458,14 +1705,7 @@ int64_t sgagg_temp_bytes(sgagg_t h) {
 sgagg_status sgagg_stats(sgagg_t h, sgagg_stats_t* out) {
   if (!h || !out) return SGAGG_EINVAL;
   if (h->have_call) cudaStreamSynchronize(h->stream);
-  if (!h->timers_read) {
-    for (int i = 0; i < h->ntimers; ++i) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, h->timers[i].a, h->timers[i].b) == cudaSuccess)
-        h->st.class_ms[h->timers[i].cls] += ms;
-    }
-    h->timers_read = true;
-  }
+  read_timers(h);
   *out = h->st;
   out->peak_scratch_bytes = scratch_in_use(h);
   out->out_bytes = h->st.out_rows * (h->key_bytes + 8ll * h->spec_aggs);
@@ -1474,9 +1714,11 @@ sgagg_status sgagg_stats(sgagg_t h, sgagg_stats_t* out) {
 
 sgagg_status sgagg_aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t count, const sgagg_spec* spec,
                                      void* stream) {
-  (void)inst; (void)count; (void)spec; (void)stream;
   if (!h) return SGAGG_EINVAL;
-  return fail(h, SGAGG_EINVAL, "batched mode not built yet");
+  h->err.clear();
+  sgagg_status s = aggregate_batched(h, inst, count, spec, reinterpret_cast<cudaStream_t>(stream));
+  h->pending_err = (int)s;
+  return s;
 }
 
 void sgagg_destroy(sgagg_t h) {
@@ -1494,6 +1736,8 @@ void sgagg_destroy(sgagg_t h) {
   free_buf(h->offs); free_buf(h->runptrs); free_buf(h->fsizes); free_buf(h->gather_keys); fv(h->gather_cols);
   free_buf(h->gather_ptrs); free_buf(h->runstarts);
   free_buf(h->marena_keys); fv(h->marena_cols); free_buf(h->moffs);
+  free_buf(h->binst); free_buf(h->bchunks); free_buf(h->bkeys); free_buf(h->bout_keys);
+  fv(h->bcols); fv(h->bout_cols);
   for (auto& b : h->in_keys) free_buf(b);
   fv(h->in_pay);
   for (auto& b : h->out_keys) free_buf(b);

@@ -260,6 +260,38 @@ class Aggregator:
         rows = sgagg_result_rows(self.h)
         return [k[:rows] for k in ok], [a[:rows] for a in oa]
 
+    def aggregate_batched(self, instances, aggs, capacities=None, stream=None):
+        """instances: list of (key tensor (one unsigned column), [int64 payload
+        tensors]) on one CUDA device.  Groups every instance independently in
+        one batched call; returns a list of (keys, [aggregates]) per instance
+        (None for an instance whose capacity was too small)."""
+        import torch
+        dev = instances[0][0].device if instances else torch.device("cuda")
+        keep = []
+        descs = []
+        outs = []
+        rows = torch.zeros(max(1, len(instances)), dtype=torch.int64, device=dev)
+        for i, (k, pay) in enumerate(instances):
+            n = int(k.numel())
+            cap = n if capacities is None else int(capacities[i])
+            ok = torch.empty(max(1, cap), dtype=k.dtype, device=dev)
+            oa = [torch.empty(max(1, cap), dtype=torch.int64, device=dev) for _ in aggs]
+            pp = torch.tensor([p.data_ptr() for p in pay] or [0], dtype=torch.int64, device=dev)
+            op = torch.tensor([a.data_ptr() for a in oa] or [0], dtype=torch.int64, device=dev)
+            keep += [k, ok, pp, op] + list(pay) + oa
+            descs.append(sgagg_instance(k.data_ptr(), k.element_size(), len(pay), pp.data_ptr(), n, ok.data_ptr(),
+                                        op.data_ptr(), cap, rows.data_ptr() + 8 * i))
+            outs.append((ok, oa))
+        s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+        sgagg_aggregate_batched(self.h, descs, aggs, s)
+        torch.cuda.synchronize(dev)
+        r = rows.cpu().tolist()
+        res = []
+        for i, (ok, oa) in enumerate(outs):
+            res.append(None if r[i] < 0 else (ok[:r[i]], [a[:r[i]] for a in oa]))
+        del keep
+        return res
+
     def rows(self):
         return sgagg_result_rows(self.h)
 

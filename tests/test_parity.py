@@ -236,3 +236,59 @@ def test_preliminary_merges(cap):
     c = datagen.config1(n=60_000, seed=13, D=9000)
     st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=1000, fanin_cap=cap)
     assert st["runs"] > 60
+
+
+def _batched_case(seed, sizes, domains, key_dtype=torch.uint32):
+    insts = []
+    for i, (n, D) in enumerate(zip(sizes, domains)):
+        c = datagen.config4_instance(dict(rows=n, D=D, seed=seed * 1000 + i)) if n > 0 else None
+        if c is None:
+            k = torch.empty(0, dtype=key_dtype)
+            p = torch.empty(0, dtype=torch.int64)
+        else:
+            k = c["key_cols"][0]
+            p = c["payload"][0]
+            if key_dtype != torch.uint32:
+                k = k.to(torch.int64).to(key_dtype) if key_dtype != torch.uint64 else k.to(torch.int64).view(torch.uint64)
+        insts.append((k, [p]))
+    return insts
+
+
+@pytest.mark.parametrize("key_dtype", [torch.uint32, torch.uint16, torch.uint64])
+def test_batched_matches_oracle(key_dtype):
+    """Independent instances of uneven sizes in one batched call; every
+    instance equals its own oracle result."""
+    sizes = [0, 1, 5, 1000, 8192, 8193, 20_000, 70_001, 3, 150_000, 9000, 12]
+    domains = [1, 1, 3, 16, 500, 20_000, 5, 100_000, 2, 1_000, 60_000, 7]
+    insts = _batched_case(3, sizes, domains, key_dtype)
+    aggs = [(0, 0), (1, 0), (2, 0), (3, 0)]
+    agg = sgagg.Aggregator(1 << 20)
+    try:
+        res = agg.aggregate_batched([(k.to(DEV), [p.to(DEV) for p in pay]) for k, pay in insts], aggs)
+        st = agg.stats()
+    finally:
+        agg.close()
+    assert st["n_rows"] == sum(sizes)
+    for (k, pay), r in zip(insts, res):
+        rk, ra = oracle_run([k], pay, aggs)
+        assert r is not None
+        np.testing.assert_array_equal(to_np(r[0]), rk[0])
+        for a in range(len(aggs)):
+            np.testing.assert_array_equal(to_np(r[1][a]), ra[a])
+
+
+def test_batched_capacity_and_equals_plain():
+    insts = _batched_case(5, [4000, 30_000, 100], [4000, 200, 100])
+    aggs = [(0, 0), (1, 0), (2, 0)]
+    agg = sgagg.Aggregator(1 << 20)
+    try:
+        res = agg.aggregate_batched([(k.to(DEV), [p.to(DEV) for p in pay]) for k, pay in insts], aggs,
+                                    capacities=[10, 30_000, 100])
+        assert res[0] is None  # 4000 rows over 4000 values need more than 10 rows
+        for (k, pay), r in zip(insts[1:], res[1:]):
+            ok, oa = agg.aggregate([k.to(DEV)], [p.to(DEV) for p in pay], aggs)
+            np.testing.assert_array_equal(to_np(r[0]), to_np(ok[0]))
+            for a in range(len(aggs)):
+                np.testing.assert_array_equal(to_np(r[1][a]), to_np(oa[a]))
+    finally:
+        agg.close()
