@@ -218,15 +218,18 @@ def bench_batched(args, dev):
     n_total = sum(sp["rows"] for sp in specs)
     outs, descs, keep = [], [], []
     rows_dev = torch.zeros(count, dtype=torch.int64, device=dev)
+    caps = []
     for i, c in enumerate(insts):
         k, p = c["key_cols"][0], c["payload"][0]
         n = k.numel()
-        ok = torch.empty(n, dtype=k.dtype, device=dev)
-        oa = [torch.empty(n, dtype=torch.int64, device=dev) for _ in aggs]
+        cap = max(1, min(n, specs[i]["D"]))  # at most D distinct keys
+        caps.append(cap)
+        ok = torch.empty(cap, dtype=k.dtype, device=dev)
+        oa = [torch.empty(cap, dtype=torch.int64, device=dev) for _ in aggs]
         pp = torch.tensor([p.data_ptr()], dtype=torch.int64, device=dev)
         op = torch.tensor([a.data_ptr() for a in oa], dtype=torch.int64, device=dev)
         keep += [pp, op]
-        descs.append(sgagg.sgagg_instance(k.data_ptr(), 4, 1, pp.data_ptr(), n, ok.data_ptr(), op.data_ptr(), n,
+        descs.append(sgagg.sgagg_instance(k.data_ptr(), 4, 1, pp.data_ptr(), n, ok.data_ptr(), op.data_ptr(), cap,
                                           rows_dev.data_ptr() + 8 * i))
         outs.append((ok, oa))
     torch.cuda.synchronize()
@@ -244,7 +247,7 @@ def bench_batched(args, dev):
             k, p = c["key_cols"][0], c["payload"][0]
             ok, oa = outs[i]
             sgagg.sgagg_aggregate(agg.h, [k.data_ptr()], [4], [p.data_ptr()], k.numel(), aggs, [ok.data_ptr()],
-                                  [a.data_ptr() for a in oa], k.numel(), s)
+                                  [a.data_ptr() for a in oa], caps[i], s)
             r += agg.rows()
         return r
 

@@ -118,14 +118,37 @@ __device__ __forceinline__ int64_t op_combine(int op, int64_t a, int64_t b) {
 // order; the coarse digit is fine >> ebits.  Keys below base go to bucket 0,
 // keys above the sampled range to the last bucket.
 // ---------------------------------------------------------------------------
+// One segment of a segmented digit: the keys whose bits above seg_shift
+// equal the segment's index (one instance of a batched call) map to buckets
+// base + ((low bits - kmin) >> shift), clamped to base + span.
+struct SegEntry {
+  unsigned long long kmin;
+  unsigned base;
+  unsigned info;  // shift in bits 0-7, span (buckets - 1) in bits 8-31
+};
+
 struct Digit {
   unsigned long long base;
   int fshift;
   int fbits;
   int ebits;
+  int seg_shift;            // with seg: segment index = key >> seg_shift
+  int seg_n;                // segments in the table
+  const SegEntry* seg;      // null: one linear digit over the whole key range
 };
 
 __device__ __forceinline__ uint32_t fine_digit(const Digit& d, uint64_t k) {
+  if (d.seg) {
+    uint64_t i = k >> d.seg_shift;
+    i = i < (uint64_t)d.seg_n ? i : (uint64_t)d.seg_n - 1;
+    const SegEntry e = d.seg[i];
+    const uint64_t low = k & ((1ull << d.seg_shift) - 1);
+    uint64_t x = low < e.kmin ? 0 : ((low - e.kmin) >> (e.info & 255u));
+    const uint64_t span = e.info >> 8;
+    x = x > span ? span : x;
+    const uint64_t f = e.base + x, lim = (1ull << d.fbits) - 1;
+    return (uint32_t)(f > lim ? lim : f);
+  }
   if (d.fbits == 0 || k < d.base) return 0;
   uint64_t x = d.fshift >= 64 ? 0 : ((k - d.base) >> d.fshift);
   uint64_t lim = (1ull << d.fbits) - 1;

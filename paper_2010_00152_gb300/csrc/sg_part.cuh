@@ -132,10 +132,11 @@ struct PlanInfo {
 
 // Single CTA.  w[0..nb) are bucket row counts in key order.  Writes bstart
 // (exclusive prefix, nb + 1 entries), the chunk list and the indices of big
-// chunks.  A bucket with more than `big` rows is a chunk of its own (kind
-// CH_COPY: solved separately).  Other buckets are grouped while their
-// exclusive prefix over non-big buckets stays in one multiple of `target`,
-// so a chunk holds fewer than target + big rows.  Chunk c covers buckets
+// chunks.  A bucket with more than `big` rows is a chunk of its own: kind
+// CH_NORMAL up to `cap` rows, else CH_COPY (solved separately, listed in
+// big_list).  Other buckets are grouped while their exclusive prefix over
+// buckets of at most `big` rows stays in one multiple of `target`, so such a
+// chunk holds fewer than target + big rows.  Chunk c covers buckets
 // [d_lo, d_hi), i.e. fine range [d_lo << fine_shift, d_hi << fine_shift).
 __device__ __forceinline__ bool plan_is_start(long long x, long long big, long long pB, long long target,
                                               bool* prev_big, long long* prev_q) {
@@ -181,7 +182,7 @@ __device__ __forceinline__ long long plan_scan(long long v, long long* total) {
 }
 
 __global__ void __launch_bounds__(1024)
-k_plan(const long long* __restrict__ w, int nb, long long target, long long big, int fine_shift,
+k_plan(const long long* __restrict__ w, int nb, long long target, long long big, long long cap, int fine_shift,
        long long* bstart, Chunk* chunks, int* big_list, PlanInfo* info) {
   const int T = blockDim.x;
   const int per = (nb + T - 1) / T;
@@ -193,7 +194,8 @@ k_plan(const long long* __restrict__ w, int nb, long long target, long long big,
   for (int d = d0; d < d1; ++d) {
     long long x = w[d];
     ta += x;
-    if (x > big) tc += 1; else tb += x;
+    if (x > cap) tc += 1;
+    if (x <= big) tb += x;
   }
   long long dummy;
   const long long A0 = plan_scan(ta, &dummy);
@@ -243,8 +245,8 @@ k_plan(const long long* __restrict__ w, int nb, long long target, long long big,
       if (plan_is_start(x, big, pB, target, &pbig, &pq)) {
         ++cidx;
         chunks[cidx].f_lo = d;  // bucket index for now
-        chunks[cidx].kind = x > big ? CH_COPY : CH_NORMAL;
-        if (x > big) big_list[nbig++] = (int)cidx;
+        chunks[cidx].kind = x > cap ? CH_COPY : CH_NORMAL;
+        if (x > cap) big_list[nbig++] = (int)cidx;
       }
       if (x <= big) pB += x;
       pA += x;
@@ -642,44 +644,59 @@ inline size_t staged_smem_bytes(int nb, int ncols) {
 }
 
 
-// Batched call, last step: the grouped rows are sorted by (instance, key), so
-// each instance's rows are one contiguous range; one CTA per instance finds
-// it (binary search on the instance bits) and copies it to the instance's own
-// outputs.  *out_rows = the range's length, or -1 when it exceeds the
-// instance's out_capacity (then nothing is written).
-__global__ void __launch_bounds__(256)
-k_distribute(const unsigned long long* keys, CopySrc states, long long total, int n_state,
-             const InstDesc* inst, int key_bits, int first) {
-  const int i = first + blockIdx.x;
-  __shared__ long long s_lo, s_hi;
-  if (threadIdx.x < 2) {
-    const unsigned long long target = (unsigned long long)(i + threadIdx.x) << key_bits;
+// start[j] = first row of instance first + j, for j in [0, count], in rows
+// whose keys carry the instance id above key_bits and come grouped by
+// instance in ascending order (sorted within an instance's rows or not).
+// With write_rows (the grouped output, step 1 of the batched output), each
+// instance's *out_rows = its row count, or -1 when that exceeds its
+// out_capacity (then nothing is written for it).
+__global__ void k_inst_bounds(const unsigned long long* keys, long long total, const InstDesc* inst,
+                              int key_bits, int first, int count, long long* start, int write_rows) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > count) return;
+  auto lower = [&](int i) {
+    const unsigned long long target = (unsigned long long)i << key_bits;
     long long lo = 0, hi = total;
     while (lo < hi) {
       const long long mid = (lo + hi) >> 1;
       if (keys[mid] < target) lo = mid + 1; else hi = mid;
     }
-    if (threadIdx.x == 0) s_lo = lo; else s_hi = lo;
+    return lo;
+  };
+  const long long a = lower(first + j);
+  start[j] = a;
+  if (write_rows && j < count) {
+    const long long rows = lower(first + j + 1) - a;
+    *inst[first + j].out_rows = rows > inst[first + j].out_capacity ? -1 : rows;
   }
-  __syncthreads();
-  const InstDesc d = inst[i];
-  const long long lo = s_lo, rows = s_hi - s_lo;
-  if (rows > d.out_capacity) {
-    if (threadIdx.x == 0) *d.out_rows = -1;
-    return;
-  }
-  const unsigned long long mask = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1);
-  for (long long j = threadIdx.x; j < rows; j += blockDim.x) {
-    const unsigned long long k = keys[lo + j] & mask;
+}
+
+// Batched output, step 2: row r of the grouped rows goes to row
+// r - start[i] of instance i's outputs (key without the instance bits).
+// A CTA copies kDistRows consecutive rows.
+constexpr int kDistRows = 2048;
+__global__ void __launch_bounds__(256)
+k_distribute(const unsigned long long* keys, CopySrc states, long long total, int n_state,
+             const InstDesc* inst, int key_bits, int first, int count, const long long* start) {
+  const long long r0 = (long long)blockIdx.x * kDistRows;
+  const long long r1 = min(total, r0 + kDistRows);
+  const unsigned long long mask = (1ull << key_bits) - 1;
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const unsigned long long key = keys[r];
+    const long long j = (long long)(key >> key_bits) - first;
+    if (j < 0 || j >= count) continue;  // not this group's row (never: rows are built so)
+    const InstDesc& d = inst[first + j];
+    const long long at = r - start[j];
+    if (start[j + 1] - start[j] > d.out_capacity) continue;
+    const unsigned long long k = key & mask;
     switch (d.key_bytes) {
-      case 1: reinterpret_cast<uint8_t*>(d.out_keys)[j] = (uint8_t)k; break;
-      case 2: reinterpret_cast<uint16_t*>(d.out_keys)[j] = (uint16_t)k; break;
-      case 4: reinterpret_cast<uint32_t*>(d.out_keys)[j] = (uint32_t)k; break;
-      default: reinterpret_cast<unsigned long long*>(d.out_keys)[j] = k; break;
+      case 1: reinterpret_cast<uint8_t*>(d.out_keys)[at] = (uint8_t)k; break;
+      case 2: reinterpret_cast<uint16_t*>(d.out_keys)[at] = (uint16_t)k; break;
+      case 4: reinterpret_cast<uint32_t*>(d.out_keys)[at] = (uint32_t)k; break;
+      default: reinterpret_cast<unsigned long long*>(d.out_keys)[at] = k; break;
     }
-    for (int a = 0; a < n_state; ++a) d.out_aggs[a][j] = states.cols[a][lo + j];
+    for (int a = 0; a < n_state; ++a) d.out_aggs[a][at] = states.cols[a][r];
   }
-  if (threadIdx.x == 0) *d.out_rows = rows;
 }
 
 }  // namespace sg

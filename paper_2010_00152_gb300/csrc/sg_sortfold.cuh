@@ -56,6 +56,8 @@ struct InstSet {
   const InstDesc* inst;
   int key_bits;
   int8_t colsel[kMaxCols];   // carried column c -> the instance's payload column
+  unsigned long long* kmin;  // per instance: least key (preset ~0), or null
+  unsigned long long* kmax;  // per instance: greatest key (preset 0)
 };
 
 struct Chunk {
@@ -954,6 +956,13 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
   load_keys<MODE>(s, src, runs, cv);
   __syncthreads();
   const int how = chunk_sort(s, cv.n);
+  if (MODE == MODE_INST && is.kmin && threadIdx.x == 0 && cv.n > 0) {
+    // key range of the instance (its tiles' sorted ends), for the digit
+    // that partitions the partial rows
+    const unsigned long long m = (1ull << is.key_bits) - 1;
+    atomicMin(is.kmin + ch.pad, s.keys[s.idx[0]] & m);
+    atomicMax(is.kmax + ch.pad, s.keys[s.idx[cv.n - 1]] & m);
+  }
   if (how == FOLD_BINS) fold_lanes<MODE, KS>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
   else fold_warps<MODE>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
 }

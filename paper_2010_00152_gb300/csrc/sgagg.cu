@@ -29,9 +29,10 @@ using namespace sg;
 
 namespace {
 
-// Planner: a chunk starts every kChunkTarget rows of non-big buckets and a
-// bucket above kBigBucket rows is solved apart, so chunks stay below
-// kChunkTarget + kBigBucket = kTileCap rows.  Coarse buckets average
+// Planner: a chunk starts every kChunkTarget rows of buckets of at most
+// kBigBucket rows, so such chunks stay below kChunkTarget + kBigBucket =
+// kTileCap rows; a bigger bucket is a chunk of its own, solved apart when it
+// holds more than kTileCap rows.  Coarse buckets average
 // kBucketRows rows (32 standard deviations below kBigBucket for uniform keys).
 constexpr long long kBigBucket = 2048;
 constexpr long long kChunkTarget = kTileCap - kBigBucket;
@@ -39,7 +40,7 @@ constexpr long long kBucketRows = 1024;
 constexpr int kMaxDepth = 70;
 constexpr long long kMaxBatch = 1ll << 30;
 constexpr int kSample = 16384;
-constexpr long long kBatchGroupRows = 1ll << 28;   // rows per group of a batched call
+constexpr long long kBatchGroupRows = 1ll << 25;   // rows per group of a batched call
 
 struct DevBuf {
   void* p = nullptr;
@@ -112,6 +113,7 @@ struct sgagg_ctx {
   DevBuf gather_ptrs;
   DevBuf runstarts;              // batches + 1 device scalars
   DevBuf binst, bchunks, bkeys, bout_keys;   // batched call: instances, tiles, partial rows, output
+  DevBuf bseg, brange, bstartb;              // batched call: segmented digit, key ranges, row starts
   std::vector<DevBuf> bcols, bout_cols;
   DevBuf marena_keys;            // runs written by preliminary merges
   std::vector<DevBuf> marena_cols;
@@ -609,7 +611,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     kend(h);
     kbytes(h, SGAGG_K_SCATTER, n * 16ll * W);
     kbegin(h, SGAGG_K_PLAN);
-    k_plan<<<1, 1024, 0, h->stream>>>(P<long long>(h->btot[depth]), nb, kChunkTarget, kBigBucket, dig.ebits,
+    k_plan<<<1, 1024, 0, h->stream>>>(P<long long>(h->btot[depth]), nb, kChunkTarget, kBigBucket, kTileCap, dig.ebits,
                                       P<long long>(h->bstart[depth]), P<Chunk>(h->chunks[depth]),
                                       P<int>(h->biglist[depth]), &ds->info);
     kend(h);
@@ -626,7 +628,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
                                                            P<long long>(h->btot[depth]));
     kend(h);
     kbegin(h, SGAGG_K_PLAN);
-    k_plan<<<1, 1024, 0, h->stream>>>(P<long long>(h->btot[depth]), nb, kChunkTarget, kBigBucket, dig.ebits,
+    k_plan<<<1, 1024, 0, h->stream>>>(P<long long>(h->btot[depth]), nb, kChunkTarget, kBigBucket, kTileCap, dig.ebits,
                                       P<long long>(h->bstart[depth]), P<Chunk>(h->chunks[depth]),
                                       P<int>(h->biglist[depth]), &ds->info);
     kend(h);
@@ -846,7 +848,7 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
   TRY(grow(h, h->chunks[0], (size_t)nf * sizeof(Chunk)));
   TRY(grow(h, h->biglist[0], (size_t)nf * 4));
   kbegin(h, SGAGG_K_PLAN);
-  k_plan<<<1, 1024, 0, stream>>>(P<long long>(h->fsizes), nf, kChunkTarget, kBigBucket, 0,
+  k_plan<<<1, 1024, 0, stream>>>(P<long long>(h->fsizes), nf, kChunkTarget, kBigBucket, kTileCap, 0,
                                  P<long long>(h->bstart[0]), P<Chunk>(h->chunks[0]), P<int>(h->biglist[0]),
                                  &ds->info);
   kend(h);
@@ -1262,7 +1264,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
       return fail(h, SGAGG_EINVAL, "aggregate column out of range for an instance");
   const int S = spec->n_aggs;
   const int key_bits = 8 * maxkb;
-  const int inst_bits = ilog2_ceil(std::max(1, count));
+  const int inst_bits = std::max(1, ilog2_ceil(std::max(1, count)));  // >= 1: key_bits stays below 64
   h->stream = stream;
   h->have_call = true;
   h->st = sgagg_stats_t{};
@@ -1325,11 +1327,23 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
   // instance table (all instances); groups of consecutive instances of at
   // most kBatchGroupRows rows bound the scratch
   TRY(grow(h, h->binst, (size_t)count * sizeof(InstDesc)));
+  TRY(grow(h, h->bseg, (size_t)count * sizeof(SegEntry)));
+  TRY(grow(h, h->brange, (size_t)count * 16));
+  TRY(grow(h, h->bstartb, (size_t)(count + 1) * 8));
+  std::vector<SegEntry> seg(count);
+  std::vector<unsigned long long> rng((size_t)count * 2);
+  std::vector<long long> cnt1((size_t)count + 1);
+  unsigned long long* kmin_d = P<unsigned long long>(h->brange);
+  unsigned long long* kmax_d = kmin_d + count;
+  CU(cudaMemsetAsync(kmin_d, 0xFF, (size_t)count * 8, stream));
+  CU(cudaMemsetAsync(kmax_d, 0, (size_t)count * 8, stream));
   static_assert(sizeof(InstDesc) == sizeof(sgagg_instance), "instance layouts differ");
   CU(cudaMemcpyAsync(h->binst.p, inst, (size_t)count * sizeof(InstDesc), cudaMemcpyHostToDevice, stream));
   InstSet is{};
   is.inst = P<InstDesc>(h->binst);
   is.key_bits = key_bits;
+  is.kmin = kmin_d;
+  is.kmax = kmax_d;
   FoldDesc fd{};
   fd.n_state = S;
   int colmap[1024];
@@ -1409,6 +1423,48 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
     for (int a = 0; a < S; ++a) g.cols[a] = P<long long>(h->bout_cols[a]);
     g.capacity = n1;
     long long rows = 0;
+    Digit sdig{};
+    if (n1 > kTileCap) {
+      // segmented digit: every instance gets buckets in proportion to its
+      // partial rows over its own key range
+      const int gi = i1 - i0;
+      kbegin(h, SGAGG_K_PROBE);
+      k_inst_bounds<<<(gi + 256) / 256, 256, 0, stream>>>(P<unsigned long long>(h->bkeys), n1, P<InstDesc>(h->binst),
+                                                          key_bits, i0, gi, P<long long>(h->bstartb), 0);
+      kend(h);
+      TRY(sync_read(h, cnt1.data(), h->bstartb.p, (size_t)(gi + 1) * 8));
+      CU(cudaMemcpy(rng.data(), kmin_d + i0, (size_t)gi * 8, cudaMemcpyDeviceToHost));
+      CU(cudaMemcpy(rng.data() + count, kmax_d + i0, (size_t)gi * 8, cudaMemcpyDeviceToHost));
+      int Db = 0;
+      for (long long per = kBucketRows;; per *= 2) {
+        long long tot = 0;
+        for (int j = 0; j < gi; ++j) {
+          const long long m = cnt1[j + 1] - cnt1[j];
+          SegEntry e{};
+          e.base = (unsigned)tot;
+          if (m > 0) {
+            const unsigned long long lo = rng[j], hi = rng[count + j];
+            const unsigned long long range = hi - lo;
+            const long long F = std::min(1ll << 20, std::max(1ll, m / per));
+            int sh = range < (unsigned long long)F ? 0 : bitlen(range) - (bitlen((unsigned long long)F) - 1);
+            sh = std::max(0, sh);
+            const long long span = (long long)(range >> sh);  // buckets - 1, below F
+            e.kmin = lo;
+            e.info = (unsigned)sh | ((unsigned)span << 8);
+            tot += span + 1;
+          }
+          seg[i0 + j] = e;
+        }
+        Db = std::max(1, ilog2_ceil(tot));
+        if (Db <= kMaxCoarseBits) break;
+      }
+      CU(cudaMemcpyAsync(P<SegEntry>(h->bseg) + i0, seg.data() + i0, (size_t)gi * sizeof(SegEntry),
+                         cudaMemcpyHostToDevice, stream));
+      sdig.fbits = Db;
+      sdig.seg = P<SegEntry>(h->bseg);
+      sdig.seg_shift = key_bits;
+      sdig.seg_n = count;
+    }
     if (n1 > 0) {
       h->top_prefold = false;
       if (n1 > kTileCap) {
@@ -1423,7 +1479,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
         h->top_prefold = want_prefold(h, cnt, dist);
       }
       CU(cudaMemsetAsync(&ds->total, 0, 8, stream));
-      TRY(solve(h, part, n1, fid, g, nullptr, &ds->total, nullptr, 0));
+      TRY(solve(h, part, n1, fid, g, nullptr, &ds->total, sdig.seg ? &sdig : nullptr, 0));
       TRY(sync_read(h, &hs->v[1], &ds->total, 8));
       TRY(check_device_err(h));
       rows = hs->v[1];
@@ -1433,8 +1489,16 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
     gs.keys = g.keys;
     for (int a = 0; a < S; ++a) gs.cols[a] = g.cols[a];
     kbegin(h, SGAGG_K_OTHER);
-    k_distribute<<<i1 - i0, 256, 0, stream>>>(g.keys, gs, rows, S, P<InstDesc>(h->binst), key_bits, i0);
+    k_inst_bounds<<<(i1 - i0 + 256) / 256, 256, 0, stream>>>(g.keys, rows, P<InstDesc>(h->binst), key_bits, i0,
+                                                             i1 - i0, P<long long>(h->bstartb), 1);
+    if (rows > 0)
+      k_distribute<<<(int)((rows + kDistRows - 1) / kDistRows), 256, 0, stream>>>(
+          g.keys, gs, rows, S, P<InstDesc>(h->binst), key_bits, i0, i1 - i0, P<long long>(h->bstartb));
     kend(h);
+    if (rows > 0) {
+      ++h->st.class_launches[SGAGG_K_OTHER];
+      ++h->st.kernel_launches;
+    }
     kbytes(h, SGAGG_K_OTHER, rows * (8ll * (1 + S) + maxkb + 8ll * S));
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(stream));  // the group's scratch is reused by the next group
@@ -1737,6 +1801,7 @@ void sgagg_destroy(sgagg_t h) {
   free_buf(h->gather_ptrs); free_buf(h->runstarts);
   free_buf(h->marena_keys); fv(h->marena_cols); free_buf(h->moffs);
   free_buf(h->binst); free_buf(h->bchunks); free_buf(h->bkeys); free_buf(h->bout_keys);
+  free_buf(h->bseg); free_buf(h->brange); free_buf(h->bstartb);
   fv(h->bcols); fv(h->bout_cols);
   for (auto& b : h->in_keys) free_buf(b);
   fv(h->in_pay);

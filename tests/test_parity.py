@@ -277,6 +277,33 @@ def test_batched_matches_oracle(key_dtype):
             np.testing.assert_array_equal(to_np(r[1][a]), ra[a])
 
 
+def test_batched_clustered_instances():
+    """Instances whose keys crowd one end of their range (one bucket of the
+    per-instance digit far above a chunk), one key value, and a wide spread;
+    every instance equals its own oracle result."""
+    g = torch.Generator().manual_seed(11)
+    a = torch.cat([torch.randperm(40_000, generator=g), torch.tensor([2**32 - 1, 2**32 - 2, 2**31])])
+    b = torch.full((50_000,), 7)
+    c = torch.randint(0, 2**32, (60_000,), generator=g)
+    d = torch.randint(0, 20, (9_000,), generator=g)
+    insts = []
+    for k in (a, b, c, d):
+        k = k.to(torch.int64).to(torch.uint32)
+        p = torch.randint(-1000, 1001, (k.numel(),), generator=g, dtype=torch.int64)
+        insts.append((k, [p]))
+    aggs = [(0, 0), (1, 0), (2, 0), (3, 0)]
+    agg = sgagg.Aggregator(1 << 20)
+    try:
+        res = agg.aggregate_batched([(k.to(DEV), [p.to(DEV) for p in pay]) for k, pay in insts], aggs)
+    finally:
+        agg.close()
+    for (k, pay), r in zip(insts, res):
+        rk, ra = oracle_run([k], pay, aggs)
+        np.testing.assert_array_equal(to_np(r[0]), rk[0])
+        for j in range(len(aggs)):
+            np.testing.assert_array_equal(to_np(r[1][j]), ra[j])
+
+
 def test_batched_capacity_and_equals_plain():
     insts = _batched_case(5, [4000, 30_000, 100], [4000, 200, 100])
     aggs = [(0, 0), (1, 0), (2, 0)]
