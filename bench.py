@@ -63,11 +63,15 @@ def make_workload(name, device, n=None):
     import datagen
     w = WORKLOADS[name]
     n = n or w["n"]
+    # a reduced row count keeps the workload's shape: ~2 rows per key and 16
+    # runs for c3, the same key domain and 16 runs for c1
     if name == "c3":
-        return datagen.config3(n=n, D=w["D"] if n == w["n"] else max(1, n // 2), M=w["M"], device=device)
+        full = n == w["n"]
+        return datagen.config3(n=n, D=w["D"] if full else max(1, n // 2), M=w["M"] if full else max(1, n // 16),
+                               device=device)
     if name == "c2":
         return datagen.config2(n=n, device=device)
-    return datagen.config1(n=n, D=w["D"], M=w["M"], device=device)
+    return datagen.config1(n=n, D=w["D"], M=w["M"] if n == w["n"] else max(1, n // 16), device=device)
 
 
 class ClockSampler:

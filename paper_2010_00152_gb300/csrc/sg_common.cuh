@@ -137,8 +137,11 @@ struct Digit {
   const SegEntry* seg;      // null: one linear digit over the whole key range
 };
 
+// SEG: the digit has a segment table (kernels are compiled for either form,
+// so the common linear digit carries no table lookup).
+template <bool SEG = false>
 __device__ __forceinline__ uint32_t fine_digit(const Digit& d, uint64_t k) {
-  if (d.seg) {
+  if (SEG) {
     uint64_t i = k >> d.seg_shift;
     i = i < (uint64_t)d.seg_n ? i : (uint64_t)d.seg_n - 1;
     const SegEntry e = d.seg[i];
@@ -155,8 +158,9 @@ __device__ __forceinline__ uint32_t fine_digit(const Digit& d, uint64_t k) {
   return (uint32_t)(x > lim ? lim : x);
 }
 
+template <bool SEG = false>
 __device__ __forceinline__ uint32_t coarse_digit(const Digit& d, uint64_t k) {
-  return fine_digit(d, k) >> d.ebits;
+  return fine_digit<SEG>(d, k) >> d.ebits;
 }
 
 // ---------------------------------------------------------------------------

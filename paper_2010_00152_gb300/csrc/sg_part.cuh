@@ -57,11 +57,13 @@ __device__ __forceinline__ void tile_range(long long n, int ntiles, int t, long 
 
 // Digit of one partitioning level: bits [dshift, dshift + log2(nb)) of the
 // coarse digit.
+template <bool SEG>
 __device__ __forceinline__ unsigned level_digit(const Digit& dig, unsigned long long k, int dshift, int nb) {
-  return (coarse_digit(dig, k) >> dshift) & (unsigned)(nb - 1);
+  return (coarse_digit<SEG>(dig, k) >> dshift) & (unsigned)(nb - 1);
 }
 
 // thist[d * ntiles + t] = rows of tile t with level digit d.
+template <bool SEG>
 __global__ void __launch_bounds__(kPartThreads)
 k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsigned int* thist) {
   extern __shared__ unsigned int sh_hist[];
@@ -85,7 +87,7 @@ k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsig
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       long long i = i0 + (long long)u * blockDim.x;
-      if (i < hi) atomicAdd(&mine[level_digit(dig, k[u], dshift, nb)], 1u);
+      if (i < hi) atomicAdd(&mine[level_digit<SEG>(dig, k[u], dshift, nb)], 1u);
     }
   }
   __syncthreads();
@@ -282,6 +284,7 @@ k_plan(const long long* __restrict__ w, int nb, long long target, long long big,
 // Scatter rows [0, n) of src into buckets: row i goes to
 // bstart[d] + (its tile's offset in bucket d) + (rank inside the tile).
 // Output rows are 1 + ncols int64 words: key, then the carried columns.
+template <bool SEG>
 __global__ void __launch_bounds__(kPartThreads)
 k_scatter(RowSrc src, long long n, Digit dig, int nb, int ntiles, const unsigned int* thist,
           const long long* bstart, long long* aos) {
@@ -307,7 +310,7 @@ k_scatter(RowSrc src, long long n, Digit dig, int nb, int ntiles, const unsigned
       for (int u = 0; u < U; ++u) {
         long long i = i0 + (long long)u * blockDim.x;
         if (i < hi) {
-          unsigned pos = atomicAdd(&cursor[coarse_digit(dig, k[u])], 1u);
+          unsigned pos = atomicAdd(&cursor[coarse_digit<SEG>(dig, k[u])], 1u);
           // one 16-byte store: key + the one carried column
           longlong2 r;
           r.x = (long long)k[u];
@@ -329,7 +332,7 @@ k_scatter(RowSrc src, long long n, Digit dig, int nb, int ntiles, const unsigned
     for (int u = 0; u < U; ++u) {
       long long i = i0 + (long long)u * blockDim.x;
       if (i < hi) {
-        unsigned pos = atomicAdd(&cursor[coarse_digit(dig, k[u])], 1u);
+        unsigned pos = atomicAdd(&cursor[coarse_digit<SEG>(dig, k[u])], 1u);
         long long* row = aos + (long long)pos * W;
         row[0] = (long long)k[u];
         for (int c = 0; c < src.ncols; ++c) row[1 + c] = src_col(src, c, i);
@@ -451,6 +454,7 @@ k_tiles2(const long long* bstart1, int nb1, Tile2* tiles, int* tfirst) {
 }
 
 // Level-2 histograms: thist2[t * nb2 + d] = rows of tile t with digit d.
+template <bool SEG>
 __global__ void __launch_bounds__(kPartThreads)
 k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, unsigned* thist2) {
   extern __shared__ unsigned sh2[];
@@ -473,7 +477,7 @@ k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, u
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       long long i = i0 + (long long)u * blockDim.x;
-      if (i < tl.hi) atomicAdd(&mine[level_digit(dig, k[u], 0, nb2)], 1u);
+      if (i < tl.hi) atomicAdd(&mine[level_digit<SEG>(dig, k[u], 0, nb2)], 1u);
     }
   }
   __syncthreads();
@@ -514,6 +518,7 @@ k_scan2(const long long* bstart1, int nb2, const int* tfirst, unsigned* thist2, 
 // bstart[d] + table[d * ntiles + t].  Level 2: tile t is tiles[t] and the
 // cursor starts at table[t * nb + d].  Output: SoA (okeys/ocols) or rows of
 // 1 + ncols words (oaos).
+template <bool SEG>
 __global__ void __launch_bounds__(kPartThreads, 2)
 k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, const Tile2* tiles,
                  const int* ntiles_dev, const unsigned* table, const long long* bstart,
@@ -585,7 +590,7 @@ k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int nti
       const int i = threadIdx.x + u * kPartThreads;
       if (i < m) {
         skey[i] = kk[u];
-        unsigned d = level_digit(dig, kk[u], dsh, nb);
+        unsigned d = level_digit<SEG>(dig, kk[u], dsh, nb);
         unsigned r = atomicAdd(&lst[d], 1u);
         dr[u] = (d << 16) | r;
       }
@@ -612,7 +617,7 @@ k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int nti
     for (int lp = threadIdx.x; lp < m; lp += kPartThreads) {
       const int i = sperm[lp];
       const unsigned long long k = skey[i];
-      const unsigned d = level_digit(dig, k, dsh, nb);
+      const unsigned d = level_digit<SEG>(dig, k, dsh, nb);
       const long long gp = (long long)cursor[d] + (lp - (int)lst[d]);
       if (oaos) {
         long long* row = oaos + gp * (1 + C);

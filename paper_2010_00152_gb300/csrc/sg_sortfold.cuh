@@ -222,20 +222,6 @@ __device__ __forceinline__ int run_of(const SortSmem& s, int k, int i) {
   return lo;
 }
 
-// Source value of column c (< 0: the constant 1 of count(*)) for chunk row i.
-template <int MODE>
-__device__ __forceinline__ long long row_value(const SortSmem& s, const RowSrc& src, const RunSet& runs,
-                                               const ChunkView& cv, int c, int i) {
-  if (c < 0) return 1;
-  if (MODE == MODE_RUNS) {
-    int r = run_of(s, cv.k, i);
-    const long long* p = runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c];
-    return p[s.slo[r] + (i - s.spre[r])];
-  }
-  if (MODE == MODE_RANGE) return src.aos[(cv.lo + i) * (1 + src.ncols) + 1 + c];  // leaf: rows of the scatter
-  return src_col(src, c, cv.lo + i);  // MODE_TILES / MODE_INST: the raw (or state) source
-}
-
 // Where chunk row i's columns live: one address computation per row.
 struct RowAt {
   const long long* aos;      // MODE_RANGE: the row's first column
@@ -468,7 +454,111 @@ __device__ int chunk_sort(const SortSmem& s, int n) {
     __syncthreads();
     return FOLD_BINS;
   }
-  lsd_sort(s, n, kmin, vb);
+  // Some bin holds more than 32 rows -- usually a key repeated many times.
+  // Bins of up to 32 rows are finished by insertion as above.  A warp takes
+  // each bigger bin: it collects the bin's distinct keys (at most 32, one per
+  // lane, with their row counts), ranks them, and places every row at its
+  // key's position.  A bin with more distinct keys sends the chunk to the
+  // LSD sort.
+  __shared__ int s_nbig, s_over;
+  if (threadIdx.x == 0) {
+    s_nbig = 0;
+    s_over = 0;
+  }
+  __syncthreads();
+  uint32_t* blist = reinterpret_cast<uint32_t*>(s.whist);  // start | end << 16; fewer than n / 32 bins
+  for (int b = threadIdx.x; b < kBins; b += kThreads) {
+    const int st = (int)bin_get(s.bins, b);
+    const int en = (b + 1 < kBins) ? (int)bin_get(s.bins, b + 1) : n;
+    if (en - st > 32) {
+      blist[atomicAdd(&s_nbig, 1)] = (unsigned)st | ((unsigned)en << 16);
+      continue;
+    }
+    for (int i = st + 1; i < en; ++i) {
+      const uint16_t v = s.idx[i];
+      const unsigned long long kv = s.keys[v];
+      int j = i - 1;
+      while (j >= st) {
+        const uint16_t u = s.idx[j];
+        if (s.keys[u] <= kv) break;
+        s.idx[j + 1] = u;
+        --j;
+      }
+      s.idx[j + 1] = v;
+    }
+  }
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1;
+    uint16_t* tmp = reinterpret_cast<uint16_t*>(s.bins);  // bin starts are no longer needed
+    const int nbig = s_nbig;
+    for (int q = w; q < nbig; q += kWarps) {
+      const int st = (int)(blist[q] & 0xFFFFu), en = (int)(blist[q] >> 16);
+      unsigned long long dkey = 0;  // lane e: distinct key e of the bin
+      int dcnt = 0, nd = 0;         // lane e: its rows; nd: keys found (warp-uniform)
+      bool over = false;
+      for (int base = st; base < en && !over; base += 32) {
+        const int i = base + lane;
+        const bool act = i < en;
+        const unsigned long long key = act ? s.keys[s.idx[i]] : 0ull;
+        bool known = false;
+        for (int e = 0; e < nd; ++e) {
+          const unsigned long long ke = __shfl_sync(0xffffffffu, dkey, e);
+          const unsigned m = __ballot_sync(0xffffffffu, act && key == ke);
+          known |= (m >> lane) & 1u;
+          if (lane == e) dcnt += __popc(m);
+        }
+        unsigned nf = __ballot_sync(0xffffffffu, act && !known);
+        while (nf) {
+          if (nd == 32) {
+            over = true;
+            break;
+          }
+          const int l = __ffs(nf) - 1;
+          const unsigned long long kl = __shfl_sync(0xffffffffu, key, l);
+          const unsigned m = __ballot_sync(0xffffffffu, act && !known && key == kl);
+          if (lane == nd) {
+            dkey = kl;
+            dcnt = __popc(m);
+          }
+          ++nd;
+          nf &= ~m;
+        }
+      }
+      if (over) {  // warp-uniform
+        if (lane == 0) s_over = 1;
+        continue;
+      }
+      // lane e: first position of key e = st + rows of the smaller keys
+      int cur = st;
+      for (int e = 0; e < nd; ++e) {
+        const unsigned long long ke = __shfl_sync(0xffffffffu, dkey, e);
+        const int ce = __shfl_sync(0xffffffffu, dcnt, e);
+        if (lane < nd && ke < dkey) cur += ce;
+      }
+      for (int base = st; base < en; base += 32) {
+        const int i = base + lane;
+        const bool act = i < en;
+        const uint16_t v = act ? s.idx[i] : (uint16_t)0;
+        const unsigned long long key = act ? s.keys[v] : 0ull;
+        int pos = -1;
+        for (int e = 0; e < nd; ++e) {
+          const unsigned long long ke = __shfl_sync(0xffffffffu, dkey, e);
+          const unsigned m = __ballot_sync(0xffffffffu, act && key == ke);
+          const int c0 = __shfl_sync(0xffffffffu, cur, e);
+          if ((m >> lane) & 1u) pos = c0 + __popc(m & lt);
+          if (lane == e) cur += __popc(m);
+        }
+        if (act && pos >= st && pos < en) tmp[pos] = v;
+      }
+      __syncwarp();
+      for (int i = st + lane; i < en; i += 32) s.idx[i] = tmp[i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (s_over) lsd_sort(s, n, kmin, vb);  // block-uniform
   return FOLD_WARPS;
 }
 
@@ -683,10 +773,6 @@ __shared__ int g_whead[kWarps];
 __shared__ int g_gstart[kFewGroups + 1];
 __shared__ long long g_gacc[kWarps * kAccBlock];
 
-__device__ __forceinline__ bool is_head(const SortSmem& s, int p) {
-  return p == 0 || s.keys[s.idx[p]] != s.keys[s.idx[p - 1]];
-}
-
 // Inclusive segmented scan across the warp: flag starts a segment.
 __device__ __forceinline__ long long warp_seg_scan(int op, bool flag, long long v) {
   const int lane = threadIdx.x & 31;
@@ -710,12 +796,15 @@ __device__ void fold_warps(const SortSmem& s, const RowSrc& src, const RunSet& r
   const unsigned le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1);
   const int Q = ((n + kWarps - 1) / kWarps + 31) & ~31;
   const int wb = min(n, w * Q), we = min(n, wb + Q);
-  // heads per warp range
+  uint32_t* hm = s.bins;  // head bitmask (the sort is done with the bins)
+  // heads -> bitmask, per-warp counts (warp ranges are 32-aligned)
   int hc = 0;
   for (int b = wb; b < we; b += 32) {
-    int p = b + lane;
-    bool h = p < we && is_head(s, p);
-    hc += __popc(__ballot_sync(0xffffffffu, h));
+    const int p = b + lane;
+    const bool h = p < we && (p == 0 || s.keys[s.idx[p]] != s.keys[s.idx[p - 1]]);
+    const unsigned hb = __ballot_sync(0xffffffffu, h);
+    if (lane == 0) hm[b >> 5] = hb;
+    hc += __popc(hb);
   }
   if (lane == 0) g_wcnt[w] = hc;
   __syncthreads();
@@ -735,10 +824,9 @@ __device__ void fold_warps(const SortSmem& s, const RowSrc& src, const RunSet& r
   {
     int run = g_wcnt[w];
     for (int b = wb; b < we; b += 32) {
-      int p = b + lane;
-      bool h = p < we && is_head(s, p);
-      unsigned hb = __ballot_sync(0xffffffffu, h);
-      if (h) {
+      const int p = b + lane;
+      const unsigned hb = hm[b >> 5];
+      if (p < we && ((hb >> lane) & 1u)) {
         long long g = run + __popc(hb & le) - 1;
         unsigned long long key = s.keys[s.idx[p]];
         if (count <= kFewGroups) g_gstart[g] = p;
@@ -749,92 +837,104 @@ __device__ void fold_warps(const SortSmem& s, const RowSrc& src, const RunSet& r
     }
   }
 
-  if (count <= kFewGroups) {
-    // few key groups: the CTA reduces one group at a time, kAccBlock
-    // aggregates per sweep
-    if (threadIdx.x == 0) g_gstart[count] = n;
+  // aggregates: one source column at a time, staged where the keys were
+  // (c = -1: count(*) of raw rows, every value 1)
+  long long* col = reinterpret_cast<long long*>(s.keys);
+  const int ncols = (MODE == MODE_RUNS) ? runs.ncols : src.ncols;
+  if (count <= kFewGroups && threadIdx.x == 0) g_gstart[count] = n;
+  for (int c = -1; c < ncols; ++c) {
+    bool used = false;
+    for (int a = 0; a < fd.n_state; ++a) used |= (fd.src[a] == c);
+    if (!used) continue;
+    __syncthreads();  // everyone is done with the keys / the previous column
+    if (c >= 0) stage_column<MODE>(s, src, runs, cv, c, col);
     __syncthreads();
-    for (int g = 0; g < count; ++g) {
-      const int gs = g_gstart[g], ge = g_gstart[g + 1];
-      for (int s0 = 0; s0 < fd.n_state; s0 += kAccBlock) {
-        long long acc[kAccBlock];
-#pragma unroll
-        for (int a = 0; a < kAccBlock; ++a)
-          if (s0 + a < fd.n_state) acc[a] = op_identity(fd.op[s0 + a]);
-        for (int p = gs + threadIdx.x; p < ge; p += kThreads) {
-          const int i = s.idx[p];
+    if (count <= kFewGroups) {
+      // few key groups: the CTA reduces one group at a time, kAccBlock
+      // aggregates per sweep
+      for (int g = 0; g < count; ++g) {
+        const int gs = g_gstart[g], ge = g_gstart[g + 1];
+        for (int s0 = 0; s0 < fd.n_state; s0 += kAccBlock) {
+          bool any = false;
+          for (int a = 0; a < kAccBlock && s0 + a < fd.n_state; ++a) any |= (fd.src[s0 + a] == c);
+          if (!any) continue;  // block-uniform
+          long long acc[kAccBlock];
 #pragma unroll
           for (int a = 0; a < kAccBlock; ++a)
-            if (s0 + a < fd.n_state)
-              acc[a] = op_combine(fd.op[s0 + a], acc[a], row_value<MODE>(s, src, runs, cv, fd.src[s0 + a], i));
-        }
+            if (s0 + a < fd.n_state) acc[a] = op_identity(fd.op[s0 + a]);
+          for (int p = gs + threadIdx.x; p < ge; p += kThreads) {
+            const long long v = c < 0 ? 1ll : col[s.idx[p]];
 #pragma unroll
-        for (int a = 0; a < kAccBlock; ++a)
-          if (s0 + a < fd.n_state) {
-            long long v = warp_reduce(fd.op[s0 + a], acc[a]);
-            if (lane == 0) g_gacc[w * kAccBlock + a] = v;
+            for (int a = 0; a < kAccBlock; ++a)
+              if (s0 + a < fd.n_state && fd.src[s0 + a] == c) acc[a] = op_combine(fd.op[s0 + a], acc[a], v);
           }
-        __syncthreads();
-        if (threadIdx.x < kAccBlock && s0 + (int)threadIdx.x < fd.n_state) {
-          const int a = threadIdx.x, op = fd.op[s0 + a];
-          long long v = op_identity(op);
-          for (int ww = 0; ww < kWarps; ++ww) v = op_combine(op, v, g_gacc[ww * kAccBlock + a]);
-          sink_val(out, s0 + a, base + g, v);
+#pragma unroll
+          for (int a = 0; a < kAccBlock; ++a)
+            if (s0 + a < fd.n_state && fd.src[s0 + a] == c) {
+              long long v = warp_reduce(fd.op[s0 + a], acc[a]);
+              if (lane == 0) g_gacc[w * kAccBlock + a] = v;
+            }
+          __syncthreads();
+          if (threadIdx.x < kAccBlock && s0 + (int)threadIdx.x < fd.n_state && fd.src[s0 + threadIdx.x] == c) {
+            const int a = threadIdx.x, op = fd.op[s0 + a];
+            long long v = op_identity(op);
+            for (int ww = 0; ww < kWarps; ++ww) v = op_combine(op, v, g_gacc[ww * kAccBlock + a]);
+            sink_val(out, s0 + a, base + g, v);
+          }
+          __syncthreads();
         }
-        __syncthreads();
       }
+      continue;
     }
-    return;
-  }
-
-  for (int st = 0; st < fd.n_state; ++st) {
-    const int op = fd.op[st];
-    const int c = fd.src[st];
-    // pass A: partial of the segment open at the end of this warp's range
-    long long carry = op_identity(op);
-    bool any_head = false;
-    for (int b = wb; b < we; b += 32) {
-      int p = b + lane;
-      bool valid = p < we;
-      bool h = valid && is_head(s, p);
-      long long v = valid ? row_value<MODE>(s, src, runs, cv, c, s.idx[p]) : op_identity(op);
-      bool f = h || lane == 0;
-      if (lane == 0 && !h) v = op_combine(op, carry, v);
-      long long x = warp_seg_scan(op, f, v);
-      carry = __shfl_sync(0xffffffffu, x, 31);
-      any_head |= __ballot_sync(0xffffffffu, h) != 0;
-    }
-    if (lane == 0) { g_wtail[w] = carry; g_whead[w] = any_head; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // exclusive segmented scan over warps (in place)
-      long long acc = op_identity(op);
-      for (int i = 0; i < kWarps; ++i) {
-        long long t = g_wtail[i];
-        int hh = g_whead[i];
-        g_wtail[i] = acc;
-        acc = hh ? t : op_combine(op, acc, t);
+    for (int st = 0; st < fd.n_state; ++st) {
+      if (fd.src[st] != c) continue;  // block-uniform
+      const int op = fd.op[st];
+      // pass A: partial of the segment open at the end of this warp's range
+      long long carry = op_identity(op);
+      bool any_head = false;
+      for (int b = wb; b < we; b += 32) {
+        const int p = b + lane;
+        const bool valid = p < we;
+        const bool h = valid && head_bit(hm, p);
+        long long v = valid ? (c < 0 ? 1ll : col[s.idx[p]]) : op_identity(op);
+        const bool f = h || lane == 0;
+        if (lane == 0 && !h) v = op_combine(op, carry, v);
+        const long long x = warp_seg_scan(op, f, v);
+        carry = __shfl_sync(0xffffffffu, x, 31);
+        any_head |= __ballot_sync(0xffffffffu, h) != 0;
       }
+      if (lane == 0) { g_wtail[w] = carry; g_whead[w] = any_head; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        // exclusive segmented scan over warps (in place)
+        long long acc = op_identity(op);
+        for (int i = 0; i < kWarps; ++i) {
+          long long t = g_wtail[i];
+          int hh = g_whead[i];
+          g_wtail[i] = acc;
+          acc = hh ? t : op_combine(op, acc, t);
+        }
+      }
+      __syncthreads();
+      // pass B: complete segments
+      carry = g_wtail[w];
+      int run = g_wcnt[w];
+      for (int b = wb; b < we; b += 32) {
+        const int p = b + lane;
+        const bool valid = p < we;
+        const bool h = valid && head_bit(hm, p);
+        long long v = valid ? (c < 0 ? 1ll : col[s.idx[p]]) : op_identity(op);
+        const bool f = h || lane == 0;
+        if (lane == 0 && !h) v = op_combine(op, carry, v);
+        const long long x = warp_seg_scan(op, f, v);
+        const unsigned hb = __ballot_sync(0xffffffffu, h);
+        const bool ends = valid && (p + 1 >= n || head_bit(hm, p + 1));
+        if (ends) sink_val(out, st, base + run + __popc(hb & le) - 1, x);
+        run += __popc(hb);
+        carry = __shfl_sync(0xffffffffu, x, 31);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // pass B: complete segments
-    carry = g_wtail[w];
-    int run = g_wcnt[w];
-    for (int b = wb; b < we; b += 32) {
-      int p = b + lane;
-      bool valid = p < we;
-      bool h = valid && is_head(s, p);
-      long long v = valid ? row_value<MODE>(s, src, runs, cv, c, s.idx[p]) : op_identity(op);
-      bool f = h || lane == 0;
-      if (lane == 0 && !h) v = op_combine(op, carry, v);
-      long long x = warp_seg_scan(op, f, v);
-      unsigned hb = __ballot_sync(0xffffffffu, h);
-      bool ends = valid && (p + 1 >= n || is_head(s, p + 1));
-      if (ends) sink_val(out, st, base + run + __popc(hb & le) - 1, x);
-      run += __popc(hb);
-      carry = __shfl_sync(0xffffffffu, x, 31);
-    }
-    __syncthreads();
   }
 }
 
