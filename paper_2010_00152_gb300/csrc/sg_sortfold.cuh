@@ -7,18 +7,16 @@
 //      or one slice from each of k sorted runs, all loads in flight at once;
 //      the runs' aggregate columns are prefetched into L2 meanwhile);
 //   2. sort a permutation of the chunk by key: a counting sort on the top
-//      kBinBits bits of (key - chunk min); bins are finished by insertion
-//      sort, or -- when some bin is large -- the chunk is sorted by a stable
-//      LSD radix sort (8-bit digits, warp-ballot ranking) over every bit that
-//      varies inside the chunk;
-//   3. fold equal keys, choosing by the shape of the chunk:
-//        lane per row     key groups of at most 32 rows (uniform keys: the
-//                         common case);
-//        CTA per group    few distinct keys (at most kFewGroups);
-//        warp ranges      anything else: segmented scans over warp ranges;
-//      the chunk's distinct-key count gives its output offset by decoupled
-//      look-back, and aggregate values are gathered by row index from the
-//      source (L2-resident) while the sorted keys stay in shared memory.
+//      kBinBits bits of (key - chunk min); bins of up to 32 rows are finished
+//      by insertion sort, a bigger bin (a repeated key, as a rule) by a warp
+//      that ranks the bin's distinct keys; a bin of more than 32 distinct
+//      keys sends the chunk to a stable LSD radix sort (8-bit digits,
+//      warp-ballot ranking) over every bit that varies inside the chunk;
+//   3. fold equal keys: a lane per key group of at most 32 rows, a warp per
+//      bigger group, or -- with at most kFewGroups groups -- the whole CTA
+//      per group; the chunk's distinct-key count gives its output offset by
+//      decoupled look-back, and each aggregate source column is staged once
+//      into shared memory (where the sorted keys were) and folded from there.
 #pragma once
 #include "sg_common.cuh"
 
@@ -366,11 +364,8 @@ __device__ void lsd_sort(const SortSmem& s, int n, unsigned long long kmin, int 
   }
 }
 
-enum : int { FOLD_BINS = 0, FOLD_WARPS = 1 };
-
-// Sort s.idx by key; returns FOLD_BINS when s.bins holds bin starts whose bins
-// contain whole key groups of at most 32 rows, else FOLD_WARPS.
-__device__ int chunk_sort(const SortSmem& s, int n) {
+// Sort s.idx by key; returns whether a key group may hold more than 32 rows.
+__device__ bool chunk_sort(const SortSmem& s, int n) {
   unsigned long long lmin = ~0ull, lmax = 0ull;
   for (int i = threadIdx.x; i < n; i += kThreads) {
     unsigned long long k = s.keys[i];
@@ -382,7 +377,7 @@ __device__ int chunk_sort(const SortSmem& s, int n) {
   if (n == 0) {
     for (int i = threadIdx.x; i < kBins / 2; i += kThreads) s.bins[i] = 0;
     __syncthreads();
-    return FOLD_BINS;
+    return false;
   }
   const unsigned long long range = kmax - kmin;
   const int vb = range == 0 ? 0 : 64 - __clzll((long long)range);
@@ -431,7 +426,7 @@ __device__ int chunk_sort(const SortSmem& s, int n) {
     if (i < n) s.idx[(int)bin_get(s.bins, (int)(br[j] >> 16)) + (int)(br[j] & 0xFFFFu)] = (uint16_t)i;
   }
   __syncthreads();
-  if (sh == 0) return maxbin <= 32 ? FOLD_BINS : FOLD_WARPS;  // every bin is one key value
+  if (sh == 0) return maxbin > 32;  // every bin is one key value
   if (maxbin <= 32) {
     // with about one row per bin, only the few bins holding two or more rows
     // need work: insertion sort in place, a thread per bin
@@ -452,7 +447,7 @@ __device__ int chunk_sort(const SortSmem& s, int n) {
       }
     }
     __syncthreads();
-    return FOLD_BINS;
+    return false;
   }
   // Some bin holds more than 32 rows -- usually a key repeated many times.
   // Bins of up to 32 rows are finished by insertion as above.  A warp takes
@@ -559,7 +554,7 @@ __device__ int chunk_sort(const SortSmem& s, int n) {
   }
   __syncthreads();
   if (s_over) lsd_sort(s, n, kmin, vb);  // block-uniform
-  return FOLD_WARPS;
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -656,18 +651,97 @@ __device__ __forceinline__ int group_end(const uint32_t* hm, int p, int n) {
   return n;
 }
 
-template <int MODE, int KS>
-__device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& runs, const ChunkView& cv,
-                           const FoldDesc& fd, const OutSink& out, const LookBack& lb, const Chunk& ch,
-                           int cid, long long* s_base) {
+constexpr int kLaneGroup = 32;  // key groups up to this many rows are folded by one lane
+
+__shared__ int g_gstart[kFewGroups + 1];
+__shared__ long long g_gacc[kWarps * kAccBlock];
+__shared__ int g_nbig;
+
+// Few key groups: the CTA reduces one group at a time (positions in
+// g_gstart), kAccBlock aggregates of source column c per sweep.
+__device__ void fold_few(const SortSmem& s, const FoldDesc& fd, const OutSink& out,
+                                      const long long* col, int c, int count, long long base) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ns = fd.n_state;
+  for (int g = 0; g < count; ++g) {
+    const int gs = g_gstart[g], ge = g_gstart[g + 1];
+    for (int s0 = 0; s0 < ns; s0 += kAccBlock) {
+      bool any = false;
+      for (int a = 0; a < kAccBlock && s0 + a < ns; ++a) any |= (fd.src[s0 + a] == c);
+      if (!any) continue;  // block-uniform
+      long long acc[kAccBlock];
+#pragma unroll
+      for (int a = 0; a < kAccBlock; ++a)
+        if (s0 + a < ns) acc[a] = op_identity(fd.op[s0 + a]);
+      for (int p = gs + threadIdx.x; p < ge; p += kThreads) {
+        const long long v = col[s.idx[p]];
+#pragma unroll
+        for (int a = 0; a < kAccBlock; ++a)
+          if (s0 + a < ns && fd.src[s0 + a] == c) acc[a] = op_combine(fd.op[s0 + a], acc[a], v);
+      }
+#pragma unroll
+      for (int a = 0; a < kAccBlock; ++a)
+        if (s0 + a < ns && fd.src[s0 + a] == c) {
+          const long long v = warp_reduce(fd.op[s0 + a], acc[a]);
+          if (lane == 0) g_gacc[w * kAccBlock + a] = v;
+        }
+      __syncthreads();
+      if (threadIdx.x < kAccBlock && s0 + (int)threadIdx.x < ns && fd.src[s0 + threadIdx.x] == c) {
+        const int a = threadIdx.x, op = fd.op[s0 + a];
+        long long v = op_identity(op);
+        for (int ww = 0; ww < kWarps; ++ww) v = op_combine(op, v, g_gacc[ww * kAccBlock + a]);
+        sink_val(out, s0 + a, base + g, v);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Key groups of more than kLaneGroup rows (listed in s.whist): a warp each.
+template <int KS>
+__device__ void fold_big(const SortSmem& s, const FoldDesc& fd, const OutSink& out,
+                                      const long long* col, int c, long long base) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ns = fd.n_state;
+  const uint32_t* big = reinterpret_cast<const uint32_t*>(s.whist);
+  const int nbig = g_nbig;
+  for (int q = w; q < nbig; q += kWarps) {
+    const int p = (int)(big[2 * q] & 0xFFFFu), e = (int)(big[2 * q] >> 16);
+    const long long pos = base + (int)big[2 * q + 1];
+#pragma unroll
+    for (int a = 0; a < KS; ++a) {
+      if (a < ns && fd.src[a] == c) {
+        const int op = fd.op[a];
+        long long acc = op_identity(op);
+        for (int i = p + lane; i < e; i += 32) acc = op_combine(op, acc, col[s.idx[i]]);
+        acc = warp_reduce(op, acc);
+        if (lane == 0) sink_val(out, a, pos, acc);
+      }
+    }
+  }
+}
+
+// Fold the sorted chunk: heads (first rows of key groups) into a bitmask and
+// the chunk's distinct-key count -> its output offset by look-back; keys and
+// count(*) per head; then the aggregates one source column at a time, the
+// column staged in shared memory where the keys were.  A lane folds a key
+// group of at most kLaneGroup rows; a warp folds a bigger one (listed while
+// the keys are written, when the sort says that groups may be that big);
+// with at most kFewGroups groups the whole CTA folds one group at a time.
+template <int MODE, int KS, bool BIGS>
+__device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& runs, const ChunkView& cv,
+                            const FoldDesc& fd, const OutSink& out, const LookBack& lb, const Chunk& ch,
+                            int cid, long long* s_base) {
   const int n = cv.n;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1;
   const int Q = ((n + kWarps - 1) / kWarps + 31) & ~31;
   const int wb = min(n, w * Q), we = min(n, wb + Q);
-  uint32_t* hm = s.bins;  // head bitmask (the bins are done with)
-  // pass 1: heads -> bitmask, per-warp counts (warp ranges are 32-aligned)
+  uint32_t* hm = s.bins;  // head bitmask (the sort is done with the bins)
   uint16_t* hpre = reinterpret_cast<uint16_t*>(s.bins + kTileCap / 32);  // heads before each word
+  uint32_t* big = reinterpret_cast<uint32_t*>(s.whist);  // big groups: (p | e << 16, group ordinal)
+  if (BIGS && threadIdx.x == 0) g_nbig = 0;
+  // pass 1: heads -> bitmask, per-warp counts (warp ranges are 32-aligned)
   int hc = 0;
   for (int b = wb; b < we; b += 32) {
     const int p = b + lane;
@@ -693,18 +767,22 @@ __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& r
   }
   __syncthreads();
   const int count = g_lcnt[kWarps];
+  const bool few = BIGS && count <= kFewGroups;  // (without BIGS every group fits a lane)
   for (int b = wb + 32 * lane; b < we; b += 32 * 32) hpre[b >> 5] += (uint16_t)g_lcnt[w];
   const long long base = chunk_base(lb, out, cid, count, s_base);
   if (base < 0) return;
+  if (out.offs && count == 0 && threadIdx.x == 0)
+    for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
   const int ns = fd.n_state;
-  // keys and count(*) of raw rows (no column to stage)
+  // keys, count(*) of raw rows, the big-group list
   {
     int run = g_lcnt[w];
     for (int b = wb; b < we; b += 32) {
       const int p = b + lane;
       const unsigned hb = hm[b >> 5];
       if ((hb >> lane) & 1u) {
-        const long long pos = base + run + __popc(hb & lt);
+        const int g = run + __popc(hb & lt);
+        const long long pos = base + g;
         sink_key(out, pos, s.keys[s.idx[p]]);
         int e = -1;
 #pragma unroll
@@ -713,6 +791,13 @@ __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& r
             if (e < 0) e = group_end(hm, p, n);
             sink_val(out, a, pos, fd.op[a] == OP_SUM ? (long long)(e - p) : 1);
           }
+        if (few) {
+          g_gstart[g] = p;
+        } else if (BIGS && (e < 0 ? (e = group_end(hm, p, n)) : e) - p > kLaneGroup) {
+          const int q = atomicAdd(&g_nbig, 1);  // fewer than n / kLaneGroup entries
+          big[2 * q] = (unsigned)p | ((unsigned)e << 16);
+          big[2 * q + 1] = (unsigned)g;
+        }
       }
       run += __popc(hb);
     }
@@ -731,16 +816,22 @@ __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& r
       out.offs[f] = base + heads;
     }
   }
-  // aggregates, one source column at a time, staged where the keys were
+  if (few && threadIdx.x == 0) g_gstart[count] = n;
+  // aggregates, one source column at a time
   long long* col = reinterpret_cast<long long*>(s.keys);
   const int ncols = (MODE == MODE_RUNS) ? runs.ncols : src.ncols;
   for (int c = 0; c < ncols; ++c) {
     bool used = false;
     for (int a = 0; a < ns; ++a) used |= (fd.src[a] == c);
-    if (!used) continue;
-    __syncthreads();  // everyone is done with the previous contents (keys, offsets)
+    if (!used) continue;  // block-uniform
+    __syncthreads();      // everyone is done with the previous contents (keys, offsets, column)
     stage_column<MODE>(s, src, runs, cv, c, col);
     __syncthreads();
+    if (few) {
+      fold_few(s, fd, out, col, c, count, base);
+      continue;
+    }
+    // a lane per group of at most kLaneGroup rows
     int run = g_lcnt[w];
     for (int b = wb; b < we; b += 32) {
       const int p = b + lane;
@@ -748,193 +839,22 @@ __device__ void fold_lanes(const SortSmem& s, const RowSrc& src, const RunSet& r
       if ((hb >> lane) & 1u) {
         const long long pos = base + run + __popc(hb & lt);
         const int e = group_end(hm, p, n);
+        if (!BIGS || e - p <= kLaneGroup) {
 #pragma unroll
-        for (int a = 0; a < KS; ++a) {
-          if (a < ns && fd.src[a] == c) {
-            const int op = fd.op[a];
-            long long acc = col[s.idx[p]];
-            for (int q = p + 1; q < e; ++q) acc = op_combine(op, acc, col[s.idx[q]]);
-            sink_val(out, a, pos, acc);
-          }
-        }
-      }
-      run += __popc(hb);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Fold: warp ranges over sorted positions with segmented warp scans, or --
-// with few distinct keys -- the whole CTA reducing one key group at a time.
-// ---------------------------------------------------------------------------
-__shared__ int g_wcnt[kWarps + 1];
-__shared__ long long g_wtail[kWarps];
-__shared__ int g_whead[kWarps];
-__shared__ int g_gstart[kFewGroups + 1];
-__shared__ long long g_gacc[kWarps * kAccBlock];
-
-// Inclusive segmented scan across the warp: flag starts a segment.
-__device__ __forceinline__ long long warp_seg_scan(int op, bool flag, long long v) {
-  const int lane = threadIdx.x & 31;
-  unsigned fl = __ballot_sync(0xffffffffu, flag);
-  // first lane of my segment within this warp step
-  unsigned upto = fl & ((lane == 31) ? 0xffffffffu : ((2u << lane) - 1));
-  int seg_start = upto ? 31 - __clz(upto) : 0;
-  for (int o = 1; o < 32; o <<= 1) {
-    long long y = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane - o >= seg_start) v = op_combine(op, y, v);
-  }
-  return v;
-}
-
-template <int MODE>
-__device__ void fold_warps(const SortSmem& s, const RowSrc& src, const RunSet& runs, const ChunkView& cv,
-                           const FoldDesc& fd, const OutSink& out, const LookBack& lb, const Chunk& ch,
-                           int cid, long long* s_base) {
-  const int n = cv.n;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1);
-  const int Q = ((n + kWarps - 1) / kWarps + 31) & ~31;
-  const int wb = min(n, w * Q), we = min(n, wb + Q);
-  uint32_t* hm = s.bins;  // head bitmask (the sort is done with the bins)
-  // heads -> bitmask, per-warp counts (warp ranges are 32-aligned)
-  int hc = 0;
-  for (int b = wb; b < we; b += 32) {
-    const int p = b + lane;
-    const bool h = p < we && (p == 0 || s.keys[s.idx[p]] != s.keys[s.idx[p - 1]]);
-    const unsigned hb = __ballot_sync(0xffffffffu, h);
-    if (lane == 0) hm[b >> 5] = hb;
-    hc += __popc(hb);
-  }
-  if (lane == 0) g_wcnt[w] = hc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int i = 0; i < kWarps; ++i) { int c = g_wcnt[i]; g_wcnt[i] = acc; acc += c; }
-    g_wcnt[kWarps] = acc;
-  }
-  __syncthreads();
-  const int count = g_wcnt[kWarps];
-  const long long base = chunk_base(lb, out, cid, count, s_base);
-  if (base < 0) return;
-  if (out.offs && count == 0 && threadIdx.x == 0)
-    for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
-
-  // keys (and run offsets)
-  {
-    int run = g_wcnt[w];
-    for (int b = wb; b < we; b += 32) {
-      const int p = b + lane;
-      const unsigned hb = hm[b >> 5];
-      if (p < we && ((hb >> lane) & 1u)) {
-        long long g = run + __popc(hb & le) - 1;
-        unsigned long long key = s.keys[s.idx[p]];
-        if (count <= kFewGroups) g_gstart[g] = p;
-        sink_key(out, base + g, key);
-        if (out.offs) write_fine_offsets(out, ch, base, g, count, key, p > 0, p > 0 ? s.keys[s.idx[p - 1]] : 0ull);
-      }
-      run += __popc(hb);
-    }
-  }
-
-  // aggregates: one source column at a time, staged where the keys were
-  // (c = -1: count(*) of raw rows, every value 1)
-  long long* col = reinterpret_cast<long long*>(s.keys);
-  const int ncols = (MODE == MODE_RUNS) ? runs.ncols : src.ncols;
-  if (count <= kFewGroups && threadIdx.x == 0) g_gstart[count] = n;
-  for (int c = -1; c < ncols; ++c) {
-    bool used = false;
-    for (int a = 0; a < fd.n_state; ++a) used |= (fd.src[a] == c);
-    if (!used) continue;
-    __syncthreads();  // everyone is done with the keys / the previous column
-    if (c >= 0) stage_column<MODE>(s, src, runs, cv, c, col);
-    __syncthreads();
-    if (count <= kFewGroups) {
-      // few key groups: the CTA reduces one group at a time, kAccBlock
-      // aggregates per sweep
-      for (int g = 0; g < count; ++g) {
-        const int gs = g_gstart[g], ge = g_gstart[g + 1];
-        for (int s0 = 0; s0 < fd.n_state; s0 += kAccBlock) {
-          bool any = false;
-          for (int a = 0; a < kAccBlock && s0 + a < fd.n_state; ++a) any |= (fd.src[s0 + a] == c);
-          if (!any) continue;  // block-uniform
-          long long acc[kAccBlock];
-#pragma unroll
-          for (int a = 0; a < kAccBlock; ++a)
-            if (s0 + a < fd.n_state) acc[a] = op_identity(fd.op[s0 + a]);
-          for (int p = gs + threadIdx.x; p < ge; p += kThreads) {
-            const long long v = c < 0 ? 1ll : col[s.idx[p]];
-#pragma unroll
-            for (int a = 0; a < kAccBlock; ++a)
-              if (s0 + a < fd.n_state && fd.src[s0 + a] == c) acc[a] = op_combine(fd.op[s0 + a], acc[a], v);
-          }
-#pragma unroll
-          for (int a = 0; a < kAccBlock; ++a)
-            if (s0 + a < fd.n_state && fd.src[s0 + a] == c) {
-              long long v = warp_reduce(fd.op[s0 + a], acc[a]);
-              if (lane == 0) g_gacc[w * kAccBlock + a] = v;
+          for (int a = 0; a < KS; ++a) {
+            if (a < ns && fd.src[a] == c) {
+              const int op = fd.op[a];
+              long long acc = col[s.idx[p]];
+              for (int q = p + 1; q < e; ++q) acc = op_combine(op, acc, col[s.idx[q]]);
+              sink_val(out, a, pos, acc);
             }
-          __syncthreads();
-          if (threadIdx.x < kAccBlock && s0 + (int)threadIdx.x < fd.n_state && fd.src[s0 + threadIdx.x] == c) {
-            const int a = threadIdx.x, op = fd.op[s0 + a];
-            long long v = op_identity(op);
-            for (int ww = 0; ww < kWarps; ++ww) v = op_combine(op, v, g_gacc[ww * kAccBlock + a]);
-            sink_val(out, s0 + a, base + g, v);
           }
-          __syncthreads();
         }
       }
-      continue;
+      run += __popc(hb);
     }
-    for (int st = 0; st < fd.n_state; ++st) {
-      if (fd.src[st] != c) continue;  // block-uniform
-      const int op = fd.op[st];
-      // pass A: partial of the segment open at the end of this warp's range
-      long long carry = op_identity(op);
-      bool any_head = false;
-      for (int b = wb; b < we; b += 32) {
-        const int p = b + lane;
-        const bool valid = p < we;
-        const bool h = valid && head_bit(hm, p);
-        long long v = valid ? (c < 0 ? 1ll : col[s.idx[p]]) : op_identity(op);
-        const bool f = h || lane == 0;
-        if (lane == 0 && !h) v = op_combine(op, carry, v);
-        const long long x = warp_seg_scan(op, f, v);
-        carry = __shfl_sync(0xffffffffu, x, 31);
-        any_head |= __ballot_sync(0xffffffffu, h) != 0;
-      }
-      if (lane == 0) { g_wtail[w] = carry; g_whead[w] = any_head; }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        // exclusive segmented scan over warps (in place)
-        long long acc = op_identity(op);
-        for (int i = 0; i < kWarps; ++i) {
-          long long t = g_wtail[i];
-          int hh = g_whead[i];
-          g_wtail[i] = acc;
-          acc = hh ? t : op_combine(op, acc, t);
-        }
-      }
-      __syncthreads();
-      // pass B: complete segments
-      carry = g_wtail[w];
-      int run = g_wcnt[w];
-      for (int b = wb; b < we; b += 32) {
-        const int p = b + lane;
-        const bool valid = p < we;
-        const bool h = valid && head_bit(hm, p);
-        long long v = valid ? (c < 0 ? 1ll : col[s.idx[p]]) : op_identity(op);
-        const bool f = h || lane == 0;
-        if (lane == 0 && !h) v = op_combine(op, carry, v);
-        const long long x = warp_seg_scan(op, f, v);
-        const unsigned hb = __ballot_sync(0xffffffffu, h);
-        const bool ends = valid && (p + 1 >= n || head_bit(hm, p + 1));
-        if (ends) sink_val(out, st, base + run + __popc(hb & le) - 1, x);
-        run += __popc(hb);
-        carry = __shfl_sync(0xffffffffu, x, 31);
-      }
-      __syncthreads();
-    }
+    // a warp per bigger group
+    if (BIGS) fold_big<KS>(s, fd, out, col, c, base);
   }
 }
 
@@ -1055,7 +975,7 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
   }
   load_keys<MODE>(s, src, runs, cv);
   __syncthreads();
-  const int how = chunk_sort(s, cv.n);
+  const bool bigs = chunk_sort(s, cv.n);
   if (MODE == MODE_INST && is.kmin && threadIdx.x == 0 && cv.n > 0) {
     // key range of the instance (its tiles' sorted ends), for the digit
     // that partitions the partial rows
@@ -1063,8 +983,8 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
     atomicMin(is.kmin + ch.pad, s.keys[s.idx[0]] & m);
     atomicMax(is.kmax + ch.pad, s.keys[s.idx[cv.n - 1]] & m);
   }
-  if (how == FOLD_BINS) fold_lanes<MODE, KS>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
-  else fold_warps<MODE>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
+  if (bigs) fold_sorted<MODE, KS, true>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
+  else fold_sorted<MODE, KS, false>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
 }
 
 }  // namespace sg
