@@ -16,7 +16,7 @@ compulsory bytes per launch / its average CUDA-event duration, against the
 measured HBM copy bandwidth.  `cpu_baseline` = the CPU oracle (sort + fold,
 one thread) on a bounded sample of the same workload.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c3|c2|c1]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c3|c2|c1|c4|c5]
   python bench.py --impl reference     # the oracle arm (CPU, bounded samples)
 """
 import argparse
@@ -47,6 +47,9 @@ WORKLOADS = {
     "c4": dict(desc="batched: 4,096 independent instances, rows log-uniform 1K-4M, uint32 keys Zipf(1.1) "
                     "over a per-instance domain log-uniform 16-1M, 1 int64 payload, count/sum/min/max",
                n=4096),
+    "c5": dict(desc="serving: Poisson stream of 10,000 requests, rows log-uniform 1K-16M, distinct/rows "
+                    "log-uniform 0.001-1, uint64 keys, 2 int64 payloads, count + sum/min/max x2, M = 2^22, "
+                    "device admission budget 64 GB", n=10_000),
     "c3": dict(desc="512M rows, uint64 keys uniform over 2^28 values, 1 int64 payload, count/sum, "
                     "memory budget 2^25 rows (16 runs + wide merge)",
                n=1 << 29, D=1 << 28, M=1 << 25),
@@ -290,6 +293,121 @@ def bench_batched(args, dev):
     return 0
 
 
+def run_stream(srv_kw, specs, rate, dev, aggs, budget, pool):
+    """Replay requests arriving at `rate` per second (Poisson; inf: all at
+    once) into a server; each request's inputs are cut from device pools
+    when it arrives (two kernels).  Returns per-request latency (ms), rows,
+    makespan (s)."""
+    import torch
+    import datagen
+    from paper_2010_00152_gb300 import sgagg
+    srv = sgagg.Server(aggs, **srv_kw)
+    gen = torch.cuda.Stream(dev)
+    t0 = sgagg.sgagg_server_now_ns() + 50_000_000
+    arrive = [t0 + int(sp["arrival"] / rate * 1e9) if rate != float("inf") else t0 for sp in specs]
+    live, lat, done_ns, rows, held = {}, [], [], 0, 0
+
+    def reap(block):
+        nonlocal held
+        for t in list(live):
+            r = srv.wait(t) if block else srv.poll(t)
+            if r is None:
+                continue
+            i, nbytes = live.pop(t)
+            held -= nbytes
+            assert r["status"] == 0, r
+            lat.append((r["done_ns"] - arrive[i]) / 1e6)
+            done_ns.append(r["done_ns"])
+
+    try:
+        for i, sp in enumerate(specs):
+            while sgagg.sgagg_server_now_ns() < arrive[i]:
+                reap(False)
+                time.sleep(0.0002)
+            n = sp["rows"]
+            nbytes = n * 24 + min(n, sp["D"]) * 64
+            while held + nbytes > budget and live:  # the client's own inputs stay within the budget
+                reap(False)
+                time.sleep(0.0002)
+            with torch.cuda.stream(gen):
+                c = datagen.config5_pooled_request(pool, sp)
+                ev = torch.cuda.Event()
+                ev.record(gen)
+            t = srv.submit(c["key_cols"][0], c["payload"], capacity=max(1, min(n, sp["D"])), ready=ev)
+            live[t] = (i, nbytes)
+            held += nbytes
+            rows += n
+            reap(False)
+        reap(True)
+    finally:
+        srv.close()
+    return lat, rows, (max(done_ns) - t0) / 1e9
+
+
+def bench_serving(args, dev):
+    """Config 5: the request loop (slots, admission, continuous batching)
+    against the plain form (one call per request, one after another) on the
+    same Poisson stream, at offered loads 0.5, 0.8 and 1.0 x the plain
+    form's measured capacity."""
+    import numpy as np
+    import torch
+    import datagen
+    from paper_2010_00152_gb300 import sgagg
+    count = args.requests or WORKLOADS["c5"]["n"]
+    specs = datagen.config5_requests(count=count, seed=1)
+    aggs = [(0, 0), (1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (3, 1)]
+    budget = 64 << 30
+    M = 1 << 22
+    plain = dict(slots=1, device_budget_bytes=budget, memory_budget_rows=M, small_rows=0, max_batch=1,
+                 max_batch_rows=1)
+    served = dict(slots=8, device_budget_bytes=budget, memory_budget_rows=M, small_rows=1 << 16, max_batch=128,
+                  max_batch_rows=1 << 22)
+    # warm both forms (allocations, module load)
+    pool = datagen.config5_pool(device=dev, seed=1)
+    run_stream(plain, specs[:20], float("inf"), dev, aggs, budget // 2, pool)
+    run_stream(served, specs[:20], float("inf"), dev, aggs, budget // 2, pool)
+    # capacity: the first cap_n requests generated beforehand, submitted at
+    # once, all results waited for (closed loop, no client in the way)
+    cap_n = min(count, args.capacity_requests)
+    pre = [datagen.config5_pooled_request(pool, sp) for sp in specs[:cap_n]]
+    torch.cuda.synchronize()
+    cap = {}
+    for name, kw in (("plain", plain), ("served", served)):
+        srv = sgagg.Server(aggs, **kw)
+        t0 = sgagg.sgagg_server_now_ns()
+        ts = [srv.submit(c["key_cols"][0], c["payload"], capacity=max(1, min(sp["rows"], sp["D"])))
+              for c, sp in zip(pre, specs)]
+        res = [srv.wait(t) for t in ts]
+        span = (max(r["done_ns"] for r in res) - t0) / 1e9
+        srv.close()
+        assert all(r["status"] == 0 for r in res)
+        cap[name] = {"requests_per_s": cap_n / span, "rows_per_s": sum(sp["rows"] for sp in specs[:cap_n]) / span}
+    del pre
+    plain_rps = cap["plain"]["requests_per_s"]
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    loads = []
+    for f in (0.5, 0.8, 1.0, 1.5):
+        entry = {"load": f, "rate_rps": round(f * plain_rps, 2)}
+        for name, kw in (("plain", plain), ("served", served)):
+            lat, rows, span = run_stream(kw, specs, f * plain_rps, dev, aggs, budget // 2, pool)
+            entry[name] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                           "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                           "rows_per_s": rows / span, "requests_per_s": len(lat) / span, "makespan_s": span}
+        loads.append(entry)
+    clk = clocks.stop()
+    line = {"metric": "served rows/s (p50/p99 latency vs plain)", "value": cap["served"]["rows_per_s"],
+            "unit": "rows/s", "n_gpus": 1, "steps": len(loads), "warmup": 2, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOADS["c5"]["desc"], "requests": count, "served": served, "plain": plain},
+            "capacity": cap, "capacity_requests": cap_n, "loads": loads, "clocks": clk,
+            "note": "value = served capacity (rows/s, closed loop over the first capacity_requests requests); "
+                    "loads = open-loop Poisson replays of all requests at the given multiple of the plain "
+                    "form's capacity, latency from scheduled arrival to results final"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,6 +420,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--instances", type=int, default=None, help="c4: instance count")
+    ap.add_argument("--requests", type=int, default=None, help="c5: request count")
+    ap.add_argument("--capacity-requests", type=int, default=1000,
+                    help="c5: requests run back to back to measure the plain form's capacity")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -323,6 +444,8 @@ def main():
     name = args.config
     if name == "c4":
         return bench_batched(args, dev)
+    if name == "c5":
+        return bench_serving(args, dev)
     w = make_workload(name, dev, args.rows)
     n = int(w["key_cols"][0].numel())
     M = int(w["M"])

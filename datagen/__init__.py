@@ -195,6 +195,32 @@ def config5_requests(count=10_000, seed=1, lo=1 << 10, hi=1 << 24, rate=None):
             for r, d, s, a in zip(rows, dom, seeds, arr)]
 
 
+def config5_pool(device="cpu", seed=1, rows=1 << 24):
+    """Device-resident pools from which config5_pooled_request cuts requests
+    with two kernels each, for replaying a request stream faster than the
+    GPU serves it: T = mix64(0 .. rows-1) (the key values), R = uniform
+    draws, P0 / P1 = payloads of the config-5 ranges.  Slots of R beyond
+    `rows` wrap, so any request of up to `rows` rows fits."""
+    return dict(rows=rows, T=mix64(torch.arange(rows, dtype=torch.int64, device=device)),
+                R=_shr(rand64(seed, 7, 2 * rows, device), 1),
+                P0=uniform_int(seed, 8, 2 * rows, -1000, 1000, device),
+                P1=uniform_int(seed, 9, 2 * rows, 0, 10**7 - 1, device))
+
+
+def config5_pooled_request(pool, req):
+    """A config-5 request from the pools: keys uniform over D = req["D"]
+    mix64-spread values (T[R mod D]), payloads as in config5_request; the
+    request's seed picks where in the pools its rows start."""
+    n, D, seed = req["rows"], req["D"], req["seed"]
+    assert n <= pool["rows"] and D <= pool["rows"]
+    o = seed % pool["rows"]
+    k = pool["T"][torch.remainder(pool["R"][o:o + n], D)]
+    p0 = pool["P0"][o:o + n]
+    p1 = pool["P1"][(o + 12345) % pool["rows"]:(o + 12345) % pool["rows"] + n]
+    aggs = [(COUNT, 0), (SUM, 0), (MIN, 0), (MAX, 0), (SUM, 1), (MIN, 1), (MAX, 1)]
+    return dict(key_cols=[as_u64(k)], payload=[p0, p1], aggs=aggs, M=1 << 22)
+
+
 def config5_request(req, device="cpu", M=1 << 22):
     n, D, seed = req["rows"], req["D"], req["seed"]
     k = keys_uniform_over(seed, 1, n, D, device)

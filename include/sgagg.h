@@ -212,11 +212,27 @@ typedef struct {
 } sgagg_instance;
 
 /*
- * Run `count` independent instances (sharing one aggregate spec) with one
- * persistent kernel launch per size class, captured once in a CUDA graph per
- * (count, spec) shape and replayed.  `inst` is a host array.  Asynchronous:
- * results are final when the stream reaches this point; sgagg_result_rows
- * returns the total of all instances' rows and any device-side error.
+ * Run `count` independent instances sharing one aggregate spec as one
+ * grouping.  Instances of at most 8192 rows (one chunk) run in one launch,
+ * a CTA each, sorted, folded and written straight to their own outputs,
+ * whatever their key width.  The bigger ones are grouped together over a
+ * composite normalized key (instance id above the key bits; Sec. 2.4 on
+ * normalized keys): one launch pre-aggregates
+ * instance-aligned tiles of every instance, the partial rows are grouped by
+ * the ordinary path with partition buckets given to each instance in
+ * proportion to its rows over its own key range, and one launch copies each
+ * instance's rows (contiguous in the sorted output) to its outputs.  The
+ * launch count does not depend on `count`: instances are taken in groups of
+ * consecutive instances of up to 2^25 rows, about a dozen launches per
+ * group.  When the widest key of the bigger instances plus ceil(log2(count))
+ * bits exceeds 64, they run one by one through sgagg_aggregate instead.
+ *
+ * `inst` is a host array; the memory budget of the handle does not apply
+ * (each instance is one batch, no runs).  The call synchronizes the stream
+ * between groups; results are final when sgagg_result_rows returns, which
+ * gives the total of all instances' rows.  An instance whose distinct keys
+ * exceed its out_capacity gets *out_rows = -1 and nothing written; the
+ * others are unaffected.
  */
 sgagg_status sgagg_aggregate_batched(sgagg_t h, const sgagg_instance *inst, int32_t count,
                                      const sgagg_spec *spec, void *stream);
@@ -252,6 +268,115 @@ sgagg_status sgagg_aggregate_noalloc(const sgagg_keys *keys, const int64_t *cons
                                      int32_t n_payload, int64_t n, const sgagg_spec *spec,
                                      void *const *out_keys, int64_t *const *out_aggs,
                                      int64_t out_capacity, int64_t *out_rows, void *stream);
+
+/*
+ * Serving: a request loop over a pool of handles ("slots", one CUDA stream
+ * and one host worker thread each).  The paper has no counterpart; this is
+ * the system pattern built on the calls above.
+ *
+ *   - Requests are admitted in arrival (submit) order, never overtaking:
+ *     the oldest waiting request starts as soon as a slot is free and its
+ *     footprint fits what is left of device_budget_bytes.
+ *   - Footprint of a request (sgagg_request_footprint): its input and
+ *     output bytes plus a bound on the workspace and runs the path allocates
+ *     for it.  A request whose footprint alone exceeds the budget is refused
+ *     at submit with SGAGG_ECAPACITY, never queued.
+ *   - Continuous batching: a request is batchable when it has at most
+ *     small_rows rows and the batched call takes it in one pass (at most 8192
+ *     rows, or keys of at most 4 bytes).  When the oldest waiting request is
+ *     batchable, it and the batchable requests queued right behind it (up to
+ *     max_batch requests and max_batch_rows rows, within the budget) run as
+ *     one sgagg_aggregate_batched call.  Requests that arrive while others
+ *     are on the GPU join the next batch; batches and large requests on
+ *     different slots overlap on the device.
+ *   - A large request runs alone through sgagg_aggregate on its slot.
+ *   - slots = 1 with small_rows = 0 is the plain form: one query per call,
+ *     one after another.
+ *
+ * Every request uses the server's aggregate spec and memory budget.  The
+ * caller owns the request's device buffers and must keep them alive until
+ * sgagg_server_wait (or a poll that reports it done) returns for it.
+ */
+typedef struct sgagg_server *sgagg_server_t;
+
+typedef struct {
+    int32_t slots;                /* >= 1 */
+    int64_t device_budget_bytes;  /* admission budget over all requests in flight */
+    int64_t memory_budget_rows;   /* M of every request (sgagg_create) */
+    int64_t small_rows;           /* batch requests of at most this many rows; 0 = never */
+    int32_t max_batch;            /* most requests in one batched call (>= 1) */
+    int64_t max_batch_rows;       /* most rows in one batched call */
+} sgagg_server_config;
+
+typedef struct {
+    const void *keys;               /* device, key_bytes per row */
+    int32_t key_bytes;              /* 1, 2, 4 or 8 */
+    int32_t n_payload;
+    const int64_t *const *payload;  /* host array of n_payload device pointers */
+    int64_t n;
+    void *out_keys;                 /* device, out_capacity rows */
+    int64_t *const *out_aggs;       /* host array of n_aggs device pointers */
+    int64_t out_capacity;
+    void *ready;                    /* cudaEvent_t or NULL: inputs are complete when it
+                                       has fired (the slot's stream waits for it) */
+} sgagg_request;
+
+typedef struct {
+    int32_t status;       /* sgagg_status of the request */
+    int32_t slot;         /* slot that ran it (-1: refused) */
+    int64_t rows;         /* distinct keys (-1 when status != SGAGG_OK) */
+    int64_t submit_ns;    /* sgagg_server_now_ns() at submit */
+    int64_t start_ns;     /* at admission */
+    int64_t done_ns;      /* when its results were final */
+    int32_t batch_size;   /* requests in the call that ran it (1 = alone) */
+    int32_t pad;
+} sgagg_request_result;
+
+/* Footprint of a request as charged by admission, in bytes: input + output
+ * bytes + 8 * m * (3 + 3C + 3(1 + S)) (workspace of one batch of
+ * m = min(n, M) rows, C = payload columns, S = aggregates) + 8 * n * (1 + S)
+ * when n > M (the runs) + 64 MiB. */
+int64_t sgagg_request_footprint(int64_t n, int32_t key_bytes, int32_t n_payload, int32_t n_aggs,
+                                int64_t out_capacity, int64_t memory_budget_rows);
+
+/* The server's clock (monotonic, nanoseconds). */
+int64_t sgagg_server_now_ns(void);
+
+/* Start a server: cfg->slots handles and streams on the current device, one
+ * worker thread each.  `spec` is copied. */
+sgagg_status sgagg_server_create(const sgagg_server_config *cfg, const sgagg_spec *spec,
+                                 sgagg_server_t *out);
+
+/* Queue a request; *ticket identifies it.  Arrays of pointers in `req` are
+ * copied before the call returns.  Refused (SGAGG_ECAPACITY) when its
+ * footprint exceeds the budget; SGAGG_EINVAL on bad arguments. */
+sgagg_status sgagg_server_submit(sgagg_server_t s, const sgagg_request *req, int64_t *ticket);
+
+/* Block until the request is done; fill *out.  Each ticket can be waited
+ * for (or polled to completion) once. */
+sgagg_status sgagg_server_wait(sgagg_server_t s, int64_t ticket, sgagg_request_result *out);
+
+/* Non-blocking: *done = 1 and *out filled when the request is done. */
+sgagg_status sgagg_server_poll(sgagg_server_t s, int64_t ticket, int32_t *done, sgagg_request_result *out);
+
+/* Finish every queued request, stop the workers, free the slots. */
+void sgagg_server_destroy(sgagg_server_t s);
+
+/*
+ * The admission and batching decisions of the server, run on the host
+ * against a cost model instead of the GPU (virtual time): request i of
+ * rows[i] rows and 8-byte keys (footprint from sgagg_request_footprint with key_bytes 8,
+ * n_payload payload columns, n_aggs aggregates and out_capacity rows[i])
+ * arrives at arrive_us[i]; a call of r rows over b requests takes
+ * cost_us[0] + cost_us[1] * r + cost_us[2] * b microseconds.  Writes, per
+ * request, its start and finish time (us), slot, and batch id (requests
+ * run by one call share it; -1 when refused).  For tests of the scheduler
+ * without a GPU.
+ */
+sgagg_status sgagg_server_simulate(const sgagg_server_config *cfg, int32_t n_payload, int32_t n_aggs,
+                                   int32_t count, const int64_t *rows, const double *arrive_us,
+                                   const double *cost_us, double *start_us, double *finish_us,
+                                   int32_t *slot, int32_t *batch);
 
 /* Free the handle and everything it owns.  NULL is ignored. */
 void sgagg_destroy(sgagg_t h);

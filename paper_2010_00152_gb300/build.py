@@ -1,8 +1,9 @@
 """Build the CUDA library (libsgagg.so) in-tree for sm_103a.
 
-One translation unit, compiled with nvcc for compute_103a / sm_103a only.  The
-library links the CUDA runtime statically so that the ctypes binding needs no
-other shared objects.
+Two translation units (the grouping path, and the serving runtime over its C
+ABI), compiled with nvcc for compute_103a / sm_103a only.  The library links
+the CUDA runtime statically so that the ctypes binding needs no other shared
+objects.
 """
 import os
 import shutil
@@ -13,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsgagg.so")
-SOURCES = [os.path.join(CSRC, "sgagg.cu")]
+SOURCES = [os.path.join(CSRC, "sgagg.cu"), os.path.join(CSRC, "sg_server.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + \
     [os.path.join(ROOT, "include", "sgagg.h")]
 
@@ -27,7 +28,7 @@ def nvcc():
 
 def flags(extra=()):
     return ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
-            "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr", "-cudart", "static",
+            "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr", "-cudart", "static", "-lpthread",
             "-I", os.path.join(ROOT, "include"), *extra]
 
 

@@ -653,10 +653,11 @@ inline size_t staged_smem_bytes(int nb, int ncols) {
 // whose keys carry the instance id above key_bits and come grouped by
 // instance in ascending order (sorted within an instance's rows or not).
 // With write_rows (the grouped output, step 1 of the batched output), each
-// instance's *out_rows = its row count, or -1 when that exceeds its
-// out_capacity (then nothing is written for it).
+// instance of more than skip_n rows gets *out_rows = its row count, or -1
+// when that exceeds its out_capacity (then nothing is written for it).
 __global__ void k_inst_bounds(const unsigned long long* keys, long long total, const InstDesc* inst,
-                              int key_bits, int first, int count, long long* start, int write_rows) {
+                              int key_bits, int first, int count, long long* start, int write_rows,
+                              long long skip_n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j > count) return;
   auto lower = [&](int i) {
@@ -670,7 +671,7 @@ __global__ void k_inst_bounds(const unsigned long long* keys, long long total, c
   };
   const long long a = lower(first + j);
   start[j] = a;
-  if (write_rows && j < count) {
+  if (write_rows && j < count && inst[first + j].n > skip_n) {
     const long long rows = lower(first + j + 1) - a;
     *inst[first + j].out_rows = rows > inst[first + j].out_capacity ? -1 : rows;
   }

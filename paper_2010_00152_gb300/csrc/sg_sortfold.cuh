@@ -33,7 +33,7 @@ constexpr int kFewGroups = 16;             // CTA-per-group fold below this many
 constexpr int kAccBlock = 8;               // state columns folded per pass
 
 enum : int { CH_NORMAL = 0, CH_COPY = 1 };
-enum : int { MODE_RANGE = 0, MODE_RUNS = 1, MODE_TILES = 2, MODE_INST = 3 };
+enum : int { MODE_RANGE = 0, MODE_RUNS = 1, MODE_TILES = 2, MODE_INST = 3, MODE_DIRECT = 4 };
 
 // One instance of a batched call (same layout as sgagg_instance).
 struct InstDesc {
@@ -89,6 +89,8 @@ struct OutSink {
   long long capacity;               // rows writable (absolute positions < capacity)
   long long* offs;                  // fine-bucket offsets of the run written, or null
   Digit dig;
+  long long* rows_out;              // MODE_DIRECT: the instance's row count (-1: over capacity)
+  unsigned long long* rows_sum;     // MODE_DIRECT: rows of all instances (added), or null
 };
 
 struct SortSmem {
@@ -583,6 +585,20 @@ __device__ __forceinline__ void sink_val(const OutSink& out, int st, long long p
   if (pos < out.capacity) out.cols[st][pos] = v;
 }
 
+// MODE_DIRECT: the chunk is a whole instance with outputs of its own: base
+// 0, and the instance's row count (or -1 when it exceeds out_capacity; then
+// nothing is written and the other instances go on).
+__device__ __forceinline__ long long direct_base(const OutSink& out, long long count, long long* s_base) {
+  if (threadIdx.x == 0) {
+    const bool fits = count <= out.capacity;
+    *out.rows_out = fits ? count : -1;
+    if (fits && out.rows_sum) atomicAdd(out.rows_sum, (unsigned long long)count);
+    *s_base = fits ? 0 : -1;
+  }
+  __syncthreads();
+  return *s_base;
+}
+
 // Publishes `count` for the chunk and returns its base (or -1: stop).
 __device__ __forceinline__ long long chunk_base(const LookBack& lb, const OutSink& out, int cid,
                                                 long long count, long long* s_base) {
@@ -769,7 +785,8 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
   const int count = g_lcnt[kWarps];
   const bool few = BIGS && count <= kFewGroups;  // (without BIGS every group fits a lane)
   for (int b = wb + 32 * lane; b < we; b += 32 * 32) hpre[b >> 5] += (uint16_t)g_lcnt[w];
-  const long long base = chunk_base(lb, out, cid, count, s_base);
+  const long long base =
+      MODE == MODE_DIRECT ? direct_base(out, count, s_base) : chunk_base(lb, out, cid, count, s_base);
   if (base < 0) return;
   if (out.offs && count == 0 && threadIdx.x == 0)
     for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
@@ -867,7 +884,8 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
            OutSink out, LookBack lb, long long tile_n, int tile_f_hi, InstSet is) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem s = carve(smem_raw);
-  __shared__ RowSrc s_src;  // MODE_INST: the chunk's instance as a source
+  __shared__ RowSrc s_src;   // MODE_INST / MODE_DIRECT: the chunk's instance as a source
+  __shared__ OutSink s_out;  // MODE_DIRECT: the instance's outputs
   __shared__ int s_cid;
   __shared__ int s_err;
   __shared__ long long s_base;
@@ -889,7 +907,7 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
   } else {
     ch = chunks[cid];
   }
-  if (MODE == MODE_INST) {
+  if (MODE == MODE_INST || MODE == MODE_DIRECT) {
     if (threadIdx.x == 0) {
       const InstDesc d = is.inst[ch.pad];
       s_src = src_param;
@@ -899,12 +917,26 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
       s_src.key.bytes[0] = d.key_bytes;
       s_src.key.shift[0] = 0;
       s_src.key.cols[0] = d.keys;
-      s_src.key_or = (unsigned long long)ch.pad << is.key_bits;
+      s_src.key_or = MODE == MODE_INST ? (unsigned long long)ch.pad << is.key_bits : 0ull;
       for (int c = 0; c < src_param.ncols; ++c) s_src.cols[c] = d.payload[is.colsel[c]];
+      if (MODE == MODE_DIRECT) {
+        // the instance's own outputs, its key width
+        s_out = out;
+        s_out.user = 1;
+        s_out.kout.n_cols = 1;
+        s_out.kout.bytes[0] = d.key_bytes;
+        s_out.kout.shift[0] = 0;
+        s_out.kout.cols[0] = d.out_keys;
+        for (int a = 0; a < fd.n_state; ++a) s_out.cols[a] = d.out_aggs[a];
+        s_out.capacity = d.out_capacity;
+        s_out.offs = nullptr;
+        s_out.rows_out = d.out_rows;
+      }
     }
     __syncthreads();
   }
-  const RowSrc& src = (MODE == MODE_INST) ? s_src : src_param;
+  const RowSrc& src = (MODE == MODE_INST || MODE == MODE_DIRECT) ? s_src : src_param;
+  const OutSink& dst = (MODE == MODE_DIRECT) ? s_out : out;
 
   if (ch.kind == CH_COPY) {
     const long long n = ch.hi - ch.lo;
@@ -983,8 +1015,8 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
     atomicMin(is.kmin + ch.pad, s.keys[s.idx[0]] & m);
     atomicMax(is.kmax + ch.pad, s.keys[s.idx[cv.n - 1]] & m);
   }
-  if (bigs) fold_sorted<MODE, KS, true>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
-  else fold_sorted<MODE, KS, false>(s, src, runs, cv, fd, out, lb, ch, cid, &s_base);
+  if (bigs) fold_sorted<MODE, KS, true>(s, src, runs, cv, fd, dst, lb, ch, cid, &s_base);
+  else fold_sorted<MODE, KS, false>(s, src, runs, cv, fd, dst, lb, ch, cid, &s_base);
 }
 
 }  // namespace sg

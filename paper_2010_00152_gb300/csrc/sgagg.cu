@@ -114,6 +114,7 @@ struct sgagg_ctx {
   DevBuf runstarts;              // batches + 1 device scalars
   DevBuf binst, bchunks, bkeys, bout_keys;   // batched call: instances, tiles, partial rows, output
   DevBuf bseg, brange, bstartb;              // batched call: segmented digit, key ranges, row starts
+  DevBuf bdirect;                            // batched call: chunks of the one-chunk instances
   std::vector<DevBuf> bcols, bout_cols;
   DevBuf marena_keys;            // runs written by preliminary merges
   std::vector<DevBuf> marena_cols;
@@ -156,6 +157,7 @@ struct Small {
   PlanInfo info;
   long long total;              // total_out of the final sort+fold
   long long pftot;              // total_out of a pre-fold pass
+  long long dsum;               // rows of the one-chunk instances of a batched call
   long long dtot[kMaxDepth + 2];  // base/total of the sub-solves under depth d
 };
 
@@ -1254,7 +1256,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
   if (count < 0 || (count > 0 && !inst) || !spec) return fail(h, SGAGG_EINVAL, "bad batched arguments");
   if (spec->n_aggs < 0 || spec->n_aggs > kMaxCols || (spec->n_aggs > 0 && !spec->aggs))
     return fail(h, SGAGG_EINVAL, "bad aggregate spec");
-  int maxkb = 1, maxcol = -1;
+  int maxkb = 1, maxcol = -1, bigkb = 1;  // bigkb: widest key of the instances above one chunk
   long long total = 0;
   for (int i = 0; i < count; ++i) {
     const sgagg_instance& d = inst[i];
@@ -1264,6 +1266,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
     if (d.n > 0 && !d.keys) return fail(h, SGAGG_EINVAL, "null instance keys");
     if (d.n_payload < 0 || d.n_payload > 1024) return fail(h, SGAGG_EINVAL, "bad instance payload count");
     maxkb = std::max(maxkb, kb);
+    if (d.n > kTileCap) bigkb = std::max(bigkb, kb);
     total += d.n;
   }
   for (int a = 0; a < spec->n_aggs; ++a) {
@@ -1278,7 +1281,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
     if (maxcol >= inst[i].n_payload || (maxcol >= 0 && inst[i].n > 0 && !inst[i].payload))
       return fail(h, SGAGG_EINVAL, "aggregate column out of range for an instance");
   const int S = spec->n_aggs;
-  const int key_bits = 8 * maxkb;
+  const int key_bits = 8 * bigkb;  // one-chunk instances never use the composite key
   const int inst_bits = std::max(1, ilog2_ceil(std::max(1, count)));  // >= 1: key_bits stays below 64
   h->stream = stream;
   h->have_call = true;
@@ -1296,48 +1299,6 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
   HostSmall* hs = hsmall(h);
   CU(cudaMemsetAsync(ds, 0, sizeof(Small), stream));
   if (count == 0) return SGAGG_OK;
-
-  if (key_bits + inst_bits > 64) {
-    // composite key too wide: one instance at a time through the ordinary
-    // path; the counters of the calls are summed
-    long long rows_all = 0;
-    sgagg_stats_t acc{};
-    for (int i = 0; i < count; ++i) {
-      const sgagg_instance& d = inst[i];
-      std::vector<const int64_t*> pay(std::max(1, d.n_payload), nullptr);
-      std::vector<int64_t*> oa(std::max(1, S), nullptr);
-      if (d.n_payload > 0) CU(cudaMemcpy(pay.data(), d.payload, (size_t)d.n_payload * 8, cudaMemcpyDeviceToHost));
-      if (S > 0) CU(cudaMemcpy(oa.data(), d.out_aggs, (size_t)S * 8, cudaMemcpyDeviceToHost));
-      int32_t kb = d.key_bytes;
-      const void* kc = d.keys;
-      sgagg_keys k{1, &kb, &kc};
-      void* ok = d.out_keys;
-      sgagg_status st = aggregate_device(h, &k, pay.data(), d.n_payload, d.n, spec, &ok, oa.data(),
-                                         d.out_capacity, stream);
-      long long r = st == SGAGG_OK ? h->last_rows : -1;
-      if (st != SGAGG_OK && st != SGAGG_ECAPACITY) return st;
-      CU(cudaMemcpyAsync(d.out_rows, &r, 8, cudaMemcpyHostToDevice, stream));
-      CU(cudaStreamSynchronize(stream));
-      rows_all += std::max(0ll, r);
-      read_timers(h);
-      const sgagg_stats_t& c = h->st;
-      acc.batches += c.batches; acc.runs += c.runs; acc.run_rows += c.run_rows;
-      acc.run_bytes_device += c.run_bytes_device; acc.run_bytes_host += c.run_bytes_host;
-      acc.out_rows += c.out_rows; acc.prefold_passes += c.prefold_passes;
-      acc.split_segments += c.split_segments; acc.merge_tiles += c.merge_tiles;
-      acc.kernel_launches += c.kernel_launches;
-      for (int k = 0; k < 8; ++k) {
-        acc.class_launches[k] += c.class_launches[k];
-        acc.class_bytes[k] += c.class_bytes[k];
-        acc.class_ms[k] += c.class_ms[k];
-      }
-    }
-    acc.n_rows = total;
-    h->st = acc;
-    h->key_bytes = maxkb;
-    h->last_rows = rows_all;
-    return SGAGG_OK;
-  }
 
   // instance table (all instances); groups of consecutive instances of at
   // most kBatchGroupRows rows bound the scratch
@@ -1385,14 +1346,95 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
   raw.ncols = C;
   const FoldDesc fid = identity_fold(fd);
   long long rows_all = 0;
+
+  // 1. instances of at most one chunk: one launch, a CTA each, written
+  //    straight to their own outputs (any key width)
+  {
+    std::vector<Chunk> dch;
+    for (int i = 0; i < count; ++i)
+      if (inst[i].n <= kTileCap) {
+        Chunk c{};
+        c.lo = 0;
+        c.hi = inst[i].n;
+        c.kind = CH_NORMAL;
+        c.pad = i;
+        dch.push_back(c);
+      }
+    if (!dch.empty()) {
+      TRY(grow(h, h->bdirect, dch.size() * sizeof(Chunk)));
+      CU(cudaMemcpyAsync(h->bdirect.p, dch.data(), dch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, stream));
+      OutSink o{};
+      o.rows_sum = reinterpret_cast<unsigned long long*>(&ds->dsum);
+      RunSet norun{};
+      CopySrc nocopy{};
+      TRY(launch_sortfold<MODE_DIRECT>(h, SGAGG_K_RUNGEN, P<Chunk>(h->bdirect), (int)dch.size(), 0, raw, norun,
+                                       nocopy, fd, o, nullptr, nullptr, 0, is));
+      long long dn = 0;
+      for (const Chunk& c : dch) dn += c.hi;
+      kbytes(h, SGAGG_K_RUNGEN, dn * (maxkb + 8ll * C));
+      TRY(sync_read(h, &hs->v[2], &ds->dsum, 8));
+      TRY(check_device_err(h));
+      rows_all += hs->v[2];
+      kbytes(h, SGAGG_K_RUNGEN, hs->v[2] * (maxkb + 8ll * S));
+    }
+  }
+  if (key_bits + inst_bits > 64) {
+    // composite key too wide: the bigger instances one at a time through
+    // the ordinary path; the counters of the calls are added
+    read_timers(h);
+    sgagg_stats_t acc = h->st;
+    for (int i = 0; i < count; ++i) {
+      const sgagg_instance& d = inst[i];
+      if (d.n <= kTileCap) continue;
+      std::vector<const int64_t*> pay(std::max(1, d.n_payload), nullptr);
+      std::vector<int64_t*> oa(std::max(1, S), nullptr);
+      if (d.n_payload > 0) CU(cudaMemcpy(pay.data(), d.payload, (size_t)d.n_payload * 8, cudaMemcpyDeviceToHost));
+      if (S > 0) CU(cudaMemcpy(oa.data(), d.out_aggs, (size_t)S * 8, cudaMemcpyDeviceToHost));
+      int32_t kb = d.key_bytes;
+      const void* kc = d.keys;
+      sgagg_keys k{1, &kb, &kc};
+      void* ok = d.out_keys;
+      sgagg_status st = aggregate_device(h, &k, pay.data(), d.n_payload, d.n, spec, &ok, oa.data(),
+                                         d.out_capacity, stream);
+      long long r = st == SGAGG_OK ? h->last_rows : -1;
+      if (st != SGAGG_OK && st != SGAGG_ECAPACITY) return st;
+      CU(cudaMemcpyAsync(d.out_rows, &r, 8, cudaMemcpyHostToDevice, stream));
+      CU(cudaStreamSynchronize(stream));
+      rows_all += std::max(0ll, r);
+      read_timers(h);
+      const sgagg_stats_t& c = h->st;
+      acc.batches += c.batches; acc.runs += c.runs; acc.run_rows += c.run_rows;
+      acc.run_bytes_device += c.run_bytes_device; acc.run_bytes_host += c.run_bytes_host;
+      acc.out_rows += c.out_rows; acc.prefold_passes += c.prefold_passes;
+      acc.split_segments += c.split_segments; acc.merge_tiles += c.merge_tiles;
+      acc.kernel_launches += c.kernel_launches;
+      for (int k = 0; k < 8; ++k) {
+        acc.class_launches[k] += c.class_launches[k];
+        acc.class_bytes[k] += c.class_bytes[k];
+        acc.class_ms[k] += c.class_ms[k];
+      }
+    }
+    acc.n_rows = total;
+    acc.out_rows = rows_all;
+    h->st = acc;
+    h->key_bytes = maxkb;
+    h->last_rows = rows_all;
+    return SGAGG_OK;
+  }
+
   int i0 = 0;
   while (i0 < count) {
     int i1 = i0;
     long long grows = 0;
-    while (i1 < count && (i1 == i0 || grows + inst[i1].n <= kBatchGroupRows)) grows += inst[i1++].n;
+    auto big_rows = [&](int i) { return inst[i].n > kTileCap ? inst[i].n : 0ll; };
+    while (i1 < count && (i1 == i0 || grows + big_rows(i1) <= kBatchGroupRows)) grows += big_rows(i1++);
+    if (grows == 0) {  // only instances of the direct launch
+      i0 = i1;
+      continue;
+    }
     std::vector<Chunk> tiles;
     for (int i = i0; i < i1; ++i)
-      for (long long lo = 0; lo < inst[i].n; lo += kTileCap) {
+      for (long long lo = 0; inst[i].n > kTileCap && lo < inst[i].n; lo += kTileCap) {
         Chunk c{};
         c.lo = lo;
         c.hi = std::min<long long>(inst[i].n, lo + kTileCap);
@@ -1445,7 +1487,8 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
       const int gi = i1 - i0;
       kbegin(h, SGAGG_K_PROBE);
       k_inst_bounds<<<(gi + 256) / 256, 256, 0, stream>>>(P<unsigned long long>(h->bkeys), n1, P<InstDesc>(h->binst),
-                                                          key_bits, i0, gi, P<long long>(h->bstartb), 0);
+                                                          key_bits, i0, gi, P<long long>(h->bstartb), 0,
+                                                          kTileCap);
       kend(h);
       TRY(sync_read(h, cnt1.data(), h->bstartb.p, (size_t)(gi + 1) * 8));
       CU(cudaMemcpy(rng.data(), kmin_d + i0, (size_t)gi * 8, cudaMemcpyDeviceToHost));
@@ -1505,7 +1548,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
     for (int a = 0; a < S; ++a) gs.cols[a] = g.cols[a];
     kbegin(h, SGAGG_K_OTHER);
     k_inst_bounds<<<(i1 - i0 + 256) / 256, 256, 0, stream>>>(g.keys, rows, P<InstDesc>(h->binst), key_bits, i0,
-                                                             i1 - i0, P<long long>(h->bstartb), 1);
+                                                             i1 - i0, P<long long>(h->bstartb), 1, kTileCap);
     if (rows > 0)
       k_distribute<<<(int)((rows + kDistRows - 1) / kDistRows), 256, 0, stream>>>(
           g.keys, gs, rows, S, P<InstDesc>(h->binst), key_bits, i0, i1 - i0, P<long long>(h->bstartb));
@@ -1816,7 +1859,7 @@ void sgagg_destroy(sgagg_t h) {
   free_buf(h->gather_ptrs); free_buf(h->runstarts);
   free_buf(h->marena_keys); fv(h->marena_cols); free_buf(h->moffs);
   free_buf(h->binst); free_buf(h->bchunks); free_buf(h->bkeys); free_buf(h->bout_keys);
-  free_buf(h->bseg); free_buf(h->brange); free_buf(h->bstartb);
+  free_buf(h->bseg); free_buf(h->brange); free_buf(h->bstartb); free_buf(h->bdirect);
   fv(h->bcols); fv(h->bout_cols);
   for (auto& b : h->in_keys) free_buf(b);
   fv(h->in_pay);

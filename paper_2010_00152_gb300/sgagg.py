@@ -61,6 +61,27 @@ class sgagg_instance(ctypes.Structure):
                 ("out_rows", ctypes.c_void_p)]
 
 
+class sgagg_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("device_budget_bytes", ctypes.c_int64),
+                ("memory_budget_rows", ctypes.c_int64), ("small_rows", ctypes.c_int64),
+                ("max_batch", ctypes.c_int32), ("max_batch_rows", ctypes.c_int64)]
+
+
+class sgagg_request(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("key_bytes", ctypes.c_int32), ("n_payload", ctypes.c_int32),
+                ("payload", ctypes.c_void_p), ("n", ctypes.c_int64), ("out_keys", ctypes.c_void_p),
+                ("out_aggs", ctypes.c_void_p), ("out_capacity", ctypes.c_int64), ("ready", ctypes.c_void_p)]
+
+
+class sgagg_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("rows", ctypes.c_int64),
+                ("submit_ns", ctypes.c_int64), ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("batch_size", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "pad"}
+
+
 _lib = None
 
 
@@ -95,6 +116,24 @@ def lib():
         L.sgagg_last_error.restype = ctypes.c_char_p
         for f in ("sgagg_create", "sgagg_set_option", "sgagg_aggregate", "sgagg_aggregate_host",
                   "sgagg_result_rows", "sgagg_stats", "sgagg_aggregate_batched"):
+            getattr(L, f).restype = i32
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.sgagg_request_footprint.argtypes = [i64, i32, i32, i32, i64, i64]
+        L.sgagg_request_footprint.restype = i64
+        L.sgagg_server_now_ns.argtypes = []
+        L.sgagg_server_now_ns.restype = i64
+        L.sgagg_server_create.argtypes = [ctypes.POINTER(sgagg_server_config), ctypes.POINTER(sgagg_spec),
+                                          ctypes.POINTER(vp)]
+        L.sgagg_server_submit.argtypes = [vp, ctypes.POINTER(sgagg_request), ctypes.POINTER(i64)]
+        L.sgagg_server_wait.argtypes = [vp, i64, ctypes.POINTER(sgagg_request_result)]
+        L.sgagg_server_poll.argtypes = [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(sgagg_request_result)]
+        L.sgagg_server_destroy.argtypes = [vp]
+        L.sgagg_server_destroy.restype = None
+        L.sgagg_server_simulate.argtypes = [ctypes.POINTER(sgagg_server_config), i32, i32, i32,
+                                            ctypes.POINTER(i64), dp, dp, dp, dp,
+                                            ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        for f in ("sgagg_server_create", "sgagg_server_submit", "sgagg_server_wait", "sgagg_server_poll",
+                  "sgagg_server_simulate"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -316,3 +355,108 @@ class Aggregator:
                                     [k.ctypes.data for k in ok], [a.ctypes.data for a in oa], cap,
                                     stream)
         return [k[:rows] for k in ok], [a[:rows] for a in oa]
+
+
+# ---- serving --------------------------------------------------------------
+def server_config(slots=8, device_budget_bytes=64 << 30, memory_budget_rows=1 << 22, small_rows=1 << 16,
+                  max_batch=256, max_batch_rows=1 << 24):
+    return sgagg_server_config(int(slots), int(device_budget_bytes), int(memory_budget_rows), int(small_rows),
+                               int(max_batch), int(max_batch_rows))
+
+
+def sgagg_request_footprint(n, key_bytes, n_payload, n_aggs, out_capacity, memory_budget_rows):
+    return int(lib().sgagg_request_footprint(int(n), int(key_bytes), int(n_payload), int(n_aggs),
+                                             int(out_capacity), int(memory_budget_rows)))
+
+
+def sgagg_server_now_ns():
+    return int(lib().sgagg_server_now_ns())
+
+
+def sgagg_server_simulate(cfg, n_payload, n_aggs, rows, arrive_us, cost_us):
+    """Run the server's admission and batching decisions on the host against
+    a cost model; returns (start_us, finish_us, slot, batch) lists."""
+    n = len(rows)
+    r = (ctypes.c_int64 * max(1, n))(*[int(x) for x in rows])
+    a = (ctypes.c_double * max(1, n))(*[float(x) for x in arrive_us])
+    c = (ctypes.c_double * 3)(*[float(x) for x in cost_us])
+    st_ = (ctypes.c_double * max(1, n))()
+    fi = (ctypes.c_double * max(1, n))()
+    sl = (ctypes.c_int32 * max(1, n))()
+    bt = (ctypes.c_int32 * max(1, n))()
+    s = lib().sgagg_server_simulate(ctypes.byref(cfg), int(n_payload), int(n_aggs), n, r, a, c, st_, fi, sl, bt)
+    if s != SGAGG_OK:
+        raise SgaggError(s, "sgagg_server_simulate")
+    return list(st_)[:n], list(fi)[:n], list(sl)[:n], list(bt)[:n]
+
+
+class Server:
+    """Request loop (sgagg_server_*) over torch tensors: submit() queues a
+    request and returns a ticket; wait()/poll() give its result dict and its
+    output tensors.  Tensors of a request are kept alive until it is done."""
+
+    def __init__(self, aggs, **cfg):
+        self.aggs = list(aggs)
+        self.cfg = server_config(**cfg)
+        self._aggs = (sgagg_agg * max(1, len(self.aggs)))(*[sgagg_agg(int(o), int(c)) for o, c in self.aggs])
+        self._spec = sgagg_spec(len(self.aggs), self._aggs)
+        self.h = ctypes.c_void_p()
+        st = lib().sgagg_server_create(ctypes.byref(self.cfg), ctypes.byref(self._spec), ctypes.byref(self.h))
+        if st != SGAGG_OK:
+            raise SgaggError(st, "sgagg_server_create")
+        self._live = {}
+
+    def submit(self, keys, payload, capacity=None, ready=None, out=None):
+        import torch
+        n = keys.numel()
+        cap = n if capacity is None else int(capacity)
+        if out is None:
+            ok = torch.empty(max(1, cap), dtype=keys.dtype, device=keys.device)
+            oa = [torch.empty(max(1, cap), dtype=torch.int64, device=keys.device) for _ in self.aggs]
+        else:
+            ok, oa = out
+        pay = (ctypes.c_void_p * max(1, len(payload)))(*[p.data_ptr() for p in payload])
+        oap = (ctypes.c_void_p * max(1, len(oa)))(*[a.data_ptr() for a in oa])
+        req = sgagg_request(keys.data_ptr(), keys.element_size(), len(payload), ctypes.cast(pay, ctypes.c_void_p),
+                            n, ok.data_ptr(), ctypes.cast(oap, ctypes.c_void_p), cap,
+                            ready.cuda_event if ready is not None else None)
+        t = ctypes.c_int64()
+        st = lib().sgagg_server_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if st != SGAGG_OK:
+            raise SgaggError(st, "sgagg_server_submit")
+        self._live[t.value] = (keys, payload, ok, oa, ready)
+        return t.value
+
+    def _finish(self, t, r):
+        keys, payload, ok, oa, ready = self._live.pop(t)
+        d = r.as_dict()
+        rows = d["rows"]
+        d["out"] = (ok[:rows], [a[:rows] for a in oa]) if rows >= 0 else None
+        return d
+
+    def wait(self, t):
+        r = sgagg_request_result()
+        st = lib().sgagg_server_wait(self.h, int(t), ctypes.byref(r))
+        if st != SGAGG_OK:
+            raise SgaggError(st, "sgagg_server_wait")
+        return self._finish(t, r)
+
+    def poll(self, t):
+        r = sgagg_request_result()
+        done = ctypes.c_int32()
+        st = lib().sgagg_server_poll(self.h, int(t), ctypes.byref(done), ctypes.byref(r))
+        if st != SGAGG_OK:
+            raise SgaggError(st, "sgagg_server_poll")
+        return self._finish(t, r) if done.value else None
+
+    def close(self):
+        if self.h:
+            lib().sgagg_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
