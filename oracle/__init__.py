@@ -41,6 +41,8 @@ def lib():
         L.orc_fold_states.restype = i64
         L.orc_run_generation.argtypes = [P, i64, i64, i32, P, i32, P, P, P, P, P]
         L.orc_run_generation.restype = i64
+        L.orc_absorb_runs.argtypes = [P, i64, i64, i64, i32, P, i32, P, P, P, P]
+        L.orc_absorb_runs.restype = i64
         _lib = L
     return _lib
 
@@ -141,6 +143,23 @@ def run_generation(keys, payload, aggs, M):
         raise ValueError("bad run-generation arguments")
     tot = int(run_rows[:r].sum())
     return [int(x) for x in run_rows[:r]], rk[:tot].copy(), [s[:tot].copy() for s in rs]
+
+
+def absorb_runs(keys, payload, aggs, M, B):
+    """Run generation with an absorbing index of at most M keys, batches of B
+    rows (Sec. 3, Sec. 6.1).  Returns (run row counts, rows left in the
+    index); no runs means the input was absorbed in memory."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    payload = [np.ascontiguousarray(p, dtype=np.int64) for p in payload]
+    n = len(keys)
+    ops, cols = _agg_arrays(aggs)
+    run_rows = np.zeros(n + 2, dtype=np.int64)
+    left = ctypes.c_int64()
+    r = lib().orc_absorb_runs(keys.ctypes.data, n, int(M), int(B), len(payload), _ptrs(payload), len(aggs),
+                              ops.ctypes.data, cols.ctypes.data, run_rows.ctypes.data, ctypes.byref(left))
+    if r < 0:
+        raise ValueError("bad absorbing run-generation arguments")
+    return [int(x) for x in run_rows[:r]], int(left.value)
 
 
 def aggregate(key_cols, payload, aggs):

@@ -203,3 +203,80 @@ int64_t orc_run_generation(const uint64_t *keys, int64_t n, int64_t M, int n_pay
     }
     return runs;
 }
+
+/*
+ * Run generation with an absorbing in-memory index (Sec. 3 on early
+ * aggregation: key values equal to ones already in the index are absorbed by
+ * aggregation; Sec. 6.1 on the in-sort aggregation algorithm: each input
+ * batch is sorted first to detect duplicates within the batch, only the
+ * batch's distinct keys are looked up in the ordered index, and when memory
+ * runs out the index is written as a sorted run, read-sort-write style, so
+ * that runs hold M keys).
+ *
+ * The index is a sorted array of at most M distinct keys with their partial
+ * aggregates.  Batch by batch (B consecutive input rows, the last shorter):
+ * the batch is grouped (sorted, equal keys folded); its distinct keys are
+ * then taken in ascending order -- a key already in the index is absorbed
+ * (aggregates combined); a new key is inserted while the index holds fewer
+ * than M keys; otherwise the whole index is written as a run, emptied, and
+ * the key inserted.  At the end, if no run was written the index is the
+ * output; else it is written as the last run.
+ *
+ * run_rows[] (capacity n + 1) receives every run's row count; returns the
+ * number of runs (0: the input was absorbed in memory), or -1 on a bad
+ * argument or allocation failure.  *index_rows receives the rows left in the
+ * index at the end (the output rows when no run was written).
+ */
+int64_t orc_absorb_runs(const uint64_t *keys, int64_t n, int64_t M, int64_t B, int n_pay,
+                        const int64_t *const *pay, int n_aggs, const int32_t *ops,
+                        const int32_t *cols, int64_t *run_rows, int64_t *index_rows)
+{
+    if (M < 1 || B < 1 || n < 0 || n_aggs > 64) return -1;
+    uint64_t *ik = (uint64_t *)malloc((size_t)M * sizeof(uint64_t));
+    int64_t *is = (int64_t *)malloc((size_t)M * (size_t)(n_aggs > 0 ? n_aggs : 1) * sizeof(int64_t));
+    int64_t bmax = B < n ? B : (n > 0 ? n : 1);
+    uint64_t *bk = (uint64_t *)malloc((size_t)bmax * sizeof(uint64_t));
+    int64_t *bsd = (int64_t *)malloc((size_t)bmax * (size_t)(n_aggs > 0 ? n_aggs : 1) * sizeof(int64_t));
+    if (!ik || !is || !bk || !bsd) { free(ik); free(is); free(bk); free(bsd); return -1; }
+    int64_t r = 0, runs = 0;
+    const int64_t *bpay[64];
+    int64_t *bst[64];
+    for (int a = 0; a < n_aggs; ++a) bst[a] = bsd + (size_t)a * (size_t)bmax;
+    for (int64_t s = 0; s < n; s += B) {
+        int64_t m = (n - s < B) ? (n - s) : B;
+        for (int c = 0; c < n_pay && c < 64; ++c) bpay[c] = pay[c] + s;
+        int64_t g = orc_groupby(keys + s, m, n_pay, bpay, n_aggs, ops, cols, bk, bst);
+        if (g < 0) { free(ik); free(is); free(bk); free(bsd); return -1; }
+        for (int64_t j = 0; j < g; ++j) {
+            const uint64_t x = bk[j];
+            int64_t lo = 0, hi = r;  /* first index entry >= x */
+            while (lo < hi) {
+                int64_t mid = (lo + hi) / 2;
+                if (ik[mid] < x) lo = mid + 1; else hi = mid;
+            }
+            if (lo < r && ik[lo] == x) {  /* absorbed */
+                for (int a = 0; a < n_aggs; ++a)
+                    is[(size_t)a * (size_t)M + (size_t)lo] =
+                        orc_combine(ops[a], is[(size_t)a * (size_t)M + (size_t)lo], bst[a][j]);
+                continue;
+            }
+            if (r == M) {  /* memory full: the index becomes a run */
+                run_rows[runs++] = r;
+                r = 0;
+                lo = 0;
+            }
+            memmove(ik + lo + 1, ik + lo, (size_t)(r - lo) * sizeof(uint64_t));
+            ik[lo] = x;
+            for (int a = 0; a < n_aggs; ++a) {
+                int64_t *col = is + (size_t)a * (size_t)M;
+                memmove(col + lo + 1, col + lo, (size_t)(r - lo) * sizeof(int64_t));
+                col[lo] = bst[a][j];
+            }
+            ++r;
+        }
+    }
+    if (runs > 0) run_rows[runs++] = r;
+    *index_rows = r;
+    free(ik); free(is); free(bk); free(bsd);
+    return runs;
+}
