@@ -133,9 +133,19 @@ typedef enum {
                                      merges of the smallest runs first (Sec. 4.3). 0 = auto */
     SGAGG_OPT_FAULT_ALLOC = 5,    /* test hook: fail the k-th internal allocation (0 = off) */
     SGAGG_OPT_TIMING = 6,         /* 1: time every kernel class with CUDA events (class_ms) */
-    SGAGG_OPT_TEST_STALL = 7      /* test hook: in the next sort+fold launch the first chunk
+    SGAGG_OPT_TEST_STALL = 7,     /* test hook: in the next sort+fold launch the first chunk
                                      never publishes its row count, so the bounded waits of
                                      the others run out -> SGAGG_ETIMEOUT (no hang) */
+    SGAGG_OPT_POLICY = 8,         /* run generation: 0 (default) one run per batch of
+                                     memory_budget_rows rows, holding the batch's distinct
+                                     keys; 1 an absorbing index of at most memory_budget_rows
+                                     distinct keys (Sec. 3, Sec. 6.1): each batch is sorted
+                                     and folded, its distinct keys are absorbed by the index
+                                     or inserted in ascending order, and when the index is
+                                     full it is written as a run and emptied -- no run at all
+                                     when the output fits memory_budget_rows */
+    SGAGG_OPT_ABSORB_BATCH = 9    /* rows per batch of policy 1 (0 = min(memory_budget_rows,
+                                     2^22)); the runs depend on it, the result does not */
 } sgagg_option;
 
 /*

@@ -232,12 +232,21 @@ int64_t orc_absorb_runs(const uint64_t *keys, int64_t n, int64_t M, int64_t B, i
                         const int32_t *cols, int64_t *run_rows, int64_t *index_rows)
 {
     if (M < 1 || B < 1 || n < 0 || n_aggs > 64) return -1;
-    uint64_t *ik = (uint64_t *)malloc((size_t)M * sizeof(uint64_t));
-    int64_t *is = (int64_t *)malloc((size_t)M * (size_t)(n_aggs > 0 ? n_aggs : 1) * sizeof(int64_t));
+    const size_t A = (size_t)(n_aggs > 0 ? n_aggs : 1);
+    /* the index (old) and the index being rebuilt while the batch's keys are
+       taken in ascending order (new); inserting keys in ascending order into
+       a sorted array is a merge of the two sorted lists */
+    uint64_t *ok = (uint64_t *)malloc((size_t)M * sizeof(uint64_t));
+    uint64_t *nk = (uint64_t *)malloc((size_t)M * sizeof(uint64_t));
+    int64_t *os = (int64_t *)malloc((size_t)M * A * sizeof(int64_t));
+    int64_t *ns = (int64_t *)malloc((size_t)M * A * sizeof(int64_t));
     int64_t bmax = B < n ? B : (n > 0 ? n : 1);
     uint64_t *bk = (uint64_t *)malloc((size_t)bmax * sizeof(uint64_t));
-    int64_t *bsd = (int64_t *)malloc((size_t)bmax * (size_t)(n_aggs > 0 ? n_aggs : 1) * sizeof(int64_t));
-    if (!ik || !is || !bk || !bsd) { free(ik); free(is); free(bk); free(bsd); return -1; }
+    int64_t *bsd = (int64_t *)malloc((size_t)bmax * A * sizeof(int64_t));
+    if (!ok || !nk || !os || !ns || !bk || !bsd) {
+        free(ok); free(nk); free(os); free(ns); free(bk); free(bsd);
+        return -1;
+    }
     int64_t r = 0, runs = 0;
     const int64_t *bpay[64];
     int64_t *bst[64];
@@ -246,37 +255,41 @@ int64_t orc_absorb_runs(const uint64_t *keys, int64_t n, int64_t M, int64_t B, i
         int64_t m = (n - s < B) ? (n - s) : B;
         for (int c = 0; c < n_pay && c < 64; ++c) bpay[c] = pay[c] + s;
         int64_t g = orc_groupby(keys + s, m, n_pay, bpay, n_aggs, ops, cols, bk, bst);
-        if (g < 0) { free(ik); free(is); free(bk); free(bsd); return -1; }
+        if (g < 0) { free(ok); free(nk); free(os); free(ns); free(bk); free(bsd); return -1; }
+        int64_t i = 0, w = 0;  /* next old entry, entries in the new index */
         for (int64_t j = 0; j < g; ++j) {
             const uint64_t x = bk[j];
-            int64_t lo = 0, hi = r;  /* first index entry >= x */
-            while (lo < hi) {
-                int64_t mid = (lo + hi) / 2;
-                if (ik[mid] < x) lo = mid + 1; else hi = mid;
+            while (i < r && ok[i] < x) {  /* old keys below x stay */
+                nk[w] = ok[i];
+                for (int a = 0; a < n_aggs; ++a) ns[(size_t)a * (size_t)M + (size_t)w] = os[(size_t)a * (size_t)M + (size_t)i];
+                ++w; ++i;
             }
-            if (lo < r && ik[lo] == x) {  /* absorbed */
+            if (i < r && ok[i] == x) {  /* absorbed */
                 for (int a = 0; a < n_aggs; ++a)
-                    is[(size_t)a * (size_t)M + (size_t)lo] =
-                        orc_combine(ops[a], is[(size_t)a * (size_t)M + (size_t)lo], bst[a][j]);
+                    os[(size_t)a * (size_t)M + (size_t)i] =
+                        orc_combine(ops[a], os[(size_t)a * (size_t)M + (size_t)i], bst[a][j]);
                 continue;
             }
-            if (r == M) {  /* memory full: the index becomes a run */
-                run_rows[runs++] = r;
-                r = 0;
-                lo = 0;
+            if (w + (r - i) == M) {  /* memory full: the index becomes a run */
+                run_rows[runs++] = M;
+                w = 0;
+                i = r = 0;
             }
-            memmove(ik + lo + 1, ik + lo, (size_t)(r - lo) * sizeof(uint64_t));
-            ik[lo] = x;
-            for (int a = 0; a < n_aggs; ++a) {
-                int64_t *col = is + (size_t)a * (size_t)M;
-                memmove(col + lo + 1, col + lo, (size_t)(r - lo) * sizeof(int64_t));
-                col[lo] = bst[a][j];
-            }
-            ++r;
+            nk[w] = x;  /* inserted */
+            for (int a = 0; a < n_aggs; ++a) ns[(size_t)a * (size_t)M + (size_t)w] = bst[a][j];
+            ++w;
         }
+        while (i < r) {  /* old keys above the batch's last key */
+            nk[w] = ok[i];
+            for (int a = 0; a < n_aggs; ++a) ns[(size_t)a * (size_t)M + (size_t)w] = os[(size_t)a * (size_t)M + (size_t)i];
+            ++w; ++i;
+        }
+        uint64_t *tk = ok; ok = nk; nk = tk;
+        int64_t *ts = os; os = ns; ns = ts;
+        r = w;
     }
     if (runs > 0) run_rows[runs++] = r;
     *index_rows = r;
-    free(ik); free(is); free(bk); free(bsd);
+    free(ok); free(nk); free(os); free(ns); free(bk); free(bsd);
     return runs;
 }

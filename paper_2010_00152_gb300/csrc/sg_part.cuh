@@ -705,4 +705,120 @@ k_distribute(const unsigned long long* keys, CopySrc states, long long total, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Absorbing-index run generation (host side in sgagg.cu): copies of sorted
+// state rows between the index, the batch, the merged index and the runs,
+// and the searches that split them.
+// ---------------------------------------------------------------------------
+struct SoaRef {
+  unsigned long long* keys;
+  long long* cols[kMaxCols];
+};
+
+// dst rows [dst_off, dst_off + n) = src rows [src_off, src_off + n), columns
+// 0 .. ncols-1; column zero_col (if >= 0) is written as 0 instead.
+__global__ void k_copy_soa(SoaRef src, long long src_off, SoaRef dst, long long dst_off, long long n, int ncols,
+                           int zero_col) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    dst.keys[dst_off + i] = src.keys[src_off + i];
+    for (int c = 0; c < ncols; ++c) dst.cols[c][dst_off + i] = c == zero_col ? 0 : src.cols[c][src_off + i];
+  }
+}
+
+// The n rows of src to the caller's output (keys unpacked to its columns).
+__global__ void k_emit_soa(SoaRef src, long long n, int ncols, OutSink out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    sink_key(out, i, src.keys[i]);
+    for (int c = 0; c < ncols; ++c) sink_val(out, c, i, src.cols[c][i]);
+  }
+}
+
+// counts[b] = nonzero entries of flag in block b's range (ranges of `per`).
+__global__ void k_flag_counts(const long long* flag, long long n, long long per, long long* counts) {
+  __shared__ long long part[32];
+  const long long lo = blockIdx.x * per, hi = min(n, lo + per);
+  long long c = 0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) c += flag[i] != 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// *pos = index of the j-th (1-based) nonzero entry of flag, or n if there
+// are fewer; one block of 1024 threads after k_flag_counts over nb ranges.
+__global__ void __launch_bounds__(1024)
+k_nth_flag(const long long* flag, long long n, long long per, const long long* counts, int nb, long long j,
+           long long* pos) {
+  __shared__ long long s_before;
+  __shared__ int s_block;
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    int b = 0;
+    while (b < nb && acc + counts[b] < j) acc += counts[b++];
+    s_before = acc;
+    s_block = b;
+  }
+  __syncthreads();
+  if (s_block >= nb) {
+    if (threadIdx.x == 0) *pos = n;
+    return;
+  }
+  const long long lo = s_block * per, hi = min(n, lo + per);
+  long long need = j - s_before;  // >= 1, and the block holds at least that many
+  __shared__ long long wsum[32];
+  for (long long base = lo; base < hi; base += blockDim.x) {
+    const long long i = base + threadIdx.x;
+    const int f = (i < hi && flag[i] != 0) ? 1 : 0;
+    // block inclusive scan of f
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = f;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      long long v = wsum[lane], t = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      wsum[lane] = t - v;
+    }
+    __syncthreads();
+    const long long incl = wsum[w] + x;
+    if (f && incl == need) *pos = i;
+    const long long tot = wsum[31] + __shfl_sync(0xffffffffu, x, 31);  // valid in warp 31 only
+    __shared__ long long s_tot;
+    if (threadIdx.x == blockDim.x - 1) s_tot = tot;
+    __syncthreads();
+    need -= s_tot;
+    if (need <= 0) return;
+    __syncthreads();
+  }
+}
+
+// With x = tkeys[*p]: out[0] = keys of a[0 .. na) below x, out[1] = keys of
+// b[0 .. nb) below x (both ascending).  One thread.
+__global__ void k_split_at(const unsigned long long* tkeys, const long long* p, const unsigned long long* a,
+                           long long na, const unsigned long long* b, long long nb, long long* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned long long x = tkeys[*p];
+  for (int w = 0; w < 2; ++w) {
+    const unsigned long long* k = w ? b : a;
+    long long lo = 0, hi = w ? nb : na;
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if (k[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    out[w] = lo;
+  }
+}
+
 }  // namespace sg

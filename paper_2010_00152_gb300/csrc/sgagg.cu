@@ -77,6 +77,8 @@ struct sgagg_ctx {
   int alloc_count = 0;
   int timing = 0;
   int test_stall = 0;
+  int policy = 0;                // 0: a run per batch, 1: absorbing index
+  long long absorb_batch = 0;    // rows per batch of the absorbing policy (0: auto)
   std::string err;
   // per-launch event pairs (SGAGG_OPT_TIMING)
   struct KT { cudaEvent_t a = nullptr, b = nullptr; int cls = 0; };
@@ -116,6 +118,8 @@ struct sgagg_ctx {
   DevBuf bseg, brange, bstartb;              // batched call: segmented digit, key ranges, row starts
   DevBuf bdirect;                            // batched call: chunks of the one-chunk instances
   std::vector<DevBuf> bcols, bout_cols;
+  DevBuf ab_keys[3], ab_offs[3], ab_tmp;   // absorbing policy: index, batch, merged index
+  std::vector<DevBuf> ab_cols[3];
   DevBuf marena_keys;            // runs written by preliminary merges
   std::vector<DevBuf> marena_cols;
   DevBuf moffs;
@@ -950,6 +954,282 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
   return SGAGG_OK;
 }
 
+// Wide merge of all runs into the caller's output (Sec. 4), after
+// preliminary merges of the smallest runs when they exceed the fan-in
+// (Sec. 4.3).
+sgagg_status merge_all(sgagg_t h, std::vector<RunRef> rr, int S, const FoldDesc& fd, int nf, long long stride,
+                       const Digit& gd, const OutSink& user) {
+  cudaStream_t stream = h->stream;
+  Small* ds = dsmall(h);
+  HostSmall* hs = hsmall(h);
+  const long long row_bytes = 8ll * (1 + S);
+  FoldDesc fid = identity_fold(fd);
+  const int cap = (h->fanin_cap > 0) ? std::min(h->fanin_cap, kMaxFanIn) : kMaxFanIn;
+  if ((int)rr.size() > cap) {
+    // preliminary merges of the smallest runs until one wide merge can take
+    // every run (Sec. 4.3); each writes a new run into the merge arena
+    // rows all preliminary merges may write: replay the schedule with each
+    // merged run as large as its inputs (an upper bound)
+    long long need = 0;
+    int extra = 0;
+    {
+      std::vector<long long> sz;
+      for (auto& r : rr) sz.push_back(r.rows);
+      while ((int)sz.size() > cap) {
+        const int g = std::min<int>(cap, (int)sz.size() - cap + 1);
+        std::stable_sort(sz.begin(), sz.end());
+        long long m = 0;
+        for (int i = 0; i < g; ++i) m += sz[i];
+        sz.erase(sz.begin(), sz.begin() + g);
+        sz.push_back(m);
+        need += m;
+        ++extra;
+      }
+    }
+    TRY(grow(h, h->marena_keys, (size_t)std::max(1ll, need) * 8));
+    TRY(grow_cols(h, h->marena_cols, S, (size_t)std::max(1ll, need) * 8));
+    TRY(grow(h, h->moffs, (size_t)extra * stride * 8));
+    long long used = 0;
+    int made = 0;
+    while ((int)rr.size() > cap) {
+      const int g = std::min<int>(cap, (int)rr.size() - cap + 1);
+      std::stable_sort(rr.begin(), rr.end(), [](const RunRef& x, const RunRef& y) { return x.rows < y.rows; });
+      std::vector<RunRef> part(rr.begin(), rr.begin() + g);
+      OutSink o{};
+      o.user = 0;
+      o.keys = P<unsigned long long>(h->marena_keys);
+      for (int s = 0; s < S; ++s) o.cols[s] = P<long long>(h->marena_cols[s]);
+      o.capacity = need;
+      o.offs = P<long long>(h->moffs) + (long long)made * stride;
+      o.dig = gd;
+      long long* slot = &ds->dtot[kMaxDepth];
+      hs->v[0] = used;
+      CU(cudaMemcpyAsync(slot, &hs->v[0], 8, cudaMemcpyHostToDevice, stream));
+      long long end = 0;
+      TRY(merge_runs(h, part, S, fid, nf, o, slot, slot, &end, false));
+      RunRef nr;
+      nr.keys = P<long long>(h->marena_keys);
+      for (int s = 0; s < S; ++s) nr.cols[s] = P<long long>(h->marena_cols[s]);
+      nr.offs = o.offs;
+      nr.rows = end - used;
+      used = end;
+      ++made;
+      h->st.run_rows += nr.rows;
+      h->st.run_bytes_device += nr.rows * row_bytes;
+      ++h->st.runs;
+      rr.erase(rr.begin(), rr.begin() + g);
+      rr.push_back(nr);
+    }
+  }
+  long long rows = 0;
+  TRY(merge_runs(h, rr, S, fid, nf, user, nullptr, &ds->total, &rows, true));
+  h->last_rows = rows;
+  h->st.out_rows = rows;
+  return SGAGG_OK;
+}
+
+// Run generation with an absorbing index (SGAGG_OPT_POLICY = 1; Sec. 3 on
+// early aggregation absorbing equal keys in the in-memory index, Sec. 6.1 on
+// the in-sort algorithm: each batch sorted first, only its distinct keys
+// looked up in the ordered index, the index written as a run when memory
+// runs out).  The index is a sorted, folded array of at most M keys with an
+// extra flag column (0 for rows of the index).  Per batch:
+//   1. the batch is grouped (sorted, folded) with flag 1 on every key;
+//   2. it is merged into the index (wide-merge kernel, two runs; flags
+//      combine by min, so a merged row's flag says "not in the index");
+//   3. if the new keys fit, the merged rows are the index; else, taking new
+//      keys in ascending order, the index is full at the (q+1)-th new key t,
+//      q = M - |index|: the merged rows below t and the index rows from t on
+//      are written as a run of M keys, and the batch's keys from t on fill the
+//      emptied index, M at a time (every full index but the last becomes a
+//      run).
+// No run at all when the output fits M keys; else the index is the last run
+// and all runs go through the wide merge.
+sgagg_status absorb_device(sgagg_t h, const RowSrc& raw, long long n, const FoldDesc& fd, int S,
+                           const OutSink& user, const Digit& gd) {
+  cudaStream_t stream = h->stream;
+  Small* ds = dsmall(h);
+  HostSmall* hs = hsmall(h);
+  const long long M = h->M;
+  const long long Bz = h->absorb_batch > 0 ? h->absorb_batch : std::min<long long>(M, 1ll << 22);
+  const long long nb = (n + Bz - 1) / Bz;
+  h->st.batches = nb;
+  const int S1 = S + 1;
+  if (S1 > kMaxCols) return fail(h, SGAGG_EINVAL, "too many aggregates for the absorbing policy");
+  FoldDesc fdx = fd;  // the batch: the aggregates, then the flag (1)
+  fdx.n_state = S1;
+  fdx.src[S] = -1;
+  fdx.op[S] = OP_MAX;
+  FoldDesc fmx = identity_fold(fdx);  // the merge: flags by min
+  fmx.op[S] = OP_MIN;
+  const int nf = 1 << gd.fbits;
+  const long long stride = nf + 1;
+  const long long cap3 = M + std::min(Bz, n);
+  for (int i = 0; i < 3; ++i) {
+    TRY(grow(h, h->ab_keys[i], (size_t)cap3 * 8));
+    TRY(grow_cols(h, h->ab_cols[i], S1, (size_t)cap3 * 8));
+    TRY(grow(h, h->ab_offs[i], (size_t)stride * 8));
+  }
+  TRY(grow(h, h->ab_tmp, (size_t)(1024 + 8) * 8));
+  const long long max_runs = n / M + 2;  // every run but the last holds M rows
+  TRY(grow(h, h->arena_keys, (size_t)n * 8));
+  TRY(grow_cols(h, h->arena_cols, S, (size_t)n * 8));
+  h->arena_keys.arena = true;
+  for (auto& b : h->arena_cols) b.arena = true;
+  TRY(grow(h, h->offs, (size_t)max_runs * stride * 8));
+
+  auto soa = [&](int i) {
+    SoaRef r{};
+    r.keys = P<unsigned long long>(h->ab_keys[i]);
+    for (int c = 0; c < S1; ++c) r.cols[c] = P<long long>(h->ab_cols[i][c]);
+    return r;
+  };
+  SoaRef arena{};
+  arena.keys = P<unsigned long long>(h->arena_keys);
+  for (int c = 0; c < S; ++c) arena.cols[c] = P<long long>(h->arena_cols[c]);
+  auto grid = [&](long long m) {
+    return (int)std::max(1ll, std::min<long long>((m + 255) / 256, (long long)h->num_sms * 8));
+  };
+  std::vector<Run> runs;
+  long long acur = 0, rstart = 0;  // arena cursor, start of the run being written
+  const long long row_bytes = 8ll * (1 + S);
+  auto append = [&](int src, long long off, long long m) {
+    if (m <= 0) return;
+    kbegin(h, SGAGG_K_OTHER);
+    k_copy_soa<<<grid(m), 256, 0, stream>>>(soa(src), off, arena, acur, m, S, -1);
+    kend(h);
+    kbytes(h, SGAGG_K_OTHER, m * 2 * row_bytes);
+    acur += m;
+  };
+  auto close_run = [&]() -> sgagg_status {
+    const long long m = acur - rstart;
+    if ((long long)runs.size() >= max_runs) return fail(h, SGAGG_ECUDA, "absorbing policy: run table overflow");
+    kbegin(h, SGAGG_K_PLAN);
+    k_offsets_by_search<<<std::max(1, std::min(4 * h->num_sms, (nf + 256) / 256)), 256, 0, stream>>>(
+        arena.keys + rstart, m, gd, nf, rstart, P<long long>(h->offs) + (long long)runs.size() * stride);
+    kend(h);
+    CU(cudaGetLastError());
+    runs.push_back(Run{rstart, m, 0});
+    h->st.run_rows += m;
+    h->st.run_bytes_device += m * row_bytes;
+    rstart = acur;
+    return SGAGG_OK;
+  };
+
+  int iR = 0, iD = 1, iT = 2;
+  long long r = 0;  // keys in the index
+  for (long long b = 0; b < nb; ++b) {
+    const long long m = std::min(Bz, n - b * Bz);
+    RowSrc bs = raw;
+    bs.offset = b * Bz;
+    OutSink od{};
+    od.user = 0;
+    SoaRef d = soa(iD);
+    od.keys = d.keys;
+    for (int c = 0; c < S1; ++c) od.cols[c] = d.cols[c];
+    od.capacity = cap3;
+    od.offs = P<long long>(h->ab_offs[iD]);
+    od.dig = gd;
+    TRY(solve(h, bs, m, fdx, od, nullptr, &ds->total, &gd, 0));
+    TRY(sync_read(h, &hs->v[0], &ds->total, 8));
+    TRY(check_device_err(h));
+    const long long dn = hs->v[0];
+    int iM = iD;  // buffer of the merged rows
+    long long tn = dn;
+    if (r > 0) {
+      RunRef a{}, c{};
+      SoaRef x = soa(iR);
+      a.keys = reinterpret_cast<const long long*>(x.keys);
+      for (int k = 0; k < S1; ++k) a.cols[k] = x.cols[k];
+      a.offs = P<long long>(h->ab_offs[iR]);
+      a.rows = r;
+      c.keys = reinterpret_cast<const long long*>(d.keys);
+      for (int k = 0; k < S1; ++k) c.cols[k] = d.cols[k];
+      c.offs = P<long long>(h->ab_offs[iD]);
+      c.rows = dn;
+      OutSink ot{};
+      ot.user = 0;
+      SoaRef t = soa(iT);
+      ot.keys = t.keys;
+      for (int k = 0; k < S1; ++k) ot.cols[k] = t.cols[k];
+      ot.capacity = cap3;
+      ot.offs = P<long long>(h->ab_offs[iT]);
+      ot.dig = gd;
+      TRY(merge_runs(h, std::vector<RunRef>{a, c}, S1, fmx, nf, ot, nullptr, &ds->total, &tn, false));
+      iM = iT;
+    }
+    const long long fresh = tn - r;  // batch keys not in the index
+    if (r + fresh <= M) {
+      std::swap(iR, iM == iT ? iT : iD);
+      r = tn;
+      CU(cudaMemsetAsync(P<long long>(h->ab_cols[iR][S]), 0, (size_t)r * 8, stream));
+      continue;
+    }
+    const long long q = M - r;
+    long long p = q, pr = 0, pd = q;
+    if (r > 0) {
+      long long* tmp = P<long long>(h->ab_tmp);
+      const long long* flag = P<long long>(h->ab_cols[iT][S]);
+      const int nbk = (int)std::max(1ll, std::min<long long>(1024, (tn + 4095) / 4096));
+      const long long per = (tn + nbk - 1) / nbk;
+      kbegin(h, SGAGG_K_PLAN);
+      k_flag_counts<<<nbk, 256, 0, stream>>>(flag, tn, per, tmp);
+      k_nth_flag<<<1, 1024, 0, stream>>>(flag, tn, per, tmp, nbk, q + 1, tmp + 1024);
+      k_split_at<<<1, 32, 0, stream>>>(soa(iT).keys, tmp + 1024, soa(iR).keys, r, d.keys, dn, tmp + 1025);
+      kend(h);
+      CU(cudaGetLastError());
+      TRY(sync_read(h, &hs->v[0], tmp + 1024, 24));
+      p = hs->v[0];
+      pr = hs->v[1];
+      pd = hs->v[2];
+      if (p >= tn || p + (r - pr) != M) return fail(h, SGAGG_ECUDA, "absorbing policy: inconsistent split");
+    }
+    // the full index: merged rows below t, then the index rows from t on
+    append(iM, 0, p);
+    append(iR, pr, r - pr);
+    TRY(close_run());
+    // the batch keys from t on refill the emptied index, M at a time
+    long long off = pd, left = dn - pd;
+    while (left > M) {
+      append(iD, off, M);
+      TRY(close_run());
+      off += M;
+      left -= M;
+    }
+    kbegin(h, SGAGG_K_OTHER);
+    k_copy_soa<<<grid(std::max(1ll, left)), 256, 0, stream>>>(d, off, soa(iR), 0, left, S1, S);
+    k_offsets_by_search<<<std::max(1, std::min(4 * h->num_sms, (nf + 256) / 256)), 256, 0, stream>>>(
+        soa(iR).keys, left, gd, nf, 0, P<long long>(h->ab_offs[iR]));
+    kend(h);
+    CU(cudaGetLastError());
+    r = left;
+  }
+  h->st.runs = (long long)runs.size();
+  if (runs.empty()) {
+    // the whole input was absorbed: the index is the output (Sec. 3)
+    if (r > user.capacity) return fail(h, SGAGG_ECAPACITY, "out_capacity is smaller than the number of distinct keys");
+    kbegin(h, SGAGG_K_OTHER);
+    k_emit_soa<<<grid(std::max(1ll, r)), 256, 0, stream>>>(soa(iR), r, S, user);
+    kend(h);
+    CU(cudaGetLastError());
+    kbytes(h, SGAGG_K_OTHER, r * (row_bytes + h->key_bytes + 8ll * S));
+    h->last_rows = r;
+    h->st.out_rows = r;
+    return SGAGG_OK;
+  }
+  append(iR, 0, r);
+  TRY(close_run());
+  h->st.runs = (long long)runs.size();
+  std::vector<RunRef> rr(runs.size());
+  for (size_t i = 0; i < runs.size(); ++i) {
+    rr[i].keys = reinterpret_cast<const long long*>(arena.keys);
+    for (int c = 0; c < S; ++c) rr[i].cols[c] = arena.cols[c];
+    rr[i].offs = P<long long>(h->offs) + (long long)i * stride;
+    rr[i].rows = runs[i].rows;
+  }
+  return merge_all(h, rr, S, fd, nf, stride, gd, user);
+}
+
 // The whole operation on device-resident inputs.
 sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* const* payload_cols,
                               int32_t n_payload, int64_t n, const sgagg_spec* spec, void* const* out_keys,
@@ -1041,6 +1321,17 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
   gd.fbits = std::min(Fb, L);
   gd.fshift = L - gd.fbits;
   gd.ebits = std::max(0, gd.fbits - Db);
+
+  if (h->policy == 1) {
+    // absorbing index: the digit's fine buckets index the index, the
+    // batches and the runs (sized by n, as for several batches)
+    Digit ad = gd;
+    const int afb = std::max(Db, std::min(22, ilog2_ceil((n + kBucketRows - 1) / kBucketRows)));
+    ad.fbits = std::min(afb, L);
+    ad.fshift = L - ad.fbits;
+    ad.ebits = std::max(0, ad.fbits - Db);
+    return absorb_device(h, raw, n, fd, S, user, ad);
+  }
 
   if (B == 1) {
     long long* tot = &ds->total;
@@ -1157,69 +1448,7 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
     r.offs = P<long long>(h->offs) + b2 * stride;
     r.rows = runs[b2].rows;
   }
-  FoldDesc fid = identity_fold(fd);
-  const int cap = (h->fanin_cap > 0) ? std::min(h->fanin_cap, kMaxFanIn) : kMaxFanIn;
-  if ((int)rr.size() > cap) {
-    // preliminary merges of the smallest runs until one wide merge can take
-    // every run (Sec. 4.3); each writes a new run into the merge arena
-    // rows all preliminary merges may write: replay the schedule with each
-    // merged run as large as its inputs (an upper bound)
-    long long need = 0;
-    int extra = 0;
-    {
-      std::vector<long long> sz;
-      for (auto& r : rr) sz.push_back(r.rows);
-      while ((int)sz.size() > cap) {
-        const int g = std::min<int>(cap, (int)sz.size() - cap + 1);
-        std::stable_sort(sz.begin(), sz.end());
-        long long m = 0;
-        for (int i = 0; i < g; ++i) m += sz[i];
-        sz.erase(sz.begin(), sz.begin() + g);
-        sz.push_back(m);
-        need += m;
-        ++extra;
-      }
-    }
-    TRY(grow(h, h->marena_keys, (size_t)std::max(1ll, need) * 8));
-    TRY(grow_cols(h, h->marena_cols, S, (size_t)std::max(1ll, need) * 8));
-    TRY(grow(h, h->moffs, (size_t)extra * stride * 8));
-    long long used = 0;
-    int made = 0;
-    while ((int)rr.size() > cap) {
-      const int g = std::min<int>(cap, (int)rr.size() - cap + 1);
-      std::stable_sort(rr.begin(), rr.end(), [](const RunRef& x, const RunRef& y) { return x.rows < y.rows; });
-      std::vector<RunRef> part(rr.begin(), rr.begin() + g);
-      OutSink o{};
-      o.user = 0;
-      o.keys = P<unsigned long long>(h->marena_keys);
-      for (int s = 0; s < S; ++s) o.cols[s] = P<long long>(h->marena_cols[s]);
-      o.capacity = need;
-      o.offs = P<long long>(h->moffs) + (long long)made * stride;
-      o.dig = gd;
-      long long* slot = &ds->dtot[kMaxDepth];
-      hs->v[0] = used;
-      CU(cudaMemcpyAsync(slot, &hs->v[0], 8, cudaMemcpyHostToDevice, stream));
-      long long end = 0;
-      TRY(merge_runs(h, part, S, fid, nf, o, slot, slot, &end, false));
-      RunRef nr;
-      nr.keys = P<long long>(h->marena_keys);
-      for (int s = 0; s < S; ++s) nr.cols[s] = P<long long>(h->marena_cols[s]);
-      nr.offs = o.offs;
-      nr.rows = end - used;
-      used = end;
-      ++made;
-      h->st.run_rows += nr.rows;
-      h->st.run_bytes_device += nr.rows * row_bytes;
-      ++h->st.runs;
-      rr.erase(rr.begin(), rr.begin() + g);
-      rr.push_back(nr);
-    }
-  }
-  long long rows = 0;
-  TRY(merge_runs(h, rr, S, fid, nf, user, nullptr, &ds->total, &rows, true));
-  h->last_rows = rows;
-  h->st.out_rows = rows;
-  return SGAGG_OK;
+  return merge_all(h, rr, S, fd, nf, stride, gd, user);
 }
 
 }  // namespace
@@ -1732,6 +1961,14 @@ sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
       return SGAGG_OK;
     case SGAGG_OPT_TIMING: h->timing = (int)value; return SGAGG_OK;
     case SGAGG_OPT_TEST_STALL: h->test_stall = value ? 1 : 0; return SGAGG_OK;
+    case SGAGG_OPT_POLICY:
+      if (value != 0 && value != 1) return fail(h, SGAGG_EINVAL, "policy must be 0 or 1");
+      h->policy = (int)value;
+      return SGAGG_OK;
+    case SGAGG_OPT_ABSORB_BATCH:
+      if (value < 0) return fail(h, SGAGG_EINVAL, "absorbing batch must be >= 0");
+      h->absorb_batch = value;
+      return SGAGG_OK;
     default: return fail(h, SGAGG_EINVAL, "unknown option");
   }
 }
@@ -1858,6 +2095,10 @@ void sgagg_destroy(sgagg_t h) {
   free_buf(h->offs); free_buf(h->runptrs); free_buf(h->fsizes); free_buf(h->gather_keys); fv(h->gather_cols);
   free_buf(h->gather_ptrs); free_buf(h->runstarts);
   free_buf(h->marena_keys); fv(h->marena_cols); free_buf(h->moffs);
+  for (int i = 0; i < 3; ++i) {
+    free_buf(h->ab_keys[i]); free_buf(h->ab_offs[i]); fv(h->ab_cols[i]);
+  }
+  free_buf(h->ab_tmp);
   free_buf(h->binst); free_buf(h->bchunks); free_buf(h->bkeys); free_buf(h->bout_keys);
   free_buf(h->bseg); free_buf(h->brange); free_buf(h->bstartb); free_buf(h->bdirect);
   fv(h->bcols); fv(h->bout_cols);

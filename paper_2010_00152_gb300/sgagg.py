@@ -19,7 +19,8 @@ STATUS_NAMES = {0: "SGAGG_OK", 1: "SGAGG_EINVAL", 2: "SGAGG_ENOMEM", 3: "SGAGG_E
                 4: "SGAGG_ETIMEOUT", 5: "SGAGG_ECAPACITY", 6: "SGAGG_ESTATE"}
 SGAGG_COUNT, SGAGG_SUM, SGAGG_MIN, SGAGG_MAX = range(4)
 (SGAGG_OPT_PREFOLD, SGAGG_OPT_ARENA_CAP, SGAGG_OPT_RADIX_BITS, SGAGG_OPT_SPIN_LIMIT,
- SGAGG_OPT_FANIN_CAP, SGAGG_OPT_FAULT_ALLOC, SGAGG_OPT_TIMING, SGAGG_OPT_TEST_STALL) = range(8)
+ SGAGG_OPT_FANIN_CAP, SGAGG_OPT_FAULT_ALLOC, SGAGG_OPT_TIMING, SGAGG_OPT_TEST_STALL,
+ SGAGG_OPT_POLICY, SGAGG_OPT_ABSORB_BATCH) = range(10)
 
 
 class sgagg_agg(ctypes.Structure):
@@ -259,7 +260,8 @@ class Aggregator:
         names = {"prefold": SGAGG_OPT_PREFOLD, "arena_cap": SGAGG_OPT_ARENA_CAP,
                  "radix_bits": SGAGG_OPT_RADIX_BITS, "spin_limit": SGAGG_OPT_SPIN_LIMIT,
                  "fanin_cap": SGAGG_OPT_FANIN_CAP, "fault_alloc": SGAGG_OPT_FAULT_ALLOC,
-                 "timing": SGAGG_OPT_TIMING, "test_stall": SGAGG_OPT_TEST_STALL}
+                 "timing": SGAGG_OPT_TIMING, "test_stall": SGAGG_OPT_TEST_STALL,
+                 "policy": SGAGG_OPT_POLICY, "absorb_batch": SGAGG_OPT_ABSORB_BATCH}
         for k, v in options.items():
             sgagg_set_option(self.h, names[k], v)
 
