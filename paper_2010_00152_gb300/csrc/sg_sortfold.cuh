@@ -122,7 +122,7 @@ __device__ __forceinline__ SortSmem carve(unsigned char* base) {
 // Block-wide helpers (kThreads threads).
 // ---------------------------------------------------------------------------
 __shared__ long long g_red[kWarps + 1];
-__shared__ unsigned long long g_redu[2 * kWarps + 2];
+__shared__ int g_wmax[kWarps];
 
 // Exclusive sum over threads; returns the thread's exclusive prefix, *total.
 __device__ __forceinline__ int block_excl_sum(int v, int* total) {
@@ -148,52 +148,6 @@ __device__ __forceinline__ int block_excl_sum(int v, int* total) {
   __syncthreads();
   int r = (int)g_red[w] + x - v;
   *total = (int)g_red[kWarps];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ void block_minmax(unsigned long long vmin, unsigned long long vmax,
-                                             unsigned long long* omin, unsigned long long* omax) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long a = __shfl_xor_sync(0xffffffffu, vmin, o);
-    unsigned long long b = __shfl_xor_sync(0xffffffffu, vmax, o);
-    vmin = a < vmin ? a : vmin;
-    vmax = b > vmax ? b : vmax;
-  }
-  __syncthreads();
-  if (lane == 0) { g_redu[w] = vmin; g_redu[kWarps + w] = vmax; }
-  __syncthreads();
-  if (w == 0) {
-    unsigned long long a = lane < kWarps ? g_redu[lane] : ~0ull;
-    unsigned long long b = lane < kWarps ? g_redu[kWarps + lane] : 0ull;
-    for (int o = 16; o > 0; o >>= 1) {
-      unsigned long long x = __shfl_xor_sync(0xffffffffu, a, o);
-      unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
-      a = x < a ? x : a;
-      b = y > b ? y : b;
-    }
-    if (lane == 0) { g_redu[2 * kWarps] = a; g_redu[2 * kWarps + 1] = b; }
-  }
-  __syncthreads();
-  *omin = g_redu[2 * kWarps];
-  *omax = g_redu[2 * kWarps + 1];
-  __syncthreads();
-}
-
-__device__ __forceinline__ int block_max_int(int v) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
-  if (lane == 0) g_red[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    long long a = lane < kWarps ? g_red[lane] : 0;
-    for (int o = 16; o > 0; o >>= 1) a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
-    if (lane == 0) g_red[kWarps] = a;
-  }
-  __syncthreads();
-  int r = (int)g_red[kWarps];
   __syncthreads();
   return r;
 }
@@ -262,7 +216,7 @@ __device__ __forceinline__ int run_advance(const SortSmem& s, int k, int r, int 
 
 template <int MODE>
 __device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, const RunSet& runs,
-                                          const ChunkView& cv) {
+                                          const ChunkView& cv, unsigned long long* lmin, unsigned long long* lmax) {
   constexpr int U = 8;  // loads in flight per thread
   int r = 0;            // a thread's positions only grow: the run cursor only advances
   for (int base = threadIdx.x; base < cv.n; base += U * kThreads) {
@@ -283,7 +237,11 @@ __device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       int i = base + u * kThreads;
-      if (i < cv.n) s.keys[i] = v[u];
+      if (i < cv.n) {
+        s.keys[i] = v[u];
+        *lmin = v[u] < *lmin ? v[u] : *lmin;
+        *lmax = v[u] > *lmax ? v[u] : *lmax;
+      }
     }
   }
 }
@@ -367,25 +325,34 @@ __device__ void lsd_sort(const SortSmem& s, int n, unsigned long long kmin, int 
 }
 
 // Sort s.idx by key; returns whether a key group may hold more than 32 rows.
-__device__ bool chunk_sort(const SortSmem& s, int n) {
-  unsigned long long lmin = ~0ull, lmax = 0ull;
-  for (int i = threadIdx.x; i < n; i += kThreads) {
-    unsigned long long k = s.keys[i];
-    lmin = k < lmin ? k : lmin;
-    lmax = k > lmax ? k : lmax;
+// Block key range: each warp's least and greatest loaded key, combined by
+// shared-memory atomics (g_kmin / g_kmax are preset when the CTA starts).
+__shared__ unsigned long long g_kmin, g_kmax;
+__shared__ int g_maxbin;
+
+// Sort s.idx by key (the keys just loaded; lmin / lmax: the thread's least
+// and greatest); returns whether a key group may hold more than 32 rows.
+__device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, unsigned long long lmax) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // zero the bins while the key range is combined: one barrier for the
+  // loaded keys, the range and the bins
+  for (int i = threadIdx.x; i < kBins / 2; i += kThreads) s.bins[i] = 0;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, lmin, o);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, lmax, o);
+    lmin = a < lmin ? a : lmin;
+    lmax = b > lmax ? b : lmax;
   }
-  unsigned long long kmin, kmax;
-  block_minmax(lmin, lmax, &kmin, &kmax);
-  if (n == 0) {
-    for (int i = threadIdx.x; i < kBins / 2; i += kThreads) s.bins[i] = 0;
-    __syncthreads();
-    return false;
+  if (lane == 0 && lmin <= lmax) {
+    atomicMin(&g_kmin, lmin);
+    atomicMax(&g_kmax, lmax);
   }
+  __syncthreads();
+  if (n == 0) return false;
+  const unsigned long long kmin = g_kmin, kmax = g_kmax;
   const unsigned long long range = kmax - kmin;
   const int vb = range == 0 ? 0 : 64 - __clzll((long long)range);
   const int sh = vb > kBinBits ? vb - kBinBits : 0;
-  for (int i = threadIdx.x; i < kBins / 2; i += kThreads) s.bins[i] = 0;
-  __syncthreads();
   // counting sort on the top bits: rank inside the bin from the atomic, kept
   // in registers (a thread's rows are i = threadIdx.x + j * kThreads)
   constexpr int EPT = kTileCap / kThreads;
@@ -409,9 +376,33 @@ __device__ bool chunk_sort(const SortSmem& s, int n) {
     loc += cnt[q];
     mx = max(mx, cnt[q]);
   }
-  int total;
-  int start = block_excl_sum(loc, &total);
-  const int maxbin = block_max_int(mx);
+  // exclusive scan of the thread counts and the largest bin, two barriers
+  int x = loc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 31) {
+    g_red[w] = x;
+    g_wmax[w] = mx;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const long long v = lane < kWarps ? g_red[lane] : 0;
+    long long t = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kWarps) g_red[lane] = t - v;
+    int m = lane < kWarps ? g_wmax[lane] : 0;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) g_maxbin = m;
+  }
+  __syncthreads();
+  int start = (int)g_red[w] + x - loc;
+  const int maxbin = g_maxbin;
 #pragma unroll
   for (int q = 0; q < kBinsPerThread; q += 2) {
     unsigned lo = (unsigned)start;
@@ -431,10 +422,17 @@ __device__ bool chunk_sort(const SortSmem& s, int n) {
   if (sh == 0) return maxbin > 32;  // every bin is one key value
   if (maxbin <= 32) {
     // with about one row per bin, only the few bins holding two or more rows
-    // need work: insertion sort in place, a thread per bin
-    for (int b = threadIdx.x; b < kBins; b += kThreads) {
-      const int st = (int)bin_get(s.bins, b);
-      const int en = (b + 1 < kBins) ? (int)bin_get(s.bins, b + 1) : n;
+    // need work: insertion sort in place; a thread takes its 16 consecutive
+    // bins, their starts read as 8 words
+    const int b0 = threadIdx.x * kBinsPerThread;
+    uint32_t wd[kBinsPerThread / 2];
+#pragma unroll
+    for (int q = 0; q < kBinsPerThread / 2; ++q) wd[q] = s.bins[(b0 >> 1) + q];
+    const int en_last = (b0 + kBinsPerThread < kBins) ? (int)(s.bins[(b0 + kBinsPerThread) >> 1] & 0xFFFFu) : n;
+#pragma unroll
+    for (int q = 0; q < kBinsPerThread; ++q) {
+      const int st = (int)((wd[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu);
+      const int en = q + 1 < kBinsPerThread ? (int)((wd[(q + 1) >> 1] >> (((q + 1) & 1) * 16)) & 0xFFFFu) : en_last;
       for (int i = st + 1; i < en; ++i) {
         const uint16_t v = s.idx[i];
         const unsigned long long kv = s.keys[v];
@@ -894,6 +892,8 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
   if (threadIdx.x == 0) {
     s_cid = (int)atomicAdd(lb.ticket, 1u);
     s_err = err_load(lb.err);
+    g_kmin = ~0ull;
+    g_kmax = 0ull;
   }
   __syncthreads();
   const int cid = s_cid;
@@ -1005,9 +1005,9 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
     if (threadIdx.x == 0) err_raise(lb.err, ERR_INTERNAL);
     return;
   }
-  load_keys<MODE>(s, src, runs, cv);
-  __syncthreads();
-  const bool bigs = chunk_sort(s, cv.n);
+  unsigned long long lmin = ~0ull, lmax = 0ull;
+  load_keys<MODE>(s, src, runs, cv, &lmin, &lmax);
+  const bool bigs = chunk_sort(s, cv.n, lmin, lmax);  // its first barrier completes the load
   if (MODE == MODE_INST && is.kmin && threadIdx.x == 0 && cv.n > 0) {
     // key range of the instance (its tiles' sorted ends), for the digit
     // that partitions the partial rows
