@@ -183,79 +183,102 @@ __device__ __forceinline__ long long plan_scan(long long v, long long* total) {
   return r;
 }
 
+// One CTA of 1024 threads.  The bucket counts are taken in tiles of
+// 1024 x kPlanPer buckets, each read with coalesced loads into shared memory;
+// a thread owns kPlanPer consecutive buckets of the tile, and the running
+// prefixes (all rows, rows of small buckets, big buckets, chunk starts) and
+// the state of the tile's last bucket carry from tile to tile.
+constexpr int kPlanPer = 4;
 __global__ void __launch_bounds__(1024)
 k_plan(const long long* __restrict__ w, int nb, long long target, long long big, long long cap, int fine_shift,
        long long* bstart, Chunk* chunks, int* big_list, PlanInfo* info) {
   const int T = blockDim.x;
-  const int per = (nb + T - 1) / T;
-  const int d0 = min(nb, (int)threadIdx.x * per), d1 = min(nb, d0 + per);
-  __shared__ long long sa[1024];
-  __shared__ int s_nc;
-  __shared__ long long s_tot[3];
-  long long ta = 0, tb = 0, tc = 0;
-  for (int d = d0; d < d1; ++d) {
-    long long x = w[d];
-    ta += x;
-    if (x > cap) tc += 1;
-    if (x <= big) tb += x;
+  __shared__ long long tile[1024 * kPlanPer];
+  __shared__ long long sa[1024 / 32];
+  __shared__ long long c_a, c_b, c_c, c_s;  // prefixes before the tile
+  __shared__ long long c_x;                 // the last bucket before the tile (-1: none)
+  __shared__ long long s_end[4];
+  if (threadIdx.x == 0) {
+    c_a = c_b = c_c = c_s = 0;
+    c_x = -1;
   }
   long long dummy;
-  const long long A0 = plan_scan(ta, &dummy);
-  const long long B0 = plan_scan(tb, &dummy);
-  const long long C0 = plan_scan(tc, &dummy);
-  if (threadIdx.x == T - 1) {
-    s_tot[0] = A0 + ta;
-    s_tot[2] = C0 + tc;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    info->total = s_tot[0];
-    info->n_big = (int)s_tot[2];
-    bstart[nb] = s_tot[0];
-  }
-  // state just before d0 (the previous bucket)
-  bool pb0 = true;
-  long long pq0 = -1;
-  if (d0 > 0 && d0 < nb) {
-    long long x = w[d0 - 1];
-    pb0 = x > big;
-    pq0 = pb0 ? -1 : (B0 - x) / target;
-  }
-  int starts = 0;
-  {
-    bool pbig = pb0;
-    long long pq = pq0, pB = B0;
-    for (int d = d0; d < d1; ++d) {
-      long long x = w[d];
-      starts += plan_is_start(x, big, pB, target, &pbig, &pq);
-      if (x <= big) pB += x;
+  for (int base = 0; base < nb; base += T * kPlanPer) {
+    const int nt = min(nb - base, T * kPlanPer);
+    for (int i = threadIdx.x; i < nt; i += T) tile[i] = w[base + i];
+    __syncthreads();
+    const int l0 = min(nt, (int)threadIdx.x * kPlanPer), l1 = min(nt, l0 + kPlanPer);
+    long long ta = 0, tb = 0, tc = 0;
+    for (int l = l0; l < l1; ++l) {
+      const long long x = tile[l];
+      ta += x;
+      if (x > cap) tc += 1;
+      if (x <= big) tb += x;
     }
-  }
-  const long long S0 = plan_scan(starts, &dummy);
-  if (threadIdx.x == T - 1) {
-    s_nc = (int)(S0 + starts);
-    info->n_chunks = (int)(S0 + starts);
-  }
-  __syncthreads();
-  {
-    bool pbig = pb0;
-    long long pq = pq0, pB = B0, pA = A0, nbig = C0;
-    long long cidx = S0 - 1;
-    for (int d = d0; d < d1; ++d) {
-      long long x = w[d];
-      bstart[d] = pA;
-      if (plan_is_start(x, big, pB, target, &pbig, &pq)) {
-        ++cidx;
-        chunks[cidx].f_lo = d;  // bucket index for now
-        chunks[cidx].kind = x > cap ? CH_COPY : CH_NORMAL;
-        if (x > cap) big_list[nbig++] = (int)cidx;
+    const long long A0 = c_a + plan_scan(ta, &dummy);
+    const long long B0 = c_b + plan_scan(tb, &dummy);
+    const long long C0 = c_c + plan_scan(tc, &dummy);
+    // state of the bucket before l0 (the previous bucket)
+    bool pb0 = true;
+    long long pq0 = -1;
+    const long long xp = l0 > 0 ? tile[l0 - 1] : c_x;
+    if (l0 < nt && xp >= 0) {
+      pb0 = xp > big;
+      pq0 = pb0 ? -1 : (B0 - xp) / target;
+    }
+    int starts = 0;
+    {
+      bool pbig = pb0;
+      long long pq = pq0, pB = B0;
+      for (int l = l0; l < l1; ++l) {
+        const long long x = tile[l];
+        starts += plan_is_start(x, big, pB, target, &pbig, &pq);
+        if (x <= big) pB += x;
       }
-      if (x <= big) pB += x;
-      pA += x;
     }
+    const long long S0 = c_s + plan_scan(starts, &dummy);
+    {
+      bool pbig = pb0;
+      long long pq = pq0, pB = B0, pA = A0, nbig = C0;
+      long long cidx = S0 - 1;
+      for (int l = l0; l < l1; ++l) {
+        const int d = base + l;
+        const long long x = tile[l];
+        bstart[d] = pA;
+        if (plan_is_start(x, big, pB, target, &pbig, &pq)) {
+          ++cidx;
+          chunks[cidx].f_lo = d;  // bucket index for now
+          chunks[cidx].kind = x > cap ? CH_COPY : CH_NORMAL;
+          if (x > cap) big_list[nbig++] = (int)cidx;
+        }
+        if (x <= big) pB += x;
+        pA += x;
+      }
+    }
+    if (threadIdx.x == T - 1) {  // the last thread's exclusive prefixes + its own part
+      s_end[0] = A0 + ta;
+      s_end[1] = B0 + tb;
+      s_end[2] = C0 + tc;
+      s_end[3] = S0 + starts;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      c_a = s_end[0];
+      c_b = s_end[1];
+      c_c = s_end[2];
+      c_s = s_end[3];
+      c_x = tile[nt - 1];
+    }
+    __syncthreads();
+  }
+  const int nc = (int)c_s;
+  if (threadIdx.x == 0) {
+    info->total = c_a;
+    info->n_big = (int)c_c;
+    info->n_chunks = nc;
+    bstart[nb] = c_a;
   }
   __syncthreads();
-  const int nc = s_nc;
   long long mx = 0;
   // chunk c ends where chunk c + 1 starts: stash the end bucket in pad
   for (int c = threadIdx.x; c < nc; c += T) {
