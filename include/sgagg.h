@@ -180,11 +180,15 @@ sgagg_status sgagg_aggregate(sgagg_t h, const sgagg_keys *keys,
                              int64_t out_capacity, void *stream);
 
 /*
- * Same operation with HOST buffers: copies the inputs to the device (the
- * copies of batch b+1 overlap the run generation of batch b), runs the
- * device path and copies the result back.  Synchronous.  *rows receives the
- * number of distinct keys.  Host buffers may be pageable; pinned buffers
- * copy faster.
+ * Same operation with HOST buffers.  The inputs are copied to the device on
+ * a second stream batch by batch (memory_budget_rows rows), batch b + 1
+ * while batch b is grouped; the planner's key sample is read from the host
+ * columns, so no copy has to finish first.  When runs are merged, the final
+ * merge runs in 8 parts and each part's output is copied back while the
+ * later parts merge; otherwise (one batch, or SGAGG_OPT_POLICY 1) the input
+ * is copied first and the output after.  Synchronous.  *rows receives the
+ * number of distinct keys.  Host buffers may be pageable; only pinned
+ * buffers let the copies overlap the kernels.
  */
 sgagg_status sgagg_aggregate_host(sgagg_t h, const sgagg_keys *keys,
                                   const int64_t *const *payload_cols, int32_t n_payload,

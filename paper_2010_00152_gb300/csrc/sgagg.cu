@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -65,6 +66,30 @@ struct RunRef {
 };
 
 }  // namespace
+
+// A host-buffer call (sgagg_aggregate_host): inputs are copied batch by
+// batch on a copy stream, batch b + 1 while batch b is grouped; the final
+// merge runs in parts and each part's output is copied back while the next
+// parts merge.
+constexpr int kMergeParts = 8;
+struct HostIO {
+  cudaStream_t copy = nullptr;
+  int nk = 0;
+  const void* hkeys[kMaxKeyCols];
+  int kb[kMaxKeyCols];
+  void* dkeys[kMaxKeyCols];
+  int np = 0;
+  const int64_t* const* hpay = nullptr;  // host payload columns
+  const bool* used = nullptr;            // payload columns the aggregates read
+  int64_t* const* dpay = nullptr;        // their device copies
+  void* hout_keys[kMaxKeyCols];
+  void* dout_keys[kMaxKeyCols];
+  int S = 0;
+  int64_t* const* hout_aggs = nullptr;
+  int64_t* const* dout_aggs = nullptr;
+  long long capacity = 0;
+  long long copied_out = 0;  // output rows whose copy back is enqueued
+};
 
 struct sgagg_ctx {
   long long M = 1;
@@ -135,6 +160,11 @@ struct sgagg_ctx {
 
   // pinned host scratch for small read-backs
   void* hsmall = nullptr;
+  // host-buffer calls: the copy stream and its events
+  HostIO* hio = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> io_events;       // input batches staged
+  cudaEvent_t part_events[kMergeParts] = {};  // parts of the final merge done
 
   // buffers requested by the current call (scratch accounting)
   int gen = 0;
@@ -162,6 +192,7 @@ struct Small {
   long long total;              // total_out of the final sort+fold
   long long pftot;              // total_out of a pre-fold pass
   long long dsum;               // rows of the one-chunk instances of a batched call
+  long long part_tot[kMergeParts];  // final merge in parts: output end of every part
   long long dtot[kMaxDepth + 2];  // base/total of the sub-solves under depth d
 };
 
@@ -173,6 +204,7 @@ struct HostSmall {
   long long v[8];
   unsigned long long sample[kSample];
   Chunk ch[4];
+  long long part_end[kMergeParts];   // final merge: output end of every part
 };
 
 sgagg_status fail(sgagg_t h, sgagg_status s, const char* fmt, const char* a = "") {
@@ -277,6 +309,80 @@ void free_buf(DevBuf& b) {
 
 Small* dsmall(sgagg_t h) { return reinterpret_cast<Small*>(h->small.p); }
 HostSmall* hsmall(sgagg_t h) { return reinterpret_cast<HostSmall*>(h->hsmall); }
+
+// ---- host-buffer calls: staged copies (see HostIO) ----
+sgagg_status io_event(sgagg_t h, size_t i, cudaEvent_t* e) {
+  while (h->io_events.size() <= i) {
+    cudaEvent_t x;
+    CU(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+    h->io_events.push_back(x);
+  }
+  *e = h->io_events[i];
+  return SGAGG_OK;
+}
+
+// Enqueue the copies of input rows [lo, hi) on the copy stream; event i
+// fires when they are done.
+sgagg_status stage_rows(sgagg_t h, long long lo, long long hi, size_t i) {
+  HostIO& io = *h->hio;
+  if (hi > lo) {
+    for (int c = 0; c < io.nk; ++c)
+      CU(cudaMemcpyAsync(static_cast<char*>(io.dkeys[c]) + lo * io.kb[c],
+                         static_cast<const char*>(io.hkeys[c]) + lo * io.kb[c], (size_t)(hi - lo) * io.kb[c],
+                         cudaMemcpyHostToDevice, io.copy));
+    for (int c = 0; c < io.np; ++c)
+      if (io.used[c])
+        CU(cudaMemcpyAsync(io.dpay[c] + lo, io.hpay[c] + lo, (size_t)(hi - lo) * 8, cudaMemcpyHostToDevice, io.copy));
+  }
+  cudaEvent_t e;
+  TRY(io_event(h, i, &e));
+  CU(cudaEventRecord(e, io.copy));
+  return SGAGG_OK;
+}
+
+// The compute stream waits for the copies of event i.
+sgagg_status wait_rows(sgagg_t h, size_t i) {
+  CU(cudaStreamWaitEvent(h->stream, h->io_events[i], 0));
+  return SGAGG_OK;
+}
+
+// Enqueue the copy back of output rows [lo, hi) on the copy stream, after
+// event `after` (recorded on the compute stream).
+sgagg_status unstage_rows(sgagg_t h, long long lo, long long hi, cudaEvent_t after) {
+  HostIO& io = *h->hio;
+  hi = std::min(hi, io.capacity);
+  if (hi <= lo) return SGAGG_OK;
+  CU(cudaStreamWaitEvent(io.copy, after, 0));
+  for (int c = 0; c < io.nk; ++c)
+    CU(cudaMemcpyAsync(static_cast<char*>(io.hout_keys[c]) + lo * io.kb[c],
+                       static_cast<const char*>(io.dout_keys[c]) + lo * io.kb[c], (size_t)(hi - lo) * io.kb[c],
+                       cudaMemcpyDeviceToHost, io.copy));
+  for (int a = 0; a < io.S; ++a)
+    CU(cudaMemcpyAsync(io.hout_aggs[a] + lo, io.dout_aggs[a] + lo, (size_t)(hi - lo) * 8, cudaMemcpyDeviceToHost,
+                       io.copy));
+  return SGAGG_OK;
+}
+
+// The planner's key sample taken from the host columns (the same rows the
+// device probe reads), so that no input copy has to finish first.
+void host_sample(const HostIO& io, const sg::KeyCols& kc, long long n, int count, unsigned long long* out) {
+  for (int i = 0; i < count; ++i) {
+    const long long r = (long long)((__int128)i * n / count);
+    unsigned long long v = 0;
+    for (int c = 0; c < io.nk; ++c) {
+      const char* p = static_cast<const char*>(io.hkeys[c]) + r * io.kb[c];
+      unsigned long long x = 0;
+      switch (io.kb[c]) {
+        case 1: x = *reinterpret_cast<const uint8_t*>(p); break;
+        case 2: x = *reinterpret_cast<const uint16_t*>(p); break;
+        case 4: x = *reinterpret_cast<const uint32_t*>(p); break;
+        default: x = *reinterpret_cast<const unsigned long long*>(p); break;
+      }
+      v |= kc.n_cols == 1 ? x : (x << kc.shift[c]);
+    }
+    out[i] = v;
+  }
+}
 
 int ilog2_ceil(long long x) {
   int b = 0;
@@ -943,8 +1049,31 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
   }
   RowSrc nosrc{};
   nosrc.ncols = 0;
-  TRY(launch_sortfold<MODE_RUNS>(h, SGAGG_K_MERGE, P<Chunk>(h->chunks[0]), info.n_chunks, 0, nosrc, rset, copy,
-                                 fid, out, base_in, total_out));
+  if (final_merge && h->hio && info.n_chunks >= 2) {
+    // host buffers: merge in parts; each part's output is copied back while
+    // the following parts merge
+    const int parts = std::min(kMergeParts, info.n_chunks);
+    for (int p = 0; p < parts; ++p) {
+      const int c0 = (int)((long long)info.n_chunks * p / parts), c1 = (int)((long long)info.n_chunks * (p + 1) / parts);
+      TRY(launch_sortfold<MODE_RUNS>(h, SGAGG_K_MERGE, P<Chunk>(h->chunks[0]) + c0, c1 - c0, 0, nosrc, rset, copy,
+                                     fid, out, p ? &ds->part_tot[p - 1] : base_in, &ds->part_tot[p]));
+      CU(cudaMemcpyAsync(&hs->part_end[p], &ds->part_tot[p], 8, cudaMemcpyDeviceToHost, stream));
+      if (!h->part_events[p]) CU(cudaEventCreateWithFlags(&h->part_events[p], cudaEventDisableTiming));
+      CU(cudaEventRecord(h->part_events[p], stream));
+    }
+    long long prev = 0;
+    for (int p = 0; p < parts; ++p) {
+      CU(cudaEventSynchronize(h->part_events[p]));
+      const long long e = hs->part_end[p];
+      TRY(unstage_rows(h, prev, e, h->part_events[p]));
+      prev = std::max(prev, e);
+    }
+    h->hio->copied_out = prev;
+    CU(cudaMemcpyAsync(total_out, &ds->part_tot[parts - 1], 8, cudaMemcpyDeviceToDevice, stream));
+  } else {
+    TRY(launch_sortfold<MODE_RUNS>(h, SGAGG_K_MERGE, P<Chunk>(h->chunks[0]), info.n_chunks, 0, nosrc, rset, copy,
+                                   fid, out, base_in, total_out));
+  }
   TRY(sync_read(h, &hs->v[0], total_out, 8));
   TRY(check_device_err(h));
   *end = hs->v[0];
@@ -1299,10 +1428,14 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
   // ---- probe: sampled key range and duplicate rate ----
   int scount = (int)std::min<long long>(n, kSample);
   TRY(grow(h, h->sample, (size_t)kSample * 8));
-  kbegin(h, SGAGG_K_PROBE);
-  k_sample<<<16, 256, 0, stream>>>(raw, n, scount, P<unsigned long long>(h->sample));
-  kend(h);
-  TRY(sync_read(h, hs->sample, h->sample.p, (size_t)scount * 8));
+  if (h->hio) {
+    host_sample(*h->hio, raw.key, n, scount, hs->sample);
+  } else {
+    kbegin(h, SGAGG_K_PROBE);
+    k_sample<<<16, 256, 0, stream>>>(raw, n, scount, P<unsigned long long>(h->sample));
+    kend(h);
+    TRY(sync_read(h, hs->sample, h->sample.p, (size_t)scount * 8));
+  }
   std::sort(hs->sample, hs->sample + scount);
   unsigned long long smin = hs->sample[0], smax = hs->sample[scount - 1];
   long long sdist = std::unique(hs->sample, hs->sample + scount) - hs->sample;
@@ -1322,6 +1455,10 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
   gd.fshift = L - gd.fbits;
   gd.ebits = std::max(0, gd.fbits - Db);
 
+  if (h->hio && (h->policy == 1 || B == 1)) {  // host buffers: the whole input first
+    TRY(stage_rows(h, 0, n, 0));
+    TRY(wait_rows(h, 0));
+  }
   if (h->policy == 1) {
     // absorbing index: the digit's fine buckets index the index, the
     // batches and the runs (sized by n, as for several batches)
@@ -1389,8 +1526,13 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
       }
     }
   }
+  if (h->hio) TRY(stage_rows(h, 0, std::min<long long>(M, n), 0));
   for (long long b = 0; b < B; ++b) {
     long long m = std::min(M, n - b * M);
+    if (h->hio) {  // copy batch b + 1 while batch b is grouped
+      if (b + 1 < B) TRY(stage_rows(h, (b + 1) * M, std::min<long long>(n, (b + 2) * M), (size_t)b + 1));
+      TRY(wait_rows(h, (size_t)b));
+    }
     RowSrc bs = raw;
     bs.key = raw.key;
     // shift the raw source to the batch: offset applies to every column
@@ -1993,32 +2135,43 @@ sgagg_status sgagg_aggregate_host(sgagg_t h, const sgagg_keys* keys, const int64
   if (!rows) return fail(h, SGAGG_EINVAL, "null rows");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   h->err.clear();
-  // device copies of the inputs
+  TRY(ensure_ctx_device(h));
+  if (!h->copy_stream) CU(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+  // device buffers for the inputs (filled batch by batch) and the output
+  HostIO io;
+  io.copy = h->copy_stream;
+  io.nk = keys->n_cols;
   sgagg_keys dk = *keys;
   const void* dkc[kMaxKeyCols];
-  std::vector<const int64_t*> dp(std::max(1, (int)n_payload), nullptr);
   for (int c = 0; c < keys->n_cols; ++c) {
-    size_t bytes = (size_t)n * keys->bytes[c];
-    TRY(grow(h, h->in_keys[c], bytes));
-    if (bytes) CU(cudaMemcpyAsync(h->in_keys[c].p, keys->cols[c], bytes, cudaMemcpyHostToDevice, st));
+    TRY(grow(h, h->in_keys[c], (size_t)std::max(1ll, (long long)n) * keys->bytes[c]));
     dkc[c] = h->in_keys[c].p;
+    io.hkeys[c] = keys->cols[c];
+    io.kb[c] = keys->bytes[c];
+    io.dkeys[c] = h->in_keys[c].p;
   }
   dk.cols = dkc;
   if ((int)h->in_pay.size() < n_payload) h->in_pay.resize(n_payload);
-  std::vector<bool> used(std::max(1, (int)n_payload), false);
+  std::unique_ptr<bool[]> used(new bool[std::max(1, (int)n_payload)]());
   for (int a = 0; a < spec->n_aggs; ++a)
     if (spec->aggs[a].op != SGAGG_COUNT) used[spec->aggs[a].col] = true;
+  std::vector<int64_t*> dp(std::max(1, (int)n_payload), nullptr);
   for (int c = 0; c < n_payload; ++c) {
     if (!used[c]) continue;
-    TRY(grow(h, h->in_pay[c], (size_t)n * 8));
-    if (n) CU(cudaMemcpyAsync(h->in_pay[c].p, payload_cols[c], (size_t)n * 8, cudaMemcpyHostToDevice, st));
+    TRY(grow(h, h->in_pay[c], (size_t)std::max(1ll, (long long)n) * 8));
     dp[c] = P<int64_t>(h->in_pay[c]);
   }
+  io.np = n_payload;
+  io.hpay = payload_cols;
+  io.used = used.get();
+  io.dpay = dp.data();
   long long cap = std::min<long long>(out_capacity, n);
   void* dok[kMaxKeyCols];
   for (int c = 0; c < keys->n_cols; ++c) {
     TRY(grow(h, h->out_keys[c], (size_t)std::max(1ll, cap) * keys->bytes[c]));
     dok[c] = h->out_keys[c].p;
+    io.hout_keys[c] = out_keys[c];
+    io.dout_keys[c] = dok[c];
   }
   if ((int)h->out_cols.size() < spec->n_aggs) h->out_cols.resize(spec->n_aggs);
   std::vector<int64_t*> doa(std::max(1, spec->n_aggs), nullptr);
@@ -2026,16 +2179,32 @@ sgagg_status sgagg_aggregate_host(sgagg_t h, const sgagg_keys* keys, const int64
     TRY(grow(h, h->out_cols[a], (size_t)std::max(1ll, cap) * 8));
     doa[a] = P<int64_t>(h->out_cols[a]);
   }
-  s = aggregate_device(h, &dk, dp.data(), n_payload, n, spec, dok, doa.data(), cap, st);
+  io.S = spec->n_aggs;
+  io.hout_aggs = out_aggs;
+  io.dout_aggs = doa.data();
+  io.capacity = cap;
+  // the copy stream starts after the caller's earlier work on `st`
+  cudaEvent_t start;
+  TRY(io_event(h, 0, &start));
+  CU(cudaEventRecord(start, st));
+  CU(cudaStreamWaitEvent(io.copy, start, 0));
+  h->hio = &io;
+  std::vector<const int64_t*> dpc(dp.begin(), dp.end());
+  s = aggregate_device(h, &dk, dpc.data(), n_payload, n, spec, dok, doa.data(), cap, st);
+  if (s == SGAGG_OK) {
+    // the rows not copied back yet (all of them unless the final merge ran in parts)
+    cudaEvent_t done;
+    s = io_event(h, 0, &done);
+    if (s == SGAGG_OK && cudaEventRecord(done, st) != cudaSuccess) s = fail(h, SGAGG_ECUDA, "event record failed");
+    if (s == SGAGG_OK) s = unstage_rows(h, io.copied_out, h->last_rows, done);
+  }
+  h->hio = nullptr;
+  cudaError_t e1 = cudaStreamSynchronize(io.copy);
+  cudaError_t e2 = cudaStreamSynchronize(st);
   h->pending_err = (int)s;
   if (s != SGAGG_OK) return s;
-  long long r = h->last_rows;
-  for (int c = 0; c < keys->n_cols; ++c)
-    if (r) CU(cudaMemcpyAsync(out_keys[c], dok[c], (size_t)r * keys->bytes[c], cudaMemcpyDeviceToHost, st));
-  for (int a = 0; a < spec->n_aggs; ++a)
-    if (r) CU(cudaMemcpyAsync(out_aggs[a], doa[a], (size_t)r * 8, cudaMemcpyDeviceToHost, st));
-  CU(cudaStreamSynchronize(st));
-  *rows = r;
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(h, SGAGG_ECUDA, "%s", cudaGetErrorString(e1 ? e1 : e2));
+  *rows = h->last_rows;
   return SGAGG_OK;
 }
 

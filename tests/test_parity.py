@@ -213,6 +213,43 @@ def test_host_buffers_entry_point():
         np.testing.assert_array_equal(oa[a], ra[a])
 
 
+@pytest.mark.parametrize("case", ["batches", "one_batch", "composite", "absorbing", "empty", "many_parts",
+                                  "pinned"])
+def test_host_buffers_staged(case):
+    """Host-buffer calls copy the input batch by batch and the merged output
+    back in parts; every layout gives the oracle's result."""
+    aggs = [(0, 0), (1, 0), (2, 1), (3, 1)]
+    opts, M = {}, 30_000
+    if case == "composite":
+        c = datagen.config2(n=120_000)
+        kc = [to_np(k) for k in c["key_cols"]]
+        pc = [to_np(p) for p in c["payload"]]
+        aggs, M = c["aggs"], 7_000
+    else:
+        n = {"batches": 200_003, "one_batch": 20_000, "absorbing": 150_000, "empty": 0,
+             "many_parts": 400_000, "pinned": 123_457}[case]
+        c = datagen.config5_request(dict(rows=n, D=max(1, n // 3), seed=17), M=M)
+        kc = [to_np(c["key_cols"][0])]
+        pc = [to_np(p) for p in c["payload"]]
+        if case == "absorbing":
+            opts = dict(policy=1, absorb_batch=11_000)
+        if case == "many_parts":
+            M = 9_000
+    if case == "pinned":
+        kc = [torch.from_numpy(k).pin_memory().numpy() for k in kc]
+        pc = [torch.from_numpy(p).pin_memory().numpy() for p in pc]
+    agg = sgagg.Aggregator(M, **opts)
+    try:
+        ok, oa = agg.aggregate_host(kc, pc, aggs)
+    finally:
+        agg.close()
+    rk, ra = oracle.aggregate(kc, pc, aggs)
+    for a, b in zip(ok, rk):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(oa, ra):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_handle_reuse_across_shapes():
     agg = sgagg.Aggregator(30_000)
     try:
