@@ -43,6 +43,8 @@ def lib():
         L.orc_run_generation.restype = i64
         L.orc_absorb_runs.argtypes = [P, i64, i64, i64, i32, P, i32, P, P, P, P]
         L.orc_absorb_runs.restype = i64
+        L.orc_count_distinct.argtypes = [P, P, i64, i32, P, i32, P, P, P, P, P]
+        L.orc_count_distinct.restype = i64
         _lib = L
     return _lib
 
@@ -160,6 +162,25 @@ def absorb_runs(keys, payload, aggs, M, B):
     if r < 0:
         raise ValueError("bad absorbing run-generation arguments")
     return [int(x) for x in run_rows[:r]], int(left.value)
+
+
+def count_distinct(key_cols, ucol, payload, aggs):
+    """count(distinct u) per group of the key columns, with aggs over all
+    rows of each group: (group key columns, distinct counts, agg arrays)."""
+    widths = [np.asarray(c).dtype.itemsize for c in key_cols]
+    g = normalize(key_cols)
+    u = np.ascontiguousarray(np.asarray(ucol).astype(np.uint64))
+    payload = [np.ascontiguousarray(p, dtype=np.int64) for p in payload]
+    n = len(g)
+    ops, cols = _agg_arrays(aggs)
+    ok = np.empty(max(n, 1), dtype=np.uint64)
+    od = np.empty(max(n, 1), dtype=np.int64)
+    oa = [np.empty(max(n, 1), dtype=np.int64) for _ in aggs]
+    r = lib().orc_count_distinct(g.ctypes.data, u.ctypes.data, n, len(payload), _ptrs(payload), len(aggs),
+                                 ops.ctypes.data, cols.ctypes.data, ok.ctypes.data, od.ctypes.data, _ptrs(oa))
+    if r < 0:
+        raise ValueError("bad count-distinct arguments")
+    return ([unpack(ok[:r], widths, c) for c in range(len(key_cols))], od[:r].copy(), [a[:r].copy() for a in oa])
 
 
 def aggregate(key_cols, payload, aggs):

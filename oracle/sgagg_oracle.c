@@ -293,3 +293,50 @@ int64_t orc_absorb_runs(const uint64_t *keys, int64_t n, int64_t M, int64_t B, i
     free(ok); free(nk); free(os); free(ns); free(bk); free(bsd);
     return runs;
 }
+
+/*
+ * count(distinct u) per group g, with the other aggregates over all rows of
+ * g (the duplicate removal followed by grouping of Sec. 7, Hypothesis 6):
+ * the plain definition -- sort the (g, u, row) triples, walk them once; a
+ * new g opens an output row, a new (g, u) pair adds one distinct value, and
+ * every row is folded into its g.  gkeys are normalized group keys, ukeys
+ * the distinct column.  out_distinct[g] receives the distinct count.
+ * Returns the number of groups, or -1 on a bad argument.
+ */
+typedef struct { uint64_t g, u; int64_t row; } orc_triple;
+
+static int orc_cmp_triple(const void *pa, const void *pb)
+{
+    const orc_triple *a = (const orc_triple *)pa, *b = (const orc_triple *)pb;
+    if (a->g != b->g) return a->g < b->g ? -1 : 1;
+    if (a->u != b->u) return a->u < b->u ? -1 : 1;
+    return (a->row > b->row) - (a->row < b->row);
+}
+
+int64_t orc_count_distinct(const uint64_t *gkeys, const uint64_t *ukeys, int64_t n, int n_pay,
+                           const int64_t *const *pay, int n_aggs, const int32_t *ops, const int32_t *cols,
+                           uint64_t *out_keys, int64_t *out_distinct, int64_t *const *out_aggs)
+{
+    for (int a = 0; a < n_aggs; ++a) {
+        if (ops[a] < ORC_COUNT || ops[a] > ORC_MAX) return -1;
+        if (ops[a] != ORC_COUNT && (cols[a] < 0 || cols[a] >= n_pay)) return -1;
+    }
+    if (n <= 0) return 0;
+    orc_triple *t = (orc_triple *)malloc((size_t)n * sizeof(orc_triple));
+    if (!t) return -1;
+    for (int64_t i = 0; i < n; ++i) { t[i].g = gkeys[i]; t[i].u = ukeys[i]; t[i].row = i; }
+    qsort(t, (size_t)n, sizeof(orc_triple), orc_cmp_triple);
+    int64_t g = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        const int new_g = (i == 0) || (t[i].g != t[i - 1].g);
+        const int new_u = new_g || (t[i].u != t[i - 1].u);
+        if (new_g) { ++g; out_keys[g] = t[i].g; out_distinct[g] = 0; }
+        if (new_u) ++out_distinct[g];
+        for (int a = 0; a < n_aggs; ++a) {
+            int64_t v = orc_init_value(ops[a], ops[a] == ORC_COUNT ? 0 : pay[cols[a]][t[i].row]);
+            out_aggs[a][g] = new_g ? v : orc_combine(ops[a], out_aggs[a][g], v);
+        }
+    }
+    free(t);
+    return g + 1;
+}
