@@ -196,6 +196,26 @@ sgagg_status sgagg_aggregate_host(sgagg_t h, const sgagg_keys *keys,
                                   void *const *out_keys, int64_t *const *out_aggs,
                                   int64_t out_capacity, int64_t *rows, void *stream);
 
+/*
+ * count(distinct u) per group (Sec. 7: duplicate removal followed by
+ * grouping; Hypothesis 6: one sort serves both).  One grouping on the
+ * composite key (group columns, u) removes duplicate (g, u) pairs -- its
+ * sorted output is an interesting ordering for g -- and one in-stream pass
+ * over it regroups on g without sorting again.  Output per distinct g, in
+ * ascending order: the group key columns (out_keys, as in sgagg_aggregate),
+ * out_distinct[i] = the number of distinct u (device int64), and every
+ * aggregate of `spec` over all rows of the group.  u is one unsigned column
+ * of distinct_bytes (1, 2, 4 or 8) bytes; group columns plus u must fit 8
+ * bytes (SGAGG_EINVAL otherwise).  The memory budget and policy of the
+ * handle apply to the first grouping.  sgagg_result_rows gives the number
+ * of groups.
+ */
+sgagg_status sgagg_aggregate_distinct(sgagg_t h, const sgagg_keys *keys, const void *distinct_col,
+                                      int32_t distinct_bytes, const int64_t *const *payload_cols,
+                                      int32_t n_payload, int64_t n, const sgagg_spec *spec,
+                                      void *const *out_keys, int64_t *out_distinct,
+                                      int64_t *const *out_aggs, int64_t out_capacity, void *stream);
+
 /* Synchronize the stream of the last call and return its number of output
  * rows (distinct keys), or the device-side error of that call. */
 sgagg_status sgagg_result_rows(sgagg_t h, int64_t *rows);

@@ -844,4 +844,91 @@ __global__ void k_split_at(const unsigned long long* tkeys, const long long* p, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// count(distinct u) per g: rows sorted by the composite key (g, u), each
+// (g, u) once, are regrouped on g = key >> ubits in one pass, without a sort
+// (the interesting ordering of Sec. 7).  A block takes kRegroupRows rows, a
+// thread kRegroupRows / 256 consecutive ones; output slots are group ranks
+// (heads before the block + heads before the row), and every thread folds
+// its piece of each group it touches into the slot with integer atomics.
+// ---------------------------------------------------------------------------
+constexpr int kRegroupRows = 4096;
+
+__device__ __forceinline__ bool regroup_head(const unsigned long long* keys, long long i, int ubits) {
+  return i == 0 || (keys[i] >> ubits) != (keys[i - 1] >> ubits);
+}
+
+// heads[b] = rows of block b that open a group
+__global__ void __launch_bounds__(256)
+k_regroup_count(const unsigned long long* keys, long long n, int ubits, long long* heads) {
+  __shared__ int s_c;
+  if (threadIdx.x == 0) s_c = 0;
+  __syncthreads();
+  const long long r0 = blockIdx.x * (long long)kRegroupRows, r1 = min(n, r0 + kRegroupRows);
+  int c = 0;
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) c += regroup_head(keys, i, ubits);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_c, c);
+  __syncthreads();
+  if (threadIdx.x == 0) heads[blockIdx.x] = s_c;
+}
+
+// Output slots [0, groups): distinct counts 0, aggregates at their identity.
+__global__ void k_regroup_init(long long* distinct, OutSink out, FoldDesc fd, long long groups) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
+       g += (long long)gridDim.x * blockDim.x) {
+    distinct[g] = 0;
+    for (int a = 0; a < fd.n_state; ++a) out.cols[a][g] = op_identity(fd.op[a]);
+  }
+}
+
+__device__ __forceinline__ void regroup_flush(long long slot, long long cnt, const long long* acc, OutSink& out,
+                                              const FoldDesc& fd, long long* distinct) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(distinct + slot), (unsigned long long)cnt);
+  for (int a = 0; a < fd.n_state; ++a) {
+    long long* p = out.cols[a] + slot;
+    if (fd.op[a] == OP_SUM) atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)acc[a]);
+    else if (fd.op[a] == OP_MIN) atomicMin(p, acc[a]);
+    else atomicMax(p, acc[a]);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_regroup_fold(const unsigned long long* keys, CopySrc states, long long n, int ubits, FoldDesc fd,
+               const long long* base, OutSink out, long long* distinct) {
+  constexpr int R = kRegroupRows / 256;
+  __shared__ int ws[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long r0 = min(n, blockIdx.x * (long long)kRegroupRows + threadIdx.x * R), r1 = min(n, r0 + R);
+  int mine = 0;
+  for (long long i = r0; i < r1; ++i) mine += regroup_head(keys, i, ubits);
+  // block exclusive scan of the heads per thread
+  int x = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  int before = 0;
+  for (int k = 0; k < w; ++k) before += ws[k];
+  long long slot = base[blockIdx.x] + before + x - mine - 1;  // the group open at r0 (-1: none)
+  long long acc[kMaxCols];
+  long long cnt = 0;
+  for (long long i = r0; i < r1; ++i) {
+    if (regroup_head(keys, i, ubits)) {
+      if (cnt > 0 && slot >= 0 && slot < out.capacity) regroup_flush(slot, cnt, acc, out, fd, distinct);
+      ++slot;
+      cnt = 0;
+      if (slot < out.capacity) sink_key(out, slot, keys[i] >> ubits);
+    }
+    for (int a = 0; a < fd.n_state; ++a) {
+      const long long v = states.cols[a][i];
+      acc[a] = cnt == 0 ? v : op_combine(fd.op[a], acc[a], v);
+    }
+    ++cnt;
+  }
+  if (cnt > 0 && slot >= 0 && slot < out.capacity) regroup_flush(slot, cnt, acc, out, fd, distinct);
+}
+
 }  // namespace sg

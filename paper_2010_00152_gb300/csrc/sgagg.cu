@@ -144,6 +144,8 @@ struct sgagg_ctx {
   DevBuf bdirect;                            // batched call: chunks of the one-chunk instances
   std::vector<DevBuf> bcols, bout_cols;
   DevBuf ab_keys[3], ab_offs[3], ab_tmp;   // absorbing policy: index, batch, merged index
+  DevBuf dk_keys, rg_heads;                // count(distinct): (g, u) rows, regroup block heads
+  std::vector<DevBuf> dk_cols;
   std::vector<DevBuf> ab_cols[3];
   DevBuf marena_keys;            // runs written by preliminary merges
   std::vector<DevBuf> marena_cols;
@@ -1362,7 +1364,8 @@ sgagg_status absorb_device(sgagg_t h, const RowSrc& raw, long long n, const Fold
 // The whole operation on device-resident inputs.
 sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* const* payload_cols,
                               int32_t n_payload, int64_t n, const sgagg_spec* spec, void* const* out_keys,
-                              int64_t* const* out_aggs, int64_t out_capacity, cudaStream_t stream) {
+                              int64_t* const* out_aggs, int64_t out_capacity, cudaStream_t stream,
+                              const KeyOut* kout_override = nullptr) {
   h->stream = stream;
   h->have_call = true;
   h->st = sgagg_stats_t{};
@@ -1411,7 +1414,7 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
 
   OutSink user{};
   user.user = 1;
-  user.kout = kout;
+  user.kout = kout_override ? *kout_override : kout;
   for (int a = 0; a < S; ++a) user.cols[a] = reinterpret_cast<long long*>(out_aggs[a]);
   user.capacity = out_capacity;
   user.offs = nullptr;
@@ -2208,6 +2211,109 @@ sgagg_status sgagg_aggregate_host(sgagg_t h, const sgagg_keys* keys, const int64
   return SGAGG_OK;
 }
 
+// count(distinct u) per g (Sec. 7, Hypothesis 6): one grouping on the
+// composite key (g, u) removes duplicate pairs and leaves them sorted by g,
+// then one in-stream pass regroups on g.
+sgagg_status aggregate_distinct(sgagg_t h, const sgagg_keys* keys, const void* dcol, int32_t dbytes,
+                                const int64_t* const* payload_cols, int32_t n_payload, int64_t n,
+                                const sgagg_spec* spec, void* const* out_keys, int64_t* out_distinct,
+                                int64_t* const* out_aggs, int64_t out_capacity, cudaStream_t stream) {
+  if (!keys || keys->n_cols < 1 || keys->n_cols + 1 > kMaxKeyCols)
+    return fail(h, SGAGG_EINVAL, "bad group key columns");
+  if (dbytes != 1 && dbytes != 2 && dbytes != 4 && dbytes != 8) return fail(h, SGAGG_EINVAL, "distinct column width must be 1, 2, 4 or 8");
+  if (n > 0 && !dcol) return fail(h, SGAGG_EINVAL, "null distinct column");
+  if (!out_distinct) return fail(h, SGAGG_EINVAL, "null out_distinct");
+  int gbytes = 0;
+  for (int c = 0; c < keys->n_cols; ++c) gbytes += keys->bytes[c];
+  if (gbytes + dbytes > 8) return fail(h, SGAGG_EINVAL, "group key plus distinct column wider than 8 bytes");
+  int32_t cb[kMaxKeyCols];
+  const void* cc[kMaxKeyCols];
+  for (int c = 0; c < keys->n_cols; ++c) {
+    cb[c] = keys->bytes[c];
+    cc[c] = keys->cols[c];
+  }
+  cb[keys->n_cols] = dbytes;
+  cc[keys->n_cols] = dcol;
+  sgagg_keys ck{keys->n_cols + 1, cb, cc};
+  const int S = spec->n_aggs;
+  TRY(ensure_ctx_device(h));
+  TRY(grow(h, h->dk_keys, (size_t)std::max(1ll, (long long)n) * 8));
+  TRY(grow_cols(h, h->dk_cols, S, (size_t)std::max(1ll, (long long)n) * 8));
+  std::vector<int64_t*> dka(std::max(1, S), nullptr);
+  for (int a = 0; a < S; ++a) dka[a] = P<int64_t>(h->dk_cols[a]);
+  KeyOut canon{};
+  canon.n_cols = 1;
+  canon.bytes[0] = 8;
+  canon.shift[0] = 0;
+  canon.cols[0] = h->dk_keys.p;
+  // 1. group on (g, u): duplicate (g, u) pairs removed, rows sorted by g
+  TRY(aggregate_device(h, &ck, payload_cols, n_payload, n, spec, nullptr, dka.data(), n, stream, &canon));
+  const long long rows1 = h->last_rows;
+  h->key_bytes = gbytes;
+  h->last_rows = 0;
+  h->st.out_rows = 0;
+  if (rows1 == 0) return SGAGG_OK;
+  // 2. regroup on g in one pass over the sorted rows
+  const int ubits = 8 * dbytes;
+  const long long nblk = (rows1 + kRegroupRows - 1) / kRegroupRows;
+  TRY(grow(h, h->rg_heads, (size_t)(2 * nblk + 1) * 8));
+  long long* heads = P<long long>(h->rg_heads);
+  long long* base = heads + nblk;
+  kbegin(h, SGAGG_K_OTHER);
+  k_regroup_count<<<(unsigned)nblk, 256, 0, stream>>>(P<unsigned long long>(h->dk_keys), rows1, ubits, heads);
+  k_excl_scan<<<1, kPartThreads, 0, stream>>>(heads, (int)nblk, base);
+  kend(h);
+  CU(cudaGetLastError());
+  HostSmall* hs = hsmall(h);
+  TRY(sync_read(h, &hs->v[0], base + nblk, 8));
+  const long long groups = hs->v[0];
+  if (groups > out_capacity)
+    return fail(h, SGAGG_ECAPACITY, "out_capacity is smaller than the number of distinct keys");
+  FoldDesc fd{};  // the (g, u) rows' aggregates fold like runs do: counts and sums add
+  fd.n_state = S;
+  for (int a = 0; a < S; ++a) {
+    const int op = spec->aggs[a].op;
+    fd.src[a] = (int8_t)a;
+    fd.op[a] = (op == SGAGG_COUNT || op == SGAGG_SUM) ? OP_SUM : (op == SGAGG_MIN ? OP_MIN : OP_MAX);
+  }
+  OutSink user{};
+  user.user = 1;
+  KeyCols gk;
+  build_keycols(keys, &gk, &user.kout, out_keys);
+  for (int a = 0; a < S; ++a) user.cols[a] = reinterpret_cast<long long*>(out_aggs[a]);
+  user.capacity = out_capacity;
+  CopySrc states{};
+  states.keys = P<unsigned long long>(h->dk_keys);
+  for (int a = 0; a < S; ++a) states.cols[a] = P<long long>(h->dk_cols[a]);
+  kbegin(h, SGAGG_K_OTHER);
+  k_regroup_init<<<std::max(1, std::min(h->num_sms * 4, (int)((groups + 255) / 256))), 256, 0, stream>>>(
+      reinterpret_cast<long long*>(out_distinct), user, fd, groups);
+  k_regroup_fold<<<(unsigned)nblk, 256, 0, stream>>>(P<unsigned long long>(h->dk_keys), states, rows1, ubits, fd,
+                                                    base, user, reinterpret_cast<long long*>(out_distinct));
+  kend(h);
+  CU(cudaGetLastError());
+  h->st.class_launches[SGAGG_K_OTHER] += 2;
+  h->st.kernel_launches += 2;
+  kbytes(h, SGAGG_K_OTHER, rows1 * 8ll * (2 + S) + groups * (gbytes + 8ll * (1 + S)));
+  h->last_rows = groups;
+  h->st.out_rows = groups;
+  return SGAGG_OK;
+}
+
+sgagg_status sgagg_aggregate_distinct(sgagg_t h, const sgagg_keys* keys, const void* distinct_col,
+                                      int32_t distinct_bytes, const int64_t* const* payload_cols,
+                                      int32_t n_payload, int64_t n, const sgagg_spec* spec, void* const* out_keys,
+                                      int64_t* out_distinct, int64_t* const* out_aggs, int64_t out_capacity,
+                                      void* stream) {
+  sgagg_status s = validate(h, keys, payload_cols, n_payload, n, spec, out_keys, out_aggs, out_capacity);
+  if (s != SGAGG_OK) return s;
+  h->err.clear();
+  s = aggregate_distinct(h, keys, distinct_col, distinct_bytes, payload_cols, n_payload, n, spec, out_keys,
+                         out_distinct, out_aggs, out_capacity, reinterpret_cast<cudaStream_t>(stream));
+  h->pending_err = (int)s;
+  return s;
+}
+
 sgagg_status sgagg_result_rows(sgagg_t h, int64_t* rows) {
   if (!h || !rows) return SGAGG_EINVAL;
   if (!h->have_call) return fail(h, SGAGG_ESTATE, "no aggregate call yet");
@@ -2268,6 +2374,7 @@ void sgagg_destroy(sgagg_t h) {
     free_buf(h->ab_keys[i]); free_buf(h->ab_offs[i]); fv(h->ab_cols[i]);
   }
   free_buf(h->ab_tmp);
+  free_buf(h->dk_keys); free_buf(h->rg_heads); fv(h->dk_cols);
   free_buf(h->binst); free_buf(h->bchunks); free_buf(h->bkeys); free_buf(h->bout_keys);
   free_buf(h->bseg); free_buf(h->brange); free_buf(h->bstartb); free_buf(h->bdirect);
   fv(h->bcols); fv(h->bout_cols);

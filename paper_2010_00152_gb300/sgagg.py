@@ -118,6 +118,9 @@ def lib():
         for f in ("sgagg_create", "sgagg_set_option", "sgagg_aggregate", "sgagg_aggregate_host",
                   "sgagg_result_rows", "sgagg_stats", "sgagg_aggregate_batched"):
             getattr(L, f).restype = i32
+        L.sgagg_aggregate_distinct.argtypes = [vp, ctypes.POINTER(sgagg_keys), vp, i32, vp, i32, i64,
+                                               ctypes.POINTER(sgagg_spec), vp, vp, vp, i64, vp]
+        L.sgagg_aggregate_distinct.restype = i32
         dp = ctypes.POINTER(ctypes.c_double)
         L.sgagg_request_footprint.argtypes = [i64, i32, i32, i32, i64, i64]
         L.sgagg_request_footprint.restype = i64
@@ -224,6 +227,17 @@ def sgagg_aggregate_host(h, key_ptrs, key_bytes, payload_ptrs, n, aggs, out_key_
                                     ctypes.byref(rows), ctypes.c_void_p(stream))
     _check(h, st)
     return int(rows.value)
+
+
+def sgagg_aggregate_distinct(h, key_ptrs, key_bytes, distinct_ptr, distinct_bytes, payload_ptrs, n, aggs,
+                             out_key_ptrs, out_distinct_ptr, out_agg_ptrs, out_capacity, stream=0):
+    """Raw call with integer device pointers: count(distinct u) per group."""
+    a = _Args(key_ptrs, key_bytes, payload_ptrs, aggs, out_key_ptrs, out_agg_ptrs)
+    st = lib().sgagg_aggregate_distinct(h, ctypes.byref(a.keys), ctypes.c_void_p(distinct_ptr), int(distinct_bytes),
+                                        a.pay, len(payload_ptrs), int(n), ctypes.byref(a.spec), a.ok,
+                                        ctypes.c_void_p(out_distinct_ptr), a.oa, int(out_capacity),
+                                        ctypes.c_void_p(stream))
+    _check(h, st)
 
 
 NOALLOC_MAX_ROWS = 8192
@@ -341,6 +355,23 @@ class Aggregator:
 
     def temp_bytes(self):
         return sgagg_temp_bytes(self.h)
+
+    def aggregate_distinct(self, key_cols, ucol, payload, aggs, capacity=None):
+        """count(distinct ucol) per group of key_cols, with aggs over all rows
+        of each group.  Returns (group key columns, distinct counts, aggs)."""
+        import torch
+        n = int(key_cols[0].numel()) if key_cols else 0
+        cap = n if capacity is None else int(capacity)
+        dev = key_cols[0].device
+        ok = [torch.empty(max(1, cap), dtype=k.dtype, device=dev) for k in key_cols]
+        od = torch.empty(max(1, cap), dtype=torch.int64, device=dev)
+        oa = [torch.empty(max(1, cap), dtype=torch.int64, device=dev) for _ in aggs]
+        s = torch.cuda.current_stream(dev).cuda_stream
+        sgagg_aggregate_distinct(self.h, [k.data_ptr() for k in key_cols], [k.element_size() for k in key_cols],
+                                 ucol.data_ptr(), ucol.element_size(), [p.data_ptr() for p in payload], n, aggs,
+                                 [k.data_ptr() for k in ok], od.data_ptr(), [a.data_ptr() for a in oa], cap, s)
+        rows = sgagg_result_rows(self.h)
+        return [k[:rows] for k in ok], od[:rows], [a[:rows] for a in oa]
 
     def aggregate_host(self, key_cols, payload, aggs, capacity=None, stream=0):
         """Host numpy arrays in, host numpy arrays out (copies inside the call)."""
