@@ -541,7 +541,19 @@ k_scan2(const long long* bstart1, int nb2, const int* tfirst, unsigned* thist2, 
 // bstart[d] + table[d * ntiles + t].  Level 2: tile t is tiles[t] and the
 // cursor starts at table[t * nb + d].  Output: SoA (okeys/ocols) or rows of
 // 1 + ncols words (oaos).
-template <bool SEG>
+// 8-byte asynchronous copy, global to shared (completion: cp.async.wait_group).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Whether k_scatter_staged can copy the source with cp.async (DIRECT).
+__host__ __device__ inline bool staged_direct(const RowSrc& src) {
+  return src.kind == SRC_SOA ||
+         (src.kind == SRC_RAW && src.key.n_cols == 1 && src.key.bytes[0] == 8 && src.key_or == 0);
+}
+
+template <bool SEG, bool DIRECT>
 __global__ void __launch_bounds__(kPartThreads, 2)
 k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, const Tile2* tiles,
                  const int* ntiles_dev, const unsigned* table, const long long* bstart,
@@ -568,12 +580,39 @@ k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int nti
   }
   const int dsh = tiles ? 0 : dshift;
   constexpr int U = kStage / kPartThreads;  // 8
+  // 8-byte keys in one column (SoA, or raw uint64 keys): the sub-tile is
+  // copied into the stage by cp.async, global to shared without passing
+  // through registers, all of it in flight at once
+  constexpr bool direct = DIRECT;  // the host checked staged_direct(src)
+  const unsigned long long* dkeys =
+      src.kind == SRC_SOA ? src.keys : reinterpret_cast<const unsigned long long*>(src.key.cols[0]);
   for (long long s0 = lo; s0 < hi; s0 += kStage) {
     const int m = (int)min((long long)kStage, hi - s0);
-    for (int d = threadIdx.x; d < nb; d += blockDim.x) lst[d] = 0;
-    __syncthreads();
     unsigned dr[U];  // digit << 16 | rank
     unsigned long long kk[U];
+    if constexpr (direct) {
+      const long long r0 = src.offset + s0;
+      for (int i = threadIdx.x; i < m; i += kPartThreads) {
+        cp_async8(&skey[i], dkeys + r0 + i);
+        for (int c = 0; c < C; ++c) cp_async8(&scol[c * kStage + i], src.cols[c] + r0 + i);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) lst[d] = 0;
+    if constexpr (direct) {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = threadIdx.x + u * kPartThreads;
+        if (i < m) {
+          kk[u] = skey[i];
+          const unsigned d = level_digit<SEG>(dig, kk[u], dsh, nb);
+          dr[u] = (d << 16) | atomicAdd(&lst[d], 1u);
+        }
+      }
+    } else {
+    __syncthreads();
     // all loads of the sub-tile first (independent, in flight together) ...
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -617,6 +656,7 @@ k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int nti
         unsigned r = atomicAdd(&lst[d], 1u);
         dr[u] = (d << 16) | r;
       }
+    }
     }
     __syncthreads();
     // local starts: exclusive scan of the per-digit counts, two digits per

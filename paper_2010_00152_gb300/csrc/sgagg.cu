@@ -231,12 +231,24 @@ sgagg_status fail(sgagg_t h, sgagg_status s, const char* fmt, const char* a = ""
     if (s_ != SGAGG_OK) return s_;      \
   } while (0)
 
-// Partition kernels come in two forms, with and without a segmented digit.
+// Partition kernels come in two forms, with and without a segmented digit;
+// the staged scatter also in two, copying by cp.async or through registers.
 #define PART_CFG(...) __VA_ARGS__
 #define PART_LAUNCH(kern, cfg, args)                             \
   do {                                                           \
     if (dig.seg) kern<true><<<PART_CFG cfg>>>(PART_CFG args);    \
     else kern<false><<<PART_CFG cfg>>>(PART_CFG args);           \
+  } while (0)
+#define STAGED_LAUNCH(srcv, cfg, args)                                                            \
+  do {                                                                                            \
+    const bool dir_ = staged_direct(srcv);                                                        \
+    if (dig.seg) {                                                                                \
+      if (dir_) k_scatter_staged<true, true><<<PART_CFG cfg>>>(PART_CFG args);                     \
+      else k_scatter_staged<true, false><<<PART_CFG cfg>>>(PART_CFG args);                         \
+    } else {                                                                                      \
+      if (dir_) k_scatter_staged<false, true><<<PART_CFG cfg>>>(PART_CFG args);                    \
+      else k_scatter_staged<false, false><<<PART_CFG cfg>>>(PART_CFG args);                        \
+    }                                                                                             \
   } while (0)
 
 // Kernel-class bookkeeping: launches, compulsory bytes, optional event time.
@@ -444,10 +456,14 @@ void set_part_attrs() {
     cudaFuncSetAttribute(k_hist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
     cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
     cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
-    cudaFuncSetAttribute(k_scatter_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_scatter_staged<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)staged_smem_bytes(1 << kMaxCoarseBits > 1024 ? 1024 : 1 << kMaxCoarseBits, kStageCols));
+    cudaFuncSetAttribute(k_scatter_staged<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)staged_smem_bytes(1 << kMaxCoarseBits > 1024 ? 1024 : 1 << kMaxCoarseBits, kStageCols));
+    cudaFuncSetAttribute(k_scatter_staged<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)staged_smem_bytes(1 << kMaxCoarseBits > 1024 ? 1024 : 1 << kMaxCoarseBits, kStageCols));
     cudaFuncSetAttribute(k_hist2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_scatter_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_scatter_staged<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)staged_smem_bytes(1 << kMaxCoarseBits > 1024 ? 1024 : 1 << kMaxCoarseBits, kStageCols));
     cudaFuncSetAttribute(k_hist2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     done = true;
@@ -707,7 +723,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     ++h->st.class_launches[SGAGG_K_PLAN];
     ++h->st.kernel_launches;
     kbegin(h, SGAGG_K_SCATTER);
-    PART_LAUNCH(k_scatter_staged, (ntiles, kPartThreads, staged_smem_bytes(nb1, C), h->stream),
+    STAGED_LAUNCH(src, (ntiles, kPartThreads, staged_smem_bytes(nb1, C), h->stream),
                 (src, n, dig, D2, nb1, ntiles, nullptr, nullptr, P<unsigned>(h->thist1[depth]),
                  P<long long>(h->bstart1[depth]), P<unsigned long long>(h->akeys[depth]),
                  reinterpret_cast<long long* const*>(h->acolptr[depth].p), nullptr));
@@ -733,7 +749,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
                                                 P<unsigned>(h->thist2[depth]), P<long long>(h->btot[depth]));
     kend(h);
     kbegin(h, SGAGG_K_SCATTER);
-    PART_LAUNCH(k_scatter_staged, ((int)nt2max, kPartThreads, staged_smem_bytes(nb2, C), h->stream),
+    STAGED_LAUNCH(a, ((int)nt2max, kPartThreads, staged_smem_bytes(nb2, C), h->stream),
                 (a, n, dig, 0, nb2, 0, P<Tile2>(h->tiles2[depth]), ntd, P<unsigned>(h->thist2[depth]), nullptr,
                  nullptr, nullptr, P<long long>(h->scatter[depth])));
     kend(h);
@@ -763,7 +779,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     kbytes(h, SGAGG_K_PLAN, (long long)nb * ntiles * 8 + (long long)nb * (8 + 8 + sizeof(Chunk)));
     kbegin(h, SGAGG_K_SCATTER);
     if (staged && Db <= kLevel1Bits)
-      PART_LAUNCH(k_scatter_staged, (ntiles, kPartThreads, staged_smem_bytes(nb, C), h->stream),
+      STAGED_LAUNCH(src, (ntiles, kPartThreads, staged_smem_bytes(nb, C), h->stream),
                   (src, n, dig, 0, nb, ntiles, nullptr, nullptr, P<unsigned>(h->thist[depth]),
                    P<long long>(h->bstart[depth]), nullptr, nullptr, P<long long>(h->scatter[depth])));
     else
