@@ -96,6 +96,33 @@ __device__ __forceinline__ long long src_col(const RowSrc& s, int c, int64_t i) 
   return __ldg(s.cols[c] + r);
 }
 
+// 8-byte asynchronous copy, global to shared (completion: cp_async_wait;
+// the copied words are visible to the issuing thread after it, to the
+// others after a barrier).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Whether a source's keys are one column of 8-byte words (copied as is).
+__host__ __device__ inline bool src_keys_direct(const RowSrc& s) {
+  return s.kind == SRC_SOA || s.kind == SRC_AOS ||
+         (s.kind == SRC_RAW && s.key.n_cols == 1 && s.key.bytes[0] == 8 && s.key_or == 0);
+}
+
+// Address of row i's key for such a source.
+__device__ __forceinline__ const unsigned long long* src_key_ptr(const RowSrc& s, int64_t i) {
+  const int64_t r = s.offset + i;
+  if (s.kind == SRC_AOS) return reinterpret_cast<const unsigned long long*>(s.aos + r * (1 + s.ncols));
+  if (s.kind == SRC_SOA) return s.keys + r;
+  return reinterpret_cast<const unsigned long long*>(s.key.cols[0]) + r;
+}
+
 struct FoldDesc {
   int n_state;
   int8_t src[kMaxCols];   // source column of state column s, -1 = constant 1

@@ -541,16 +541,9 @@ k_scan2(const long long* bstart1, int nb2, const int* tfirst, unsigned* thist2, 
 // bstart[d] + table[d * ntiles + t].  Level 2: tile t is tiles[t] and the
 // cursor starts at table[t * nb + d].  Output: SoA (okeys/ocols) or rows of
 // 1 + ncols words (oaos).
-// 8-byte asynchronous copy, global to shared (completion: cp.async.wait_group).
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
-}
-
 // Whether k_scatter_staged can copy the source with cp.async (DIRECT).
 __host__ __device__ inline bool staged_direct(const RowSrc& src) {
-  return src.kind == SRC_SOA ||
-         (src.kind == SRC_RAW && src.key.n_cols == 1 && src.key.bytes[0] == 8 && src.key_or == 0);
+  return src.kind != SRC_AOS && src_keys_direct(src);
 }
 
 template <bool SEG, bool DIRECT>
@@ -596,11 +589,10 @@ k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int nti
         cp_async8(&skey[i], dkeys + r0 + i);
         for (int c = 0; c < C; ++c) cp_async8(&scol[c * kStage + i], src.cols[c] + r0 + i);
       }
-      asm volatile("cp.async.commit_group;" ::: "memory");
     }
     for (int d = threadIdx.x; d < nb; d += blockDim.x) lst[d] = 0;
     if constexpr (direct) {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      cp_async_wait();
       __syncthreads();
 #pragma unroll
       for (int u = 0; u < U; ++u) {

@@ -217,6 +217,30 @@ __device__ __forceinline__ int run_advance(const SortSmem& s, int k, int r, int 
 template <int MODE>
 __device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, const RunSet& runs,
                                           const ChunkView& cv, unsigned long long* lmin, unsigned long long* lmax) {
+  if (MODE == MODE_RUNS || src_keys_direct(src)) {
+    // 8-byte keys: copied global to shared by cp.async, all in flight at once
+    int r = 0;
+    for (int i = threadIdx.x; i < cv.n; i += kThreads) {
+      const unsigned long long* p;
+      if (MODE == MODE_RUNS) {
+        r = run_advance(s, cv.k, r, i);
+        p = reinterpret_cast<const unsigned long long*>(runs.ptrs[(long long)r * (1 + runs.ncols)]) + s.slo[r] +
+            (i - s.spre[r]);
+      } else if (MODE == MODE_RANGE) {
+        p = reinterpret_cast<const unsigned long long*>(src.aos + (cv.lo + i) * (1 + src.ncols));
+      } else {
+        p = src_key_ptr(src, cv.lo + i);
+      }
+      cp_async8(&s.keys[i], p);
+    }
+    cp_async_wait();
+    for (int i = threadIdx.x; i < cv.n; i += kThreads) {  // the thread's own copies
+      const unsigned long long v = s.keys[i];
+      *lmin = v < *lmin ? v : *lmin;
+      *lmax = v > *lmax ? v : *lmax;
+    }
+    return;
+  }
   constexpr int U = 8;  // loads in flight per thread
   int r = 0;            // a thread's positions only grow: the run cursor only advances
   for (int base = threadIdx.x; base < cv.n; base += U * kThreads) {
@@ -621,35 +645,27 @@ __device__ __forceinline__ long long chunk_base(const LookBack& lb, const OutSin
 // ---------------------------------------------------------------------------
 __shared__ int g_lcnt[kWarps + 1];
 
-// Stage source column c of every chunk row (chunk order) into dst: one
-// coalesced pass with kU loads in flight per thread.
+// Stage source column c of every chunk row (chunk order) into dst: 8-byte
+// cp.async copies, global to shared, all in flight at once; complete when
+// it returns (visible to the other threads after a barrier).
 template <int MODE>
 __device__ __forceinline__ void stage_column(const SortSmem& s, const RowSrc& src, const RunSet& runs,
                                              const ChunkView& cv, int c, long long* dst) {
-  constexpr int U = 8;
   int r = 0;
-  for (int base = threadIdx.x; base < cv.n; base += U * kThreads) {
-    long long v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * kThreads;
-      if (i < cv.n) {
-        if (MODE == MODE_RUNS) {
-          r = run_advance(s, cv.k, r, i);
-          v[u] = __ldg(runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c] + s.slo[r] + (i - s.spre[r]));
-        } else if (MODE == MODE_RANGE) {
-          v[u] = src.aos[(cv.lo + i) * (1 + src.ncols) + 1 + c];
-        } else {
-          v[u] = src_col(src, c, cv.lo + i);
-        }
-      }
+  for (int i = threadIdx.x; i < cv.n; i += kThreads) {
+    const long long* p;
+    if (MODE == MODE_RUNS) {
+      r = run_advance(s, cv.k, r, i);
+      p = runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c] + s.slo[r] + (i - s.spre[r]);
+    } else if (MODE == MODE_RANGE) {
+      p = src.aos + (cv.lo + i) * (1 + src.ncols) + 1 + c;
+    } else {
+      const int64_t row = src.offset + cv.lo + i;
+      p = src.kind == SRC_AOS ? src.aos + row * (1 + src.ncols) + 1 + c : src.cols[c] + row;
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * kThreads;
-      if (i < cv.n) dst[i] = v[u];
-    }
+    cp_async8(&dst[i], p);
   }
+  cp_async_wait();
 }
 
 __device__ __forceinline__ bool head_bit(const uint32_t* hm, int p) { return (hm[p >> 5] >> (p & 31)) & 1u; }
