@@ -541,6 +541,12 @@ k_scan2(const long long* bstart1, int nb2, const int* tfirst, unsigned* thist2, 
 // bstart[d] + table[d * ntiles + t].  Level 2: tile t is tiles[t] and the
 // cursor starts at table[t * nb + d].  Output: SoA (okeys/ocols) or rows of
 // 1 + ncols words (oaos).
+// SoA output columns of a staged scatter, passed by value (no pointer table
+// to copy to the device before the launch).
+struct StageCols {
+  long long* c[kStageCols];
+};
+
 // Whether k_scatter_staged can copy the source with cp.async (DIRECT).
 __host__ __device__ inline bool staged_direct(const RowSrc& src) {
   return src.kind != SRC_AOS && src_keys_direct(src);
@@ -550,7 +556,7 @@ template <bool SEG, bool DIRECT>
 __global__ void __launch_bounds__(kPartThreads, 2)
 k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, const Tile2* tiles,
                  const int* ntiles_dev, const unsigned* table, const long long* bstart,
-                 unsigned long long* okeys, long long* const* ocols, long long* oaos) {
+                 unsigned long long* okeys, StageCols ocols, long long* oaos) {
   extern __shared__ __align__(16) unsigned char st_raw[];
   unsigned* cursor = reinterpret_cast<unsigned*>(st_raw);
   unsigned* lst = cursor + nb;
@@ -687,7 +693,7 @@ k_scatter_staged(RowSrc src, long long n, Digit dig, int dshift, int nb, int nti
         }
       } else {
         okeys[gp] = k;
-        for (int c = 0; c < C; ++c) ocols[c][gp] = scol[c * kStage + i];
+        for (int c = 0; c < C; ++c) ocols.c[c][gp] = scol[c * kStage + i];
       }
     }
     __syncthreads();
