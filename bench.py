@@ -293,6 +293,21 @@ def bench_batched(args, dev):
     return 0
 
 
+def reduce_over_ranks(ms, rows, device):
+    """Whole-job numbers over the replicas: the slowest rank's time per step
+    (max over ranks) and all ranks' rows per step (sum).  One process: as is."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), int(rows)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    r = torch.tensor([int(rows)], dtype=torch.int64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(r.item())
+
+
 def run_stream(srv_kw, specs, rate, dev, aggs, budget, pool):
     """Replay requests arriving at `rate` per second (Poisson; inf: all at
     once) into a server; each request's inputs are cut from device pools
@@ -490,12 +505,8 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = n * world / (ms_max / 1e3)
+    ms_max, rows_all = reduce_over_ranks(ms, n, dev)
+    value = rows_all / (ms_max / 1e3)
 
     st = agg.stats()
     peaks, peak_kind = load_peaks()

@@ -1,0 +1,47 @@
+"""The replica path of bench.py (one process per GPU, no data-path
+collective): whole-job rows/s = all ranks' rows / the slowest rank's time.
+Run as two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms, rows = bench.reduce_over_ranks(10.0 * (rank + 1), 1000 + rank, torch.device("cpu"))
+    q.put((rank, ms, rows))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_max_time_sum_rows():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out == [(0, 20.0, 2001), (1, 20.0, 2001)]
+
+
+def test_one_process_unchanged():
+    import bench
+    assert bench.reduce_over_ranks(3.5, 42, torch.device("cpu")) == (3.5, 42)
