@@ -381,32 +381,14 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
   // in registers (a thread's rows are i = threadIdx.x + j * kThreads)
   constexpr int EPT = kTileCap / kThreads;
   uint32_t br[EPT];  // bin << 16 | rank in bin
-  if (sh == 0) {
-    // every bin is one key value, and few keys make many lanes hit the
-    // same bin: lanes of a warp with equal bins share one atomic (block-uniform branch)
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-      const int i = threadIdx.x + j * kThreads;
-      const bool act = i < n;
-      const int b = act ? (int)(s.keys[i] - kmin) : -1;
-      const unsigned peers = __match_any_sync(0xffffffffu, b);
-      const int leader = __ffs(peers) - 1;
-      unsigned old = 0;
+  for (int j = 0; j < EPT; ++j) {
+    const int i = threadIdx.x + j * kThreads;
+    if (i < n) {
+      const int b = (int)((s.keys[i] - kmin) >> sh);
       const unsigned sft = (b & 1) * 16;
-      if (act && lane == leader) old = atomicAdd(&s.bins[b >> 1], (unsigned)__popc(peers) << sft);
-      old = __shfl_sync(0xffffffffu, old, leader);
-      if (act) br[j] = ((unsigned)b << 16) | (((old >> sft) + __popc(peers & ((1u << lane) - 1))) & 0xFFFFu);
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-      const int i = threadIdx.x + j * kThreads;
-      if (i < n) {
-        const int b = (int)((s.keys[i] - kmin) >> sh);
-        const unsigned sft = (b & 1) * 16;
-        const unsigned old = atomicAdd(&s.bins[b >> 1], 1u << sft);
-        br[j] = ((unsigned)b << 16) | ((old >> sft) & 0xFFFFu);
-      }
+      const unsigned old = atomicAdd(&s.bins[b >> 1], 1u << sft);
+      br[j] = ((unsigned)b << 16) | ((old >> sft) & 0xFFFFu);
     }
   }
   __syncthreads();
