@@ -86,7 +86,7 @@ typedef struct {
     const void *const *cols;     /* host array of device pointers, one per column */
 } sgagg_keys;
 
-/* Counters of the last sgagg_aggregate / sgagg_aggregate_batched call. */
+/* Counters of the last call on the handle (any grouping entry point). */
 typedef struct {
     int64_t n_rows;              /* input rows */
     int64_t batches;             /* ceil(n / memory_budget_rows) */
@@ -118,7 +118,9 @@ enum {
     SGAGG_K_PREFOLD = 4,    /* tile sort+fold before partitioning */
     SGAGG_K_RUNGEN = 5,     /* chunk sort+fold writing a run (or the output) */
     SGAGG_K_MERGE = 6,      /* wide merge: sort+fold of merge tiles */
-    SGAGG_K_OTHER = 7       /* gathers and offsets of split key ranges */
+    SGAGG_K_OTHER = 7       /* copies: gathers of split key ranges, the batched call's
+                               output copy, the absorbing index's runs, the
+                               count(distinct) regroup */
 };
 
 /* Options for sgagg_set_option. */
@@ -126,7 +128,7 @@ typedef enum {
     SGAGG_OPT_PREFOLD = 0,        /* -1 auto (sampled duplicate rate), 0 off, 1 on */
     SGAGG_OPT_ARENA_CAP = 1,      /* max bytes of runs kept in device memory; more spill
                                      to pinned host memory.  Default: no cap (-1). */
-    SGAGG_OPT_RADIX_BITS = 2,     /* bits of the batch partitioning digit, 0 = auto (1..16) */
+    SGAGG_OPT_RADIX_BITS = 2,     /* bits of the batch partitioning digit, 0 = auto (1..15) */
     SGAGG_OPT_SPIN_LIMIT = 3,     /* iteration cap of device-side waits (default 1<<26);
                                      exceeded -> SGAGG_ETIMEOUT, no hang */
     SGAGG_OPT_FANIN_CAP = 4,      /* max runs in one wide merge; more runs get preliminary
@@ -149,9 +151,10 @@ typedef enum {
 } sgagg_option;
 
 /*
- * Create a handle.  memory_budget_rows (M >= 1) is the number of input rows
- * in one batch of run generation, i.e. the paper's memory size in rows
- * (Sec. 3: read-sort-write cycles make runs of at most M rows).
+ * Create a handle.  memory_budget_rows (M >= 1) is the paper's memory size in
+ * rows (Sec. 3: read-sort-write cycles make runs of memory size): with the
+ * default policy the number of input rows in one batch of run generation,
+ * with SGAGG_OPT_POLICY 1 the most distinct keys the absorbing index holds.
  * Returns SGAGG_EINVAL for M < 1 or out == NULL.
  */
 sgagg_status sgagg_create(int64_t memory_budget_rows, sgagg_t *out);

@@ -2104,7 +2104,7 @@ sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
       return SGAGG_OK;
     case SGAGG_OPT_ARENA_CAP: h->arena_cap = value; return SGAGG_OK;
     case SGAGG_OPT_RADIX_BITS:
-      if (value < 0 || value > 16) return fail(h, SGAGG_EINVAL, "radix bits must be 0..16");
+      if (value < 0 || value > 15) return fail(h, SGAGG_EINVAL, "radix bits must be 0..15");
       h->radix_bits = (int)value;
       return SGAGG_OK;
     case SGAGG_OPT_SPIN_LIMIT:
