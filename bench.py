@@ -131,10 +131,13 @@ class ClockSampler:
 
 
 def src_sha():
+    """Hash of the device code (the kernel headers): the DRAM counters in
+    profiles/traffic.json hold only for the kernels they were taken on."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2010_00152_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+        if f.endswith(".cuh"):
+            h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
