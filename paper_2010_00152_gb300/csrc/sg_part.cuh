@@ -6,8 +6,8 @@
 //   k_hist     per-tile histogram of the coarse digit (one read of the keys);
 //   k_tilescan per bucket, exclusive scan over tiles -> each tile's write
 //              offset inside the bucket; bucket totals;
-//   k_plan     bucket starts, and a grouping of consecutive buckets into
-//              chunks of at most kTileCap rows; a bucket bigger than half a
+//   k_plan_*   bucket starts, and a grouping of consecutive buckets into
+//              chunks of at most kTileCap rows; a bucket of more than a
 //              chunk is set apart (solved separately, then copied in);
 //   k_scatter  every row written once to its bucket (rows of 1 + ncols words).
 // The same planner groups the fine buckets of the wide merge into merge
@@ -132,9 +132,10 @@ struct PlanInfo {
   long long max_chunk;
 };
 
-// Single CTA.  w[0..nb) are bucket row counts in key order.  Writes bstart
-// (exclusive prefix, nb + 1 entries), the chunk list and the indices of big
-// chunks.  A bucket with more than `big` rows is a chunk of its own: kind
+// The chunk plan (k_plan_* below).  w[0..nb) are bucket row counts in key
+// order.  It writes bstart (exclusive prefix, nb + 1 entries), the chunk list
+// and the indices of big chunks.  A bucket with more than `big` rows is a
+// chunk of its own: kind
 // CH_NORMAL up to `cap` rows, else CH_COPY (solved separately, listed in
 // big_list).  Other buckets are grouped while their exclusive prefix over
 // buckets of at most `big` rows stays in one multiple of `target`, so such a
@@ -155,153 +156,206 @@ __device__ __forceinline__ bool plan_is_start(long long x, long long big, long l
   return st;
 }
 
-// Exclusive sum over the 1024 threads of k_plan (32 warps); lane 31 of warp 0
-// writes the sum to *total (a shared or local slot of that thread).
-__device__ __forceinline__ long long plan_scan(long long v, long long* total) {
-  __shared__ long long ws[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+// ---------------------------------------------------------------------------
+// The same plan computed by several blocks (k_plan_*): block b owns buckets
+// [b * per, (b + 1) * per), a thread `sub` consecutive ones of them.
+//   sums:   per-block rows of all / small buckets and big-bucket count;
+//   scan3:  exclusive prefixes of the three (one block), totals into info;
+//   starts: chunk starts per block (they need the global small-row prefix);
+//   scan1:  exclusive prefix of the starts (one block), chunk count;
+//   apply:  bucket starts, chunk first buckets and kinds, the big list;
+//   finish: chunk ends, row ranges, fine ranges, the largest chunk.
+// ---------------------------------------------------------------------------
+constexpr int kPlanThreads = 256;
+
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  long long t = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+  return t;
+}
+
+// exclusive prefix of v over the block (blockDim.x <= 1024)
+__device__ __forceinline__ long long block_excl_ll(long long v, long long* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   long long x = v;
   for (int o = 1; o < 32; o <<= 1) {
-    long long y = __shfl_up_sync(0xffffffffu, x, o);
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
   __syncthreads();
-  if (lane == 31) ws[wid] = x;
+  if (lane == 31) red[w] = x;
   __syncthreads();
-  if (wid == 0) {
-    long long t = ws[lane], u = t;
-    for (int o = 1; o < 32; o <<= 1) {
-      long long y = __shfl_up_sync(0xffffffffu, u, o);
-      if (lane >= o) u += y;
-    }
-    ws[lane] = u - t;
-    if (lane == 31) *total = u;
-  }
-  __syncthreads();
-  long long r = ws[wid] + x - v;
-  __syncthreads();
-  return r;
+  long long before = 0;
+  for (int k = 0; k < w; ++k) before += red[k];
+  return before + x - v;
 }
 
-// One CTA of 1024 threads.  The bucket counts are taken in tiles of
-// 1024 x kPlanPer buckets, each read with coalesced loads into shared memory;
-// a thread owns kPlanPer consecutive buckets of the tile, and the running
-// prefixes (all rows, rows of small buckets, big buckets, chunk starts) and
-// the state of the tile's last bucket carry from tile to tile.
-constexpr int kPlanPer = 4;
+__global__ void __launch_bounds__(kPlanThreads)
+k_plan_sums(const long long* __restrict__ w, int nb, int per, int sub, long long big, long long cap, long long* part) {
+  __shared__ long long red[32];
+  const int d0 = min(nb, blockIdx.x * per + (int)threadIdx.x * sub), d1 = min(min(nb, (blockIdx.x + 1) * per), d0 + sub);
+  long long ta = 0, tb = 0, tc = 0;
+  for (int d = d0; d < d1; ++d) {
+    const long long x = w[d];
+    ta += x;
+    if (x > cap) tc += 1;
+    if (x <= big) tb += x;
+  }
+  ta = block_sum_ll(ta, red);
+  tb = block_sum_ll(tb, red);
+  tc = block_sum_ll(tc, red);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = ta;
+    part[3 * blockIdx.x + 1] = tb;
+    part[3 * blockIdx.x + 2] = tc;
+  }
+}
+
+// exclusive prefix over g entries of stride `stride` (one block of 1024)
+__device__ void scan_column(long long* v, int g, int stride, long long* total) {
+  __shared__ long long red[32];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < g; b0 += blockDim.x) {
+    const int b = b0 + threadIdx.x;
+    const long long x = b < g ? v[(long long)b * stride] : 0;
+    const long long ex = block_excl_ll(x, red);
+    const long long c = carry;
+    __syncthreads();
+    if (b < g) v[(long long)b * stride] = c + ex;
+    if (threadIdx.x == blockDim.x - 1) carry = c + ex + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
 __global__ void __launch_bounds__(1024)
-k_plan(const long long* __restrict__ w, int nb, long long target, long long big, long long cap, int fine_shift,
-       long long* bstart, Chunk* chunks, int* big_list, PlanInfo* info) {
-  const int T = blockDim.x;
-  __shared__ long long tile[1024 * kPlanPer];
-  __shared__ long long sa[1024 / 32];
-  __shared__ long long c_a, c_b, c_c, c_s;  // prefixes before the tile
-  __shared__ long long c_x;                 // the last bucket before the tile (-1: none)
-  __shared__ long long s_end[4];
+k_plan_scan3(long long* part, int g, int nb, long long* bstart, PlanInfo* info) {
+  __shared__ long long tot[3];
+  for (int k = 0; k < 3; ++k) {
+    scan_column(part + k, g, 3, &tot[k]);
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    c_a = c_b = c_c = c_s = 0;
-    c_x = -1;
+    info->total = tot[0];
+    info->n_big = (int)tot[2];
+    info->max_chunk = 0;
+    bstart[nb] = tot[0];
   }
-  long long dummy;
-  for (int base = 0; base < nb; base += T * kPlanPer) {
-    const int nt = min(nb - base, T * kPlanPer);
-    for (int i = threadIdx.x; i < nt; i += T) tile[i] = w[base + i];
-    __syncthreads();
-    const int l0 = min(nt, (int)threadIdx.x * kPlanPer), l1 = min(nt, l0 + kPlanPer);
-    long long ta = 0, tb = 0, tc = 0;
-    for (int l = l0; l < l1; ++l) {
-      const long long x = tile[l];
-      ta += x;
-      if (x > cap) tc += 1;
-      if (x <= big) tb += x;
-    }
-    const long long A0 = c_a + plan_scan(ta, &dummy);
-    const long long B0 = c_b + plan_scan(tb, &dummy);
-    const long long C0 = c_c + plan_scan(tc, &dummy);
-    // state of the bucket before l0 (the previous bucket)
-    bool pb0 = true;
-    long long pq0 = -1;
-    const long long xp = l0 > 0 ? tile[l0 - 1] : c_x;
-    if (l0 < nt && xp >= 0) {
-      pb0 = xp > big;
-      pq0 = pb0 ? -1 : (B0 - xp) / target;
-    }
-    int starts = 0;
-    {
-      bool pbig = pb0;
-      long long pq = pq0, pB = B0;
-      for (int l = l0; l < l1; ++l) {
-        const long long x = tile[l];
-        starts += plan_is_start(x, big, pB, target, &pbig, &pq);
-        if (x <= big) pB += x;
-      }
-    }
-    const long long S0 = c_s + plan_scan(starts, &dummy);
-    {
-      bool pbig = pb0;
-      long long pq = pq0, pB = B0, pA = A0, nbig = C0;
-      long long cidx = S0 - 1;
-      for (int l = l0; l < l1; ++l) {
-        const int d = base + l;
-        const long long x = tile[l];
-        bstart[d] = pA;
-        if (plan_is_start(x, big, pB, target, &pbig, &pq)) {
-          ++cidx;
-          chunks[cidx].f_lo = d;  // bucket index for now
-          chunks[cidx].kind = x > cap ? CH_COPY : CH_NORMAL;
-          if (x > cap) big_list[nbig++] = (int)cidx;
-        }
-        if (x <= big) pB += x;
-        pA += x;
-      }
-    }
-    if (threadIdx.x == T - 1) {  // the last thread's exclusive prefixes + its own part
-      s_end[0] = A0 + ta;
-      s_end[1] = B0 + tb;
-      s_end[2] = C0 + tc;
-      s_end[3] = S0 + starts;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      c_a = s_end[0];
-      c_b = s_end[1];
-      c_c = s_end[2];
-      c_s = s_end[3];
-      c_x = tile[nt - 1];
-    }
-    __syncthreads();
+}
+
+// state of bucket d0 - 1 (the one before a thread's range) from the small-row
+// prefix B0 at d0, as k_plan computes it
+__device__ __forceinline__ void plan_prev(const long long* w, int d0, long long B0, long long big, long long target,
+                                          bool* pb, long long* pq) {
+  *pb = true;
+  *pq = -1;
+  if (d0 > 0) {
+    const long long x = w[d0 - 1];
+    *pb = x > big;
+    *pq = *pb ? -1 : (B0 - x) / target;
   }
-  const int nc = (int)c_s;
-  if (threadIdx.x == 0) {
-    info->total = c_a;
-    info->n_big = (int)c_c;
-    info->n_chunks = nc;
-    bstart[nb] = c_a;
+}
+
+__global__ void __launch_bounds__(kPlanThreads)
+k_plan_starts(const long long* __restrict__ w, int nb, int per, int sub, long long target, long long big,
+              const long long* part, long long* starts) {
+  __shared__ long long red[32];
+  const int d0 = min(nb, blockIdx.x * per + (int)threadIdx.x * sub), d1 = min(min(nb, (blockIdx.x + 1) * per), d0 + sub);
+  long long tb = 0;
+  for (int d = d0; d < d1; ++d) {
+    const long long x = w[d];
+    if (x <= big) tb += x;
   }
+  const long long B0 = part[3 * blockIdx.x + 1] + block_excl_ll(tb, red);
+  bool pbig;
+  long long pq, pB = B0;
+  plan_prev(w, d0, B0, big, target, &pbig, &pq);
+  long long st = 0;
+  for (int d = d0; d < d1; ++d) {
+    const long long x = w[d];
+    st += plan_is_start(x, big, pB, target, &pbig, &pq);
+    if (x <= big) pB += x;
+  }
+  st = block_sum_ll(st, red);
+  if (threadIdx.x == 0) starts[blockIdx.x] = st;
+}
+
+__global__ void __launch_bounds__(1024) k_plan_scan1(long long* starts, int g, PlanInfo* info) {
+  __shared__ long long tot;
+  scan_column(starts, g, 1, &tot);
   __syncthreads();
+  if (threadIdx.x == 0) info->n_chunks = (int)tot;
+}
+
+__global__ void __launch_bounds__(kPlanThreads)
+k_plan_apply(const long long* __restrict__ w, int nb, int per, int sub, long long target, long long big,
+             long long cap, const long long* part, const long long* starts, long long* bstart, Chunk* chunks,
+             int* big_list) {
+  __shared__ long long red[32];
+  const int d0 = min(nb, blockIdx.x * per + (int)threadIdx.x * sub), d1 = min(min(nb, (blockIdx.x + 1) * per), d0 + sub);
+  long long ta = 0, tb = 0, tc = 0;
+  for (int d = d0; d < d1; ++d) {
+    const long long x = w[d];
+    ta += x;
+    if (x > cap) tc += 1;
+    if (x <= big) tb += x;
+  }
+  const long long A0 = part[3 * blockIdx.x] + block_excl_ll(ta, red);
+  const long long B0 = part[3 * blockIdx.x + 1] + block_excl_ll(tb, red);
+  long long nbig = part[3 * blockIdx.x + 2] + block_excl_ll(tc, red);
+  bool pbig;
+  long long pq, pB = B0;
+  plan_prev(w, d0, B0, big, target, &pbig, &pq);
+  long long st = 0;
+  {
+    bool pb2 = pbig;
+    long long pq2 = pq, pB2 = B0;
+    for (int d = d0; d < d1; ++d) {
+      const long long x = w[d];
+      st += plan_is_start(x, big, pB2, target, &pb2, &pq2);
+      if (x <= big) pB2 += x;
+    }
+  }
+  long long cidx = starts[blockIdx.x] + block_excl_ll(st, red) - 1;
+  long long pA = A0;
+  for (int d = d0; d < d1; ++d) {
+    const long long x = w[d];
+    bstart[d] = pA;
+    if (plan_is_start(x, big, pB, target, &pbig, &pq)) {
+      ++cidx;
+      chunks[cidx].pad = d;  // first bucket (its fine range is set by k_plan_finish)
+      chunks[cidx].kind = x > cap ? CH_COPY : CH_NORMAL;
+      if (x > cap) big_list[nbig++] = (int)cidx;
+    }
+    if (x <= big) pB += x;
+    pA += x;
+  }
+}
+
+__global__ void k_plan_finish(int nb, int fine_shift, const long long* bstart, Chunk* chunks, PlanInfo* info) {
+  const int nc = info->n_chunks;
   long long mx = 0;
-  // chunk c ends where chunk c + 1 starts: stash the end bucket in pad
-  for (int c = threadIdx.x; c < nc; c += T) {
-    int dhi = (c + 1 < nc) ? chunks[c + 1].f_lo : nb;
-    chunks[c].pad = dhi;
-    chunks[c].lo = bstart[chunks[c].f_lo];
-    chunks[c].hi = bstart[dhi];
-    if (chunks[c].kind == CH_NORMAL) mx = max(mx, chunks[c].hi - chunks[c].lo);
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < nc; c += T) {
-    chunks[c].f_lo = chunks[c].f_lo << fine_shift;
-    chunks[c].f_hi = chunks[c].pad << fine_shift;
-    chunks[c].pad = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    const int dlo = chunks[c].pad;
+    const int dhi = (c + 1 < nc) ? chunks[c + 1].pad : nb;
+    Chunk& ch = chunks[c];
+    ch.lo = bstart[dlo];
+    ch.hi = bstart[dhi];
+    ch.f_lo = dlo << fine_shift;
+    ch.f_hi = dhi << fine_shift;
+    if (ch.kind == CH_NORMAL) mx = max(mx, ch.hi - ch.lo);
   }
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) sa[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    long long m = sa[threadIdx.x];
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) info->max_chunk = m;
-  }
+  if ((threadIdx.x & 31) == 0 && mx > 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(&info->max_chunk), (unsigned long long)mx);
 }
 
 // Scatter rows [0, n) of src into buckets: row i goes to

@@ -145,6 +145,7 @@ struct sgagg_ctx {
   std::vector<DevBuf> bcols, bout_cols;
   DevBuf ab_keys[3], ab_offs[3], ab_tmp;   // absorbing policy: index, batch, merged index
   DevBuf dk_keys, rg_heads;                // count(distinct): (g, u) rows, regroup block heads
+  DevBuf plan_tmp;                         // chunk planner: per-block sums and starts
   std::vector<DevBuf> dk_cols;
   std::vector<DevBuf> ab_cols[3];
   DevBuf marena_keys;            // runs written by preliminary merges
@@ -550,6 +551,31 @@ struct Solver {
   int n_state;
 };
 
+// The chunk planner over nb bucket counts w: six small launches over up to
+// 1024 blocks (k_plan_*), one bucket per thread up to 2^18 buckets.
+sgagg_status run_plan(sgagg_t h, const long long* w, int nb, int fine_shift, long long* bstart, Chunk* chunks,
+                      int* biglist, PlanInfo* info) {
+  cudaStream_t st = h->stream;
+  const int sub = std::max(1, (nb + kPlanThreads * 1024 - 1) / (kPlanThreads * 1024));
+  const int per = sub * kPlanThreads;
+  const int g = (nb + per - 1) / per;
+  TRY(grow(h, h->plan_tmp, (size_t)(4 * g + 4) * 8));
+  long long* part = P<long long>(h->plan_tmp);
+  long long* starts = part + 3 * g;
+  k_plan_sums<<<g, kPlanThreads, 0, st>>>(w, nb, per, sub, kBigBucket, kTileCap, part);
+  k_plan_scan3<<<1, 1024, 0, st>>>(part, g, nb, bstart, info);
+  k_plan_starts<<<g, kPlanThreads, 0, st>>>(w, nb, per, sub, kChunkTarget, kBigBucket, part, starts);
+  k_plan_scan1<<<1, 1024, 0, st>>>(starts, g, info);
+  k_plan_apply<<<g, kPlanThreads, 0, st>>>(w, nb, per, sub, kChunkTarget, kBigBucket, kTileCap, part, starts,
+                                           bstart, chunks, biglist);
+  k_plan_finish<<<std::max(1, std::min(4 * h->num_sms, (nb + 255) / 256)), 256, 0, st>>>(nb, fine_shift, bstart,
+                                                                                        chunks, info);
+  CU(cudaGetLastError());
+  h->st.class_launches[SGAGG_K_PLAN] += 5;  // kbegin counted one
+  h->st.kernel_launches += 5;
+  return SGAGG_OK;
+}
+
 sgagg_status ensure_depth(sgagg_t h, int depth) {
   if (depth >= kMaxDepth) return fail(h, SGAGG_ECUDA, "recursion too deep");
   return SGAGG_OK;
@@ -754,9 +780,8 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     kend(h);
     kbytes(h, SGAGG_K_SCATTER, n * 16ll * W);
     kbegin(h, SGAGG_K_PLAN);
-    k_plan<<<1, 1024, 0, h->stream>>>(P<long long>(h->btot[depth]), nb, kChunkTarget, kBigBucket, kTileCap, dig.ebits,
-                                      P<long long>(h->bstart[depth]), P<Chunk>(h->chunks[depth]),
-                                      P<int>(h->biglist[depth]), &ds->info);
+    TRY(run_plan(h, P<long long>(h->btot[depth]), nb, dig.ebits, P<long long>(h->bstart[depth]),
+                 P<Chunk>(h->chunks[depth]), P<int>(h->biglist[depth]), &ds->info));
     kend(h);
     CU(cudaGetLastError());
   } else {
@@ -771,9 +796,8 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
                                                            P<long long>(h->btot[depth]));
     kend(h);
     kbegin(h, SGAGG_K_PLAN);
-    k_plan<<<1, 1024, 0, h->stream>>>(P<long long>(h->btot[depth]), nb, kChunkTarget, kBigBucket, kTileCap, dig.ebits,
-                                      P<long long>(h->bstart[depth]), P<Chunk>(h->chunks[depth]),
-                                      P<int>(h->biglist[depth]), &ds->info);
+    TRY(run_plan(h, P<long long>(h->btot[depth]), nb, dig.ebits, P<long long>(h->bstart[depth]),
+                 P<Chunk>(h->chunks[depth]), P<int>(h->biglist[depth]), &ds->info));
     kend(h);
     kbytes(h, SGAGG_K_PLAN, (long long)nb * ntiles * 8 + (long long)nb * (8 + 8 + sizeof(Chunk)));
     kbegin(h, SGAGG_K_SCATTER);
@@ -992,9 +1016,8 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
   TRY(grow(h, h->chunks[0], (size_t)nf * sizeof(Chunk)));
   TRY(grow(h, h->biglist[0], (size_t)nf * 4));
   kbegin(h, SGAGG_K_PLAN);
-  k_plan<<<1, 1024, 0, stream>>>(P<long long>(h->fsizes), nf, kChunkTarget, kBigBucket, kTileCap, 0,
-                                 P<long long>(h->bstart[0]), P<Chunk>(h->chunks[0]), P<int>(h->biglist[0]),
-                                 &ds->info);
+  TRY(run_plan(h, P<long long>(h->fsizes), nf, 0, P<long long>(h->bstart[0]), P<Chunk>(h->chunks[0]),
+               P<int>(h->biglist[0]), &ds->info));
   kend(h);
   CU(cudaGetLastError());
   TRY(sync_read(h, &hs->info, &ds->info, sizeof(PlanInfo)));
@@ -2389,7 +2412,7 @@ void sgagg_destroy(sgagg_t h) {
     free_buf(h->ab_keys[i]); free_buf(h->ab_offs[i]); fv(h->ab_cols[i]);
   }
   free_buf(h->ab_tmp);
-  free_buf(h->dk_keys); free_buf(h->rg_heads); fv(h->dk_cols);
+  free_buf(h->dk_keys); free_buf(h->rg_heads); fv(h->dk_cols); free_buf(h->plan_tmp);
   free_buf(h->binst); free_buf(h->bchunks); free_buf(h->bkeys); free_buf(h->bout_keys);
   free_buf(h->bseg); free_buf(h->brange); free_buf(h->bstartb); free_buf(h->bdirect);
   fv(h->bcols); fv(h->bout_cols);
