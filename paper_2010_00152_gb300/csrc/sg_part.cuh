@@ -63,7 +63,7 @@ __device__ __forceinline__ unsigned level_digit(const Digit& dig, unsigned long 
 }
 
 // thist[d * ntiles + t] = rows of tile t with level digit d.
-template <bool SEG>
+template <bool SEG, bool DIRECT>
 __global__ void __launch_bounds__(kPartThreads)
 k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsigned int* thist) {
   extern __shared__ unsigned int sh_hist[];
@@ -82,7 +82,7 @@ k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsig
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       long long i = i0 + (long long)u * blockDim.x;
-      if (i < hi) k[u] = src_key(src, i);
+      if (i < hi) k[u] = DIRECT ? __ldg(src_key_ptr(src, i)) : src_key(src, i);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -531,7 +531,7 @@ k_tiles2(const long long* bstart1, int nb1, Tile2* tiles, int* tfirst) {
 }
 
 // Level-2 histograms: thist2[t * nb2 + d] = rows of tile t with digit d.
-template <bool SEG>
+template <bool SEG, bool DIRECT>
 __global__ void __launch_bounds__(kPartThreads)
 k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, unsigned* thist2) {
   extern __shared__ unsigned sh2[];
@@ -549,7 +549,7 @@ k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, u
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       long long i = i0 + (long long)u * blockDim.x;
-      if (i < tl.hi) k[u] = src_key(src, i);
+      if (i < tl.hi) k[u] = DIRECT ? __ldg(src_key_ptr(src, i)) : src_key(src, i);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {

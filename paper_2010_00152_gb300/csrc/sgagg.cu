@@ -240,6 +240,17 @@ sgagg_status fail(sgagg_t h, sgagg_status s, const char* fmt, const char* a = ""
     if (dig.seg) kern<true><<<PART_CFG cfg>>>(PART_CFG args);    \
     else kern<false><<<PART_CFG cfg>>>(PART_CFG args);           \
   } while (0)
+#define HIST_LAUNCH(kern, srcv, cfg, args)                                                        \
+  do {                                                                                            \
+    const bool dir_ = staged_direct(srcv);                                                        \
+    if (dig.seg) {                                                                                \
+      if (dir_) kern<true, true><<<PART_CFG cfg>>>(PART_CFG args);                                 \
+      else kern<true, false><<<PART_CFG cfg>>>(PART_CFG args);                                     \
+    } else {                                                                                      \
+      if (dir_) kern<false, true><<<PART_CFG cfg>>>(PART_CFG args);                                \
+      else kern<false, false><<<PART_CFG cfg>>>(PART_CFG args);                                    \
+    }                                                                                             \
+  } while (0)
 #define STAGED_LAUNCH(srcv, cfg, args)                                                            \
   do {                                                                                            \
     const bool dir_ = staged_direct(srcv);                                                        \
@@ -453,8 +464,10 @@ constexpr int kMaxCoarseBits = 15;  // per-tile histogram / cursors: 2^15 x 4 B 
 void set_part_attrs() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_hist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
-    cudaFuncSetAttribute(k_hist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
+    cudaFuncSetAttribute(k_hist<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
+    cudaFuncSetAttribute(k_hist<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
+    cudaFuncSetAttribute(k_hist<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
+    cudaFuncSetAttribute(k_hist<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
     cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
     cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
     cudaFuncSetAttribute(k_scatter_staged<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -463,10 +476,12 @@ void set_part_attrs() {
                          (int)staged_smem_bytes(1 << kMaxCoarseBits > 1024 ? 1024 : 1 << kMaxCoarseBits, kStageCols));
     cudaFuncSetAttribute(k_scatter_staged<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)staged_smem_bytes(1 << kMaxCoarseBits > 1024 ? 1024 : 1 << kMaxCoarseBits, kStageCols));
-    cudaFuncSetAttribute(k_hist2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_hist2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_hist2<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_scatter_staged<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)staged_smem_bytes(1 << kMaxCoarseBits > 1024 ? 1024 : 1 << kMaxCoarseBits, kStageCols));
-    cudaFuncSetAttribute(k_hist2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_hist2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_hist2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     done = true;
   }
 }
@@ -736,7 +751,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     StageCols acs{};
     for (int c = 0; c < C; ++c) acp[c] = acs.c[c] = P<long long>(h->acols[depth][c]);
     kbegin(h, SGAGG_K_HIST);
-    PART_LAUNCH(k_hist, (ntiles, kPartThreads, hist_smem_bytes(nb1, kPartThreads), h->stream),
+    HIST_LAUNCH(k_hist, src, (ntiles, kPartThreads, hist_smem_bytes(nb1, kPartThreads), h->stream),
                 (src, n, dig, D2, nb1, ntiles, P<unsigned>(h->thist1[depth])));
     kend(h);
     kbytes(h, SGAGG_K_HIST, n * (srb - 8ll * C) + (long long)nb1 * ntiles * 4);
@@ -765,7 +780,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
                                                P<int>(h->tfirst[depth]));
     kend(h);
     kbegin(h, SGAGG_K_HIST);
-    PART_LAUNCH(k_hist2, ((int)nt2max, kPartThreads, hist_smem_bytes(nb2, kPartThreads), h->stream),
+    HIST_LAUNCH(k_hist2, a, ((int)nt2max, kPartThreads, hist_smem_bytes(nb2, kPartThreads), h->stream),
                 (a, dig, nb2, P<Tile2>(h->tiles2[depth]), ntd, P<unsigned>(h->thist2[depth])));
     kend(h);
     kbytes(h, SGAGG_K_HIST, n * 8ll + nt2max * nb2 * 4);
@@ -787,7 +802,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
   } else {
     TRY(grow(h, h->thist[depth], (size_t)nb * ntiles * 4));
     kbegin(h, SGAGG_K_HIST);
-    PART_LAUNCH(k_hist, (ntiles, kPartThreads, hist_smem_bytes(nb, kPartThreads), h->stream),
+    HIST_LAUNCH(k_hist, src, (ntiles, kPartThreads, hist_smem_bytes(nb, kPartThreads), h->stream),
                 (src, n, dig, 0, nb, ntiles, P<unsigned int>(h->thist[depth])));
     kend(h);
     kbytes(h, SGAGG_K_HIST, n * (srb - 8ll * C) + (long long)nb * ntiles * 4);
