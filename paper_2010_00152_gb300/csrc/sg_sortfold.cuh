@@ -599,8 +599,10 @@ __device__ __forceinline__ void write_fine_offsets(const OutSink& out, const Chu
 
 __device__ __forceinline__ void sink_key(const OutSink& out, long long pos, unsigned long long key) {
   if (pos >= out.capacity) return;
-  if (out.user) store_key(out.kout, pos, key);
-  else out.keys[pos] = key;
+  if (!out.user) out.keys[pos] = key;
+  else if (out.kout.n_cols == 1 && out.kout.bytes[0] == 8)  // one 8-byte column: the key as is
+    reinterpret_cast<unsigned long long*>(out.kout.cols[0])[pos] = key;
+  else store_key(out.kout, pos, key);
 }
 
 __device__ __forceinline__ void sink_val(const OutSink& out, int st, long long pos, long long v) {
