@@ -7,11 +7,13 @@
 //      or one slice from each of k sorted runs, all loads in flight at once;
 //      the runs' aggregate columns are prefetched into L2 meanwhile);
 //   2. sort a permutation of the chunk by key: a counting sort on the top
-//      kBinBits bits of (key - chunk min); bins of up to 32 rows are finished
-//      by insertion sort, a bigger bin (a repeated key, as a rule) by a warp
-//      that ranks the bin's distinct keys; a bin of more than 32 distinct
-//      keys sends the chunk to a stable LSD radix sort (8-bit digits,
-//      warp-ballot ranking) over every bit that varies inside the chunk;
+//      kBinBits bits of (key - chunk min); one pass over adjacent positions
+//      flags the bins still out of key order, and only those are finished:
+//      by insertion sort up to 32 rows, a bigger bin (a repeated key, as a
+//      rule) by a warp that ranks the bin's distinct keys; a bin of more
+//      than 32 distinct keys sends the chunk to a stable LSD radix sort
+//      (8-bit digits, warp-ballot ranking) over every bit that varies inside
+//      the chunk;
 //   3. fold equal keys: a lane per key group of at most 32 rows, a warp per
 //      bigger group, or -- with at most kFewGroups groups -- the whole CTA
 //      per group; the chunk's distinct-key count gives its output offset by
@@ -348,6 +350,22 @@ __device__ void lsd_sort(const SortSmem& s, int n, unsigned long long kmin, int 
   }
 }
 
+// Insertion sort of positions [st, en) of s.idx by key (one thread).
+__device__ __forceinline__ void insertion_sort_bin(const SortSmem& s, int st, int en) {
+  for (int i = st + 1; i < en; ++i) {
+    const uint16_t v = s.idx[i];
+    const unsigned long long kv = s.keys[v];
+    int j = i - 1;
+    while (j >= st) {
+      const uint16_t u = s.idx[j];
+      if (s.keys[u] <= kv) break;
+      s.idx[j + 1] = u;
+      --j;
+    }
+    s.idx[j + 1] = v;
+  }
+}
+
 // Sort s.idx by key; returns whether a key group may hold more than 32 rows.
 // Block key range: each warp's least and greatest loaded key, combined by
 // shared-memory atomics (g_kmin / g_kmax are preset when the CTA starts).
@@ -436,7 +454,18 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
     s.bins[(threadIdx.x * kBinsPerThread + q) >> 1] = lo | (hi << 16);
   }
   __syncthreads();
-  // place
+  // place; the bin flags (below) and the big-bin list live in the LSD
+  // histogram area, which is free until an LSD sort
+  uint32_t* flag = reinterpret_cast<uint32_t*>(s.whist);  // [kBins / 32]: bin holds an inversion
+  uint32_t* blist = flag + kBins / 32;                    // start | end << 16; fewer than n / 32 bins
+  __shared__ int s_nbig, s_over;
+  if (sh != 0) {  // block-uniform
+    for (int i = threadIdx.x; i < kBins / 32; i += kThreads) flag[i] = 0;
+    if (threadIdx.x == 0) {
+      s_nbig = 0;
+      s_over = 0;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < EPT; ++j) {
     const int i = threadIdx.x + j * kThreads;
@@ -444,67 +473,45 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
   }
   __syncthreads();
   if (sh == 0) return maxbin > 32;  // every bin is one key value
+  // Bins are key ranges in key order, so two adjacent positions out of key
+  // order lie in one bin: only the bins holding such an inversion need
+  // sorting.  One pass over adjacent positions flags them.
+  for (int p0 = threadIdx.x - lane; p0 < n; p0 += kThreads) {  // warp-uniform
+    const int p = p0 + lane;
+    const unsigned long long a = p < n ? s.keys[s.idx[p]] : ~0ull;
+    unsigned long long b = __shfl_down_sync(0xffffffffu, a, 1);
+    if (lane == 31 && p + 1 < n) b = s.keys[s.idx[p + 1]];
+    if (p + 1 < n && a > b) {
+      const int bin = (int)((a - kmin) >> sh);
+      atomicOr(&flag[bin >> 5], 1u << (bin & 31));
+    }
+  }
+  __syncthreads();
   if (maxbin <= 32) {
-    // with about one row per bin, only the few bins holding two or more rows
-    // need work: insertion sort in place; a thread takes its 16 consecutive
-    // bins, their starts read as 8 words
+    // a thread takes its kBinsPerThread consecutive bins; flagged ones are
+    // sorted by insertion
     const int b0 = threadIdx.x * kBinsPerThread;
-    uint32_t wd[kBinsPerThread / 2];
-#pragma unroll
-    for (int q = 0; q < kBinsPerThread / 2; ++q) wd[q] = s.bins[(b0 >> 1) + q];
-    const int en_last = (b0 + kBinsPerThread < kBins) ? (int)(s.bins[(b0 + kBinsPerThread) >> 1] & 0xFFFFu) : n;
-#pragma unroll
-    for (int q = 0; q < kBinsPerThread; ++q) {
-      const int st = (int)((wd[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu);
-      const int en = q + 1 < kBinsPerThread ? (int)((wd[(q + 1) >> 1] >> (((q + 1) & 1) * 16)) & 0xFFFFu) : en_last;
-      for (int i = st + 1; i < en; ++i) {
-        const uint16_t v = s.idx[i];
-        const unsigned long long kv = s.keys[v];
-        int j = i - 1;
-        while (j >= st) {
-          const uint16_t u = s.idx[j];
-          if (s.keys[u] <= kv) break;
-          s.idx[j + 1] = u;
-          --j;
-        }
-        s.idx[j + 1] = v;
-      }
+    unsigned m = (flag[b0 >> 5] >> (b0 & 31)) & ((1u << kBinsPerThread) - 1u);
+    while (m) {
+      const int b = b0 + __ffs(m) - 1;
+      m &= m - 1;
+      insertion_sort_bin(s, (int)bin_get(s.bins, b), b + 1 < kBins ? (int)bin_get(s.bins, b + 1) : n);
     }
     __syncthreads();
     return false;
   }
   // Some bin holds more than 32 rows -- usually a key repeated many times.
-  // Bins of up to 32 rows are finished by insertion as above.  A warp takes
-  // each bigger bin: it collects the bin's distinct keys (at most 32, one per
-  // lane, with their row counts), ranks them, and places every row at its
-  // key's position.  A bin with more distinct keys sends the chunk to the
-  // LSD sort.
-  __shared__ int s_nbig, s_over;
-  if (threadIdx.x == 0) {
-    s_nbig = 0;
-    s_over = 0;
-  }
-  __syncthreads();
-  uint32_t* blist = reinterpret_cast<uint32_t*>(s.whist);  // start | end << 16; fewer than n / 32 bins
+  // Flagged bins of up to 32 rows are finished by insertion as above.  A warp
+  // takes each bigger flagged bin: it collects the bin's distinct keys (at
+  // most 32, one per lane, with their row counts), ranks them, and places
+  // every row at its key's position.  A bin with more distinct keys sends the
+  // chunk to the LSD sort.
   for (int b = threadIdx.x; b < kBins; b += kThreads) {
+    if (!((flag[b >> 5] >> (b & 31)) & 1u)) continue;
     const int st = (int)bin_get(s.bins, b);
     const int en = (b + 1 < kBins) ? (int)bin_get(s.bins, b + 1) : n;
-    if (en - st > 32) {
-      blist[atomicAdd(&s_nbig, 1)] = (unsigned)st | ((unsigned)en << 16);
-      continue;
-    }
-    for (int i = st + 1; i < en; ++i) {
-      const uint16_t v = s.idx[i];
-      const unsigned long long kv = s.keys[v];
-      int j = i - 1;
-      while (j >= st) {
-        const uint16_t u = s.idx[j];
-        if (s.keys[u] <= kv) break;
-        s.idx[j + 1] = u;
-        --j;
-      }
-      s.idx[j + 1] = v;
-    }
+    if (en - st > 32) blist[atomicAdd(&s_nbig, 1)] = (unsigned)st | ((unsigned)en << 16);
+    else insertion_sort_bin(s, st, en);
   }
   __syncthreads();
   {
