@@ -99,8 +99,9 @@ struct SortSmem {
   unsigned long long* keys;   // [kTileCap]
   uint16_t* idx;              // [kTileCap] sorted permutation
   uint32_t* bins;             // [kBins / 2] packed 16-bit bin starts; LSD ping-pong buffer;
-                              // then the head bitmask and its word prefix
-  uint16_t* whist;            // [kWarps * 256] LSD per-warp digit counts
+                              // then the inverse permutation (sorted position of each row)
+  uint16_t* whist;            // [kWarps * 256] LSD per-warp digit counts; bin flags; then
+                              // the head bitmask, its word prefix and the big-group list
   long long* slo;             // [kMaxFanIn] merge: slice start per run
   long long* spre;            // [kMaxFanIn + 1] merge: slice prefix
 };
@@ -167,48 +168,6 @@ struct ChunkView {
   int n;
   int k;            // MODE_RUNS: runs
 };
-
-// Run holding chunk position i (MODE_RUNS): largest r with spre[r] <= i.
-__device__ __forceinline__ int run_of(const SortSmem& s, int k, int i) {
-  int lo = 0, hi = k - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (s.spre[mid] <= i) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Where chunk row i's columns live: one address computation per row.
-struct RowAt {
-  const long long* aos;      // MODE_RANGE: the row's first column
-  long long off;             // MODE_RUNS: row inside the run; MODE_TILES: source row
-  int run;                   // MODE_RUNS
-};
-
-template <int MODE>
-__device__ __forceinline__ RowAt row_at(const SortSmem& s, const RowSrc& src, const ChunkView& cv, int i) {
-  RowAt a;
-  a.aos = nullptr;
-  a.run = 0;
-  a.off = 0;
-  if (MODE == MODE_RUNS) {
-    a.run = run_of(s, cv.k, i);
-    a.off = s.slo[a.run] + (i - s.spre[a.run]);
-  } else if (MODE == MODE_RANGE) {
-    a.aos = src.aos + (cv.lo + i) * (1 + src.ncols) + 1;
-  } else {
-    a.off = cv.lo + i;
-  }
-  return a;
-}
-
-template <int MODE>
-__device__ __forceinline__ long long col_at(const RowSrc& src, const RunSet& runs, const RowAt& a, int c) {
-  if (c < 0) return 1;
-  if (MODE == MODE_RUNS) return runs.ptrs[(long long)a.run * (1 + runs.ncols) + 1 + c][a.off];
-  if (MODE == MODE_RANGE) return a.aos[c];
-  return src_col(src, c, a.off);
-}
 
 // Advance a run cursor r (MODE_RUNS) to the run holding position i >= its start.
 __device__ __forceinline__ int run_advance(const SortSmem& s, int k, int r, int i) {
@@ -654,12 +613,13 @@ __device__ __forceinline__ long long chunk_base(const LookBack& lb, const OutSin
 // ---------------------------------------------------------------------------
 __shared__ int g_lcnt[kWarps + 1];
 
-// Stage source column c of every chunk row (chunk order) into dst: 8-byte
-// cp.async copies, global to shared, all in flight at once; complete when
-// it returns (visible to the other threads after a barrier).
+// Stage source column c of every chunk row into dst in sorted order (row i
+// to dst[inv[i]]): 8-byte cp.async copies, global to shared, read in chunk
+// order and all in flight at once; complete when it returns (visible to the
+// other threads after a barrier).
 template <int MODE>
 __device__ __forceinline__ void stage_column(const SortSmem& s, const RowSrc& src, const RunSet& runs,
-                                             const ChunkView& cv, int c, long long* dst) {
+                                             const ChunkView& cv, int c, const uint16_t* inv, long long* dst) {
   int r = 0;
   for (int i = threadIdx.x; i < cv.n; i += kThreads) {
     const long long* p;
@@ -672,7 +632,7 @@ __device__ __forceinline__ void stage_column(const SortSmem& s, const RowSrc& sr
       const int64_t row = src.offset + cv.lo + i;
       p = src.kind == SRC_AOS ? src.aos + row * (1 + src.ncols) + 1 + c : src.cols[c] + row;
     }
-    cp_async8(&dst[i], p);
+    cp_async8(&dst[inv[i]], p);
   }
   cp_async_wait();
 }
@@ -713,7 +673,7 @@ __device__ void fold_few(const SortSmem& s, const FoldDesc& fd, const OutSink& o
       for (int a = 0; a < kAccBlock; ++a)
         if (s0 + a < ns) acc[a] = op_identity(fd.op[s0 + a]);
       for (int p = gs + threadIdx.x; p < ge; p += kThreads) {
-        const long long v = col[s.idx[p]];
+        const long long v = col[p];
 #pragma unroll
         for (int a = 0; a < kAccBlock; ++a)
           if (s0 + a < ns && fd.src[s0 + a] == c) acc[a] = op_combine(fd.op[s0 + a], acc[a], v);
@@ -742,7 +702,7 @@ __device__ void fold_big(const SortSmem& s, const FoldDesc& fd, const OutSink& o
                                       const long long* col, int c, long long base) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int ns = fd.n_state;
-  const uint32_t* big = reinterpret_cast<const uint32_t*>(s.whist);
+  const uint32_t* big = reinterpret_cast<const uint32_t*>(s.whist + kTileCap / 32 * 3);
   const int nbig = g_nbig;
   for (int q = w; q < nbig; q += kWarps) {
     const int p = (int)(big[2 * q] & 0xFFFFu), e = (int)(big[2 * q] >> 16);
@@ -752,7 +712,7 @@ __device__ void fold_big(const SortSmem& s, const FoldDesc& fd, const OutSink& o
       if (a < ns && fd.src[a] == c) {
         const int op = fd.op[a];
         long long acc = op_identity(op);
-        for (int i = p + lane; i < e; i += 32) acc = op_combine(op, acc, col[s.idx[i]]);
+        for (int i = p + lane; i < e; i += 32) acc = op_combine(op, acc, col[i]);
         acc = warp_reduce(op, acc);
         if (lane == 0) sink_val(out, a, pos, acc);
       }
@@ -776,16 +736,26 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
   const unsigned lt = (1u << lane) - 1;
   const int Q = ((n + kWarps - 1) / kWarps + 31) & ~31;
   const int wb = min(n, w * Q), we = min(n, wb + Q);
-  uint32_t* hm = s.bins;  // head bitmask (the sort is done with the bins)
-  uint16_t* hpre = reinterpret_cast<uint16_t*>(s.bins + kTileCap / 32);  // heads before each word
-  uint32_t* big = reinterpret_cast<uint32_t*>(s.whist);  // big groups: (p | e << 16, group ordinal)
+  // the sort is done with the bins and the histogram area
+  uint32_t* hm = reinterpret_cast<uint32_t*>(s.whist);                   // head bitmask
+  uint16_t* hpre = s.whist + kTileCap / 32 * 2;                           // heads before each word
+  uint32_t* big = reinterpret_cast<uint32_t*>(s.whist + kTileCap / 32 * 3);  // (p | e << 16, group ordinal)
+  uint16_t* inv = reinterpret_cast<uint16_t*>(s.bins);                    // sorted position of row i
   if (BIGS && threadIdx.x == 0) g_nbig = 0;
-  // pass 1: heads -> bitmask, per-warp counts (warp ranges are 32-aligned)
+  // pass 1: heads -> bitmask, per-warp counts (warp ranges are 32-aligned);
+  // the inverse permutation
   int hc = 0;
   for (int b = wb; b < we; b += 32) {
     const int p = b + lane;
+    const int ip = p < we ? s.idx[p] : 0;
+    const unsigned long long kp = s.keys[ip];
+    unsigned long long kq = __shfl_up_sync(0xffffffffu, kp, 1);
+    if (lane == 0 && p > 0) kq = s.keys[s.idx[p - 1]];
     bool h = false;
-    if (p < we) h = (p == 0) || s.keys[s.idx[p]] != s.keys[s.idx[p - 1]];
+    if (p < we) {
+      h = (p == 0) || kp != kq;
+      inv[ip] = (uint16_t)p;
+    }
     const unsigned hb = __ballot_sync(0xffffffffu, h);
     if (lane == 0) {
       hm[b >> 5] = hb;
@@ -865,7 +835,7 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
     for (int a = 0; a < ns; ++a) used |= (fd.src[a] == c);
     if (!used) continue;  // block-uniform
     __syncthreads();      // everyone is done with the previous contents (keys, offsets, column)
-    stage_column<MODE>(s, src, runs, cv, c, col);
+    stage_column<MODE>(s, src, runs, cv, c, inv, col);
     __syncthreads();
     if (few) {
       fold_few(s, fd, out, col, c, count, base);
@@ -884,8 +854,8 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
           for (int a = 0; a < KS; ++a) {
             if (a < ns && fd.src[a] == c) {
               const int op = fd.op[a];
-              long long acc = col[s.idx[p]];
-              for (int q = p + 1; q < e; ++q) acc = op_combine(op, acc, col[s.idx[q]]);
+              long long acc = col[p];
+              for (int q = p + 1; q < e; ++q) acc = op_combine(op, acc, col[q]);
               sink_val(out, a, pos, acc);
             }
           }
