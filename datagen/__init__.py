@@ -256,4 +256,11 @@ def edge_keys(kind, n, seed=7, device="cpu"):
         c = uniform_int(seed, 9, n, 0, 3, device)
         off = uniform_int(seed, 10, n, 0, max(1, n // 2), device)
         return (mix64(c) + off).view(torch.uint64)
+    if kind == "heavy_light":
+        # 40 heavy keys (30 % of the rows: hundreds of rows each) among light
+        # keys of about one row each, interleaved in key order
+        u = uniform_int(seed, 9, n, 0, 99, device)
+        heavy = uniform_int(seed, 10, n, 0, 39, device)
+        light = uniform_int(seed, 11, n, 40, 40 + n, device)
+        return as_u64(mix64(torch.where(u < 30, heavy, light)))
     raise ValueError(kind)

@@ -14,11 +14,11 @@
 //      than 32 distinct keys sends the chunk to a stable LSD radix sort
 //      (8-bit digits, warp-ballot ranking) over every bit that varies inside
 //      the chunk;
-//   3. fold equal keys: a lane per key group of at most 32 rows, a warp per
-//      bigger group, or -- with at most kFewGroups groups -- the whole CTA
-//      per group; the chunk's distinct-key count gives its output offset by
-//      decoupled look-back, and each aggregate source column is staged once
-//      into shared memory (where the sorted keys were) and folded from there.
+//   3. fold equal keys: the chunk's distinct-key count gives its output
+//      offset by decoupled look-back; each aggregate source column is staged
+//      once into shared memory in sorted order (where the keys were) and
+//      folded from there by segmented warp scans over head bits, or -- with
+//      at most kFewGroups groups -- by the whole CTA one group at a time.
 #pragma once
 #include "sg_common.cuh"
 
@@ -101,14 +101,20 @@ struct SortSmem {
   uint32_t* bins;             // [kBins / 2] packed 16-bit bin starts; LSD ping-pong buffer;
                               // then the inverse permutation (sorted position of each row)
   uint16_t* whist;            // [kWarps * 256] LSD per-warp digit counts; bin flags; then
-                              // the head bitmask, its word prefix and the big-group list
-  long long* slo;             // [kMaxFanIn] merge: slice start per run
+                              // the head bitmask and its word prefix
+  long long* slo;             // [kMaxFanIn] merge: slice start per run, less the chunk
+                              // position of the slice's first row
   long long* spre;            // [kMaxFanIn + 1] merge: slice prefix
+  unsigned long long* sadr;   // [kMaxFanIn] merge: address of chunk row 0 in each run's
+                              // current column (keys, then each staged column)
 };
 
 constexpr size_t kSortSmemBytes =
-    kTileCap * 8 + kTileCap * 2 + (kBins / 2) * 4 + kWarps * 256 * 2 + kMaxFanIn * 8 + (kMaxFanIn + 1) * 8 + 64;
+    kTileCap * 8 + kTileCap * 2 + (kBins / 2) * 4 + kWarps * 256 * 2 + kMaxFanIn * 8 + (kMaxFanIn + 1) * 8 +
+    kMaxFanIn * 8 + 64;
 static_assert(kBins >= kTileCap, "the LSD ping-pong buffer lives in the bins area");
+// two CTAs per SM: 2 x (dynamic + static (< 2.5 KB) + 1 KB reserved) within 228 KB
+static_assert(kSortSmemBytes <= 113000, "k_sortfold must keep two CTAs per SM");
 
 __device__ __forceinline__ SortSmem carve(unsigned char* base) {
   SortSmem s;
@@ -118,6 +124,7 @@ __device__ __forceinline__ SortSmem carve(unsigned char* base) {
   s.whist = reinterpret_cast<uint16_t*>(base + kTileCap * 10 + (kBins / 2) * 4);
   s.slo = reinterpret_cast<long long*>(base + kTileCap * 10 + (kBins / 2) * 4 + kWarps * 256 * 2);
   s.spre = s.slo + kMaxFanIn;
+  s.sadr = reinterpret_cast<unsigned long long*>(s.spre + kMaxFanIn + 1);
   return s;
 }
 
@@ -185,8 +192,7 @@ __device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, 
       const unsigned long long* p;
       if (MODE == MODE_RUNS) {
         r = run_advance(s, cv.k, r, i);
-        p = reinterpret_cast<const unsigned long long*>(runs.ptrs[(long long)r * (1 + runs.ncols)]) + s.slo[r] +
-            (i - s.spre[r]);
+        p = reinterpret_cast<const unsigned long long*>(s.sadr[r]) + i;
       } else if (MODE == MODE_RANGE) {
         p = reinterpret_cast<const unsigned long long*>(src.aos + (cv.lo + i) * (1 + src.ncols));
       } else {
@@ -203,20 +209,13 @@ __device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, 
     return;
   }
   constexpr int U = 8;  // loads in flight per thread
-  int r = 0;            // a thread's positions only grow: the run cursor only advances
   for (int base = threadIdx.x; base < cv.n; base += U * kThreads) {
     unsigned long long v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       int i = base + u * kThreads;
       if (i < cv.n) {
-        if (MODE == MODE_RUNS) {
-          r = run_advance(s, cv.k, r, i);
-          const long long* p = runs.ptrs[(long long)r * (1 + runs.ncols)];
-          v[u] = (unsigned long long)__ldg(p + s.slo[r] + (i - s.spre[r]));
-        } else {
-          v[u] = src_key(src, cv.lo + i);
-        }
+        v[u] = src_key(src, cv.lo + i);  // (MODE_RUNS always takes the path above)
       }
     }
 #pragma unroll
@@ -620,12 +619,18 @@ __shared__ int g_lcnt[kWarps + 1];
 template <int MODE>
 __device__ __forceinline__ void stage_column(const SortSmem& s, const RowSrc& src, const RunSet& runs,
                                              const ChunkView& cv, int c, const uint16_t* inv, long long* dst) {
+  if (MODE == MODE_RUNS) {  // each run's base address for column c
+    for (int r = threadIdx.x; r < cv.k; r += kThreads)
+      s.sadr[r] = reinterpret_cast<unsigned long long>(runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c]) +
+                  8ull * (unsigned long long)s.slo[r];
+    __syncthreads();
+  }
   int r = 0;
   for (int i = threadIdx.x; i < cv.n; i += kThreads) {
     const long long* p;
     if (MODE == MODE_RUNS) {
       r = run_advance(s, cv.k, r, i);
-      p = runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c] + s.slo[r] + (i - s.spre[r]);
+      p = reinterpret_cast<const long long*>(s.sadr[r]) + i;
     } else if (MODE == MODE_RANGE) {
       p = src.aos + (cv.lo + i) * (1 + src.ncols) + 1 + c;
     } else {
@@ -650,11 +655,8 @@ __device__ __forceinline__ int group_end(const uint32_t* hm, int p, int n) {
   return n;
 }
 
-constexpr int kLaneGroup = 32;  // key groups up to this many rows are folded by one lane
-
 __shared__ int g_gstart[kFewGroups + 1];
 __shared__ long long g_gacc[kWarps * kAccBlock];
-__shared__ int g_nbig;
 
 // Few key groups: the CTA reduces one group at a time (positions in
 // g_gstart), kAccBlock aggregates of source column c per sweep.
@@ -696,26 +698,62 @@ __device__ void fold_few(const SortSmem& s, const FoldDesc& fd, const OutSink& o
   }
 }
 
-// Key groups of more than kLaneGroup rows (listed in s.whist): a warp each.
-template <int KS>
-__device__ void fold_big(const SortSmem& s, const FoldDesc& fd, const OutSink& out,
-                                      const long long* col, int c, long long base) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int ns = fd.n_state;
-  const uint32_t* big = reinterpret_cast<const uint32_t*>(s.whist + kTileCap / 32 * 3);
-  const int nbig = g_nbig;
-  for (int q = w; q < nbig; q += kWarps) {
-    const int p = (int)(big[2 * q] & 0xFFFFu), e = (int)(big[2 * q] >> 16);
-    const long long pos = base + (int)big[2 * q + 1];
-#pragma unroll(KS <= 8 ? KS : 1)
-    for (int a = 0; a < KS; ++a) {
-      if (a < ns && fd.src[a] == c) {
-        const int op = fd.op[a];
-        long long acc = op_identity(op);
-        for (int i = p + lane; i < e; i += 32) acc = op_combine(op, acc, col[i]);
-        acc = warp_reduce(op, acc);
-        if (lane == 0) sink_val(out, a, pos, acc);
-      }
+template <int OP>
+__device__ __forceinline__ long long op_id() {
+  return OP == OP_SUM ? 0 : (OP == OP_MIN ? INT64_MAX : INT64_MIN);
+}
+
+template <int OP>
+__device__ __forceinline__ long long op_do(long long a, long long b) {
+  if (OP == OP_SUM) return (long long)((unsigned long long)a + (unsigned long long)b);
+  if (OP == OP_MIN) return b < a ? b : a;
+  return b > a ? b : a;
+}
+
+// A warp's key groups (those whose heads lie in its position range), folded
+// over their sorted positions [fh, xe) of col: per 32-position window a
+// segmented inclusive scan (a segment starts at a head bit), the open
+// group's value carried from window to window (a window inside one group
+// only adds lane partials); the lane at a group's last position writes the
+// group's value to dst[base + group ordinal].
+template <int OP>
+__device__ void fold_scan(const uint32_t* hm, const uint16_t* hpre, const long long* col, int n, int fh, int xe,
+                          long long* dst, long long cap, long long base) {
+  const int lane = threadIdx.x & 31;
+  long long carry = op_id<OP>(), lacc = op_id<OP>();
+  bool pend = false;  // warp-uniform: lane partials not yet in carry
+  for (int b = fh & ~31; b < xe; b += 32) {
+    const unsigned hb = hm[b >> 5];
+    const int p = b + lane;
+    const bool own = p >= fh && p < xe;
+    const long long v0 = own ? col[p] : op_id<OP>();
+    if (hb == 0 && b >= fh && b + 32 < xe && !(hm[(b >> 5) + 1] & 1u)) {
+      // warp-uniform: the window lies inside one group, which goes on after it
+      lacc = op_do<OP>(lacc, v0);
+      pend = true;
+      continue;
+    }
+    if (pend) {
+      for (int o = 16; o > 0; o >>= 1) lacc = op_do<OP>(lacc, __shfl_xor_sync(0xffffffffu, lacc, o));
+      carry = op_do<OP>(carry, lacc);
+      lacc = op_id<OP>();
+      pend = false;
+    }
+    const unsigned le = hb & (0xffffffffu >> (31 - lane));  // heads at or below the lane
+    const int ss = 31 - __clz(le);                          // its group's head lane; -1: an earlier window
+    const int d = ss >= 0 ? lane - ss : lane;               // earlier lanes of its group in this window
+    const int dmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)d);
+    long long v = v0;
+    for (int o = 1; o <= dmax; o <<= 1) {
+      const long long u = __shfl_up_sync(0xffffffffu, v, o);
+      if (o <= d) v = op_do<OP>(v, u);
+    }
+    if (ss < 0) v = op_do<OP>(v, carry);
+    carry = __shfl_sync(0xffffffffu, v, 31);
+    const bool nh = lane < 31 ? ((hb >> (lane + 1)) & 1u) != 0 : (b + 32 >= n || (hm[(b >> 5) + 1] & 1u));
+    if (own && (nh || p + 1 == xe)) {
+      const long long pos = base + (long long)hpre[b >> 5] + __popc(le) - 1;
+      if (pos < cap) dst[pos] = v;
     }
   }
 }
@@ -723,10 +761,12 @@ __device__ void fold_big(const SortSmem& s, const FoldDesc& fd, const OutSink& o
 // Fold the sorted chunk: heads (first rows of key groups) into a bitmask and
 // the chunk's distinct-key count -> its output offset by look-back; keys and
 // count(*) per head; then the aggregates one source column at a time, the
-// column staged in shared memory where the keys were.  A lane folds a key
-// group of at most kLaneGroup rows; a warp folds a bigger one (listed while
-// the keys are written, when the sort says that groups may be that big);
-// with at most kFewGroups groups the whole CTA folds one group at a time.
+// column staged in sorted order in shared memory where the keys were.  Each
+// warp folds the groups whose heads lie in its position range: a lane per
+// group where nearly every row is a group of its own, else by segmented
+// scans (fold_scan); with at most kFewGroups groups (possible only when the
+// sort says that groups may exceed 32 rows) the whole CTA folds one group at
+// a time.
 template <int MODE, int KS, bool BIGS>
 __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& runs, const ChunkView& cv,
                             const FoldDesc& fd, const OutSink& out, const LookBack& lb, const Chunk& ch,
@@ -739,9 +779,7 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
   // the sort is done with the bins and the histogram area
   uint32_t* hm = reinterpret_cast<uint32_t*>(s.whist);                   // head bitmask
   uint16_t* hpre = s.whist + kTileCap / 32 * 2;                           // heads before each word
-  uint32_t* big = reinterpret_cast<uint32_t*>(s.whist + kTileCap / 32 * 3);  // (p | e << 16, group ordinal)
   uint16_t* inv = reinterpret_cast<uint16_t*>(s.bins);                    // sorted position of row i
-  if (BIGS && threadIdx.x == 0) g_nbig = 0;
   // pass 1: heads -> bitmask, per-warp counts (warp ranges are 32-aligned);
   // the inverse permutation
   int hc = 0;
@@ -776,15 +814,36 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
   }
   __syncthreads();
   const int count = g_lcnt[kWarps];
-  const bool few = BIGS && count <= kFewGroups;  // (without BIGS every group fits a lane)
+  const bool few = BIGS && count <= kFewGroups;
   for (int b = wb + 32 * lane; b < we; b += 32 * 32) hpre[b >> 5] += (uint16_t)g_lcnt[w];
+  // mostly one-row groups (three heads in four positions or more, each group
+  // within 32 rows): a lane folds each group; otherwise segmented scans
+  const bool lanefold = !BIGS && 4 * hc >= 3 * (we - wb);
+  // the warp's groups for the scans: heads in [wb, we), positions [fh, xe)
+  // (a word of hm lies inside one warp's range)
+  int fh = n, xe = 0;
+  if (!few && !lanefold) {
+    int lh = -1;
+    for (int b0 = wb; b0 < we; b0 += 32 * 32) {
+      const int b = b0 + 32 * lane;
+      const unsigned x = b < we ? hm[b >> 5] : 0u;
+      const unsigned nz = __ballot_sync(0xffffffffu, x != 0);
+      if (nz) {  // warp-uniform
+        const int l0 = __ffs(nz) - 1, l1 = 31 - __clz(nz);
+        const unsigned x0 = __shfl_sync(0xffffffffu, x, l0), x1 = __shfl_sync(0xffffffffu, x, l1);
+        fh = min(fh, b0 + 32 * l0 + __ffs(x0) - 1);
+        lh = b0 + 32 * l1 + 31 - __clz(x1);
+      }
+    }
+    if (lh >= 0) xe = group_end(hm, lh, n);
+  }
   const long long base =
       MODE == MODE_DIRECT ? direct_base(out, count, s_base) : chunk_base(lb, out, cid, count, s_base);
   if (base < 0) return;
   if (out.offs && count == 0 && threadIdx.x == 0)
     for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
   const int ns = fd.n_state;
-  // keys, count(*) of raw rows, the big-group list
+  // keys, count(*) of raw rows
   {
     int run = g_lcnt[w];
     for (int b = wb; b < we; b += 32) {
@@ -801,13 +860,7 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
             if (e < 0) e = group_end(hm, p, n);
             sink_val(out, a, pos, fd.op[a] == OP_SUM ? (long long)(e - p) : 1);
           }
-        if (few) {
-          g_gstart[g] = p;
-        } else if (BIGS && (e < 0 ? (e = group_end(hm, p, n)) : e) - p > kLaneGroup) {
-          const int q = atomicAdd(&g_nbig, 1);  // fewer than n / kLaneGroup entries
-          big[2 * q] = (unsigned)p | ((unsigned)e << 16);
-          big[2 * q + 1] = (unsigned)g;
-        }
+        if (few) g_gstart[g] = p;
       }
       run += __popc(hb);
     }
@@ -841,15 +894,15 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
       fold_few(s, fd, out, col, c, count, base);
       continue;
     }
-    // a lane per group of at most kLaneGroup rows
-    int run = g_lcnt[w];
-    for (int b = wb; b < we; b += 32) {
-      const int p = b + lane;
-      const unsigned hb = hm[b >> 5];
-      if ((hb >> lane) & 1u) {
-        const long long pos = base + run + __popc(hb & lt);
-        const int e = group_end(hm, p, n);
-        if (!BIGS || e - p <= kLaneGroup) {
+    if (lanefold) {
+      // a lane per group (every group has at most 32 rows)
+      int run = g_lcnt[w];
+      for (int b = wb; b < we; b += 32) {
+        const int p = b + lane;
+        const unsigned hb = hm[b >> 5];
+        if ((hb >> lane) & 1u) {
+          const long long pos = base + run + __popc(hb & lt);
+          const int e = group_end(hm, p, n);
 #pragma unroll(KS <= 8 ? KS : 1)
           for (int a = 0; a < KS; ++a) {
             if (a < ns && fd.src[a] == c) {
@@ -860,11 +913,20 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
             }
           }
         }
+        run += __popc(hb);
       }
-      run += __popc(hb);
+      continue;
     }
-    // a warp per bigger group
-    if (BIGS) fold_big<KS>(s, fd, out, col, c, base);
+    if (fh >= xe) continue;  // warp-uniform: no group of this warp
+#pragma unroll(KS <= 8 ? KS : 1)
+    for (int a = 0; a < KS; ++a) {
+      if (a < ns && fd.src[a] == c) {
+        const int op = fd.op[a];
+        if (op == OP_SUM) fold_scan<OP_SUM>(hm, hpre, col, n, fh, xe, out.cols[a], out.capacity, base);
+        else if (op == OP_MIN) fold_scan<OP_MIN>(hm, hpre, col, n, fh, xe, out.cols[a], out.capacity, base);
+        else fold_scan<OP_MAX>(hm, hpre, col, n, fh, xe, out.cols[a], out.capacity, base);
+      }
+    }
   }
 }
 
@@ -982,7 +1044,15 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
           long long y = __shfl_up_sync(0xffffffffu, x, o);
           if ((int)threadIdx.x >= o) x += y;
         }
-        if (r < k) s.spre[r + 1] = run + x;
+        if (r < k) {
+          s.spre[r + 1] = run + x;
+          // slice start less the chunk position of its first row: chunk row
+          // i of run r is row slo[r] + i of its arrays
+          const long long off = s.slo[r] - (run + x - v);
+          s.slo[r] = off;
+          s.sadr[r] = reinterpret_cast<unsigned long long>(runs.ptrs[(long long)r * (1 + runs.ncols)]) +
+                      8ull * (unsigned long long)off;
+        }
         run += __shfl_sync(0xffffffffu, x, 31);
       }
       if (threadIdx.x == 0) {

@@ -114,7 +114,7 @@ def numpy_groupby(keys, payload, aggs):
 
 
 @pytest.mark.parametrize("kind", ["c1", "wide", "extremes", "all_equal", "sorted", "reverse",
-                                  "same_digit", "small_int", "clustered"])
+                                  "same_digit", "small_int", "clustered", "heavy_light"])
 def test_oracle_matches_numpy(kind):
     n = 200_003
     if kind == "c1":

@@ -92,7 +92,7 @@ def test_budget_not_dividing_n():
 
 
 @pytest.mark.parametrize("kind", ["all_equal", "distinct", "sorted", "reverse", "small_int",
-                                  "extremes", "same_digit", "clustered"])
+                                  "extremes", "same_digit", "clustered", "heavy_light"])
 @pytest.mark.parametrize("M", [1 << 30, 50_000])
 def test_adversarial_keys(kind, M):
     kc, pay = u64_case(kind, 150_001, npay=2)
