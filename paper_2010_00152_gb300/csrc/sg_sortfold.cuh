@@ -416,12 +416,15 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
   // histogram area, which is free until an LSD sort
   uint32_t* flag = reinterpret_cast<uint32_t*>(s.whist);  // [kBins / 32]: bin holds an inversion
   uint32_t* blist = flag + kBins / 32;                    // start | end << 16; fewer than n / 32 bins
-  __shared__ int s_nbig, s_over;
+  uint16_t* flist = s.whist + kBins / 16 * 2;             // [kFlagList] the flagged bins
+  constexpr int kFlagList = kWarps * 256 - kBins / 16 * 2;
+  __shared__ int s_nbig, s_over, s_nflag;
   if (sh != 0) {  // block-uniform
     for (int i = threadIdx.x; i < kBins / 32; i += kThreads) flag[i] = 0;
     if (threadIdx.x == 0) {
       s_nbig = 0;
       s_over = 0;
+      s_nflag = 0;
     }
   }
 #pragma unroll
@@ -433,7 +436,8 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
   if (sh == 0) return maxbin > 32;  // every bin is one key value
   // Bins are key ranges in key order, so two adjacent positions out of key
   // order lie in one bin: only the bins holding such an inversion need
-  // sorting.  One pass over adjacent positions flags them.
+  // sorting.  One pass over adjacent positions flags them (a bit per bin)
+  // and lists them (first flag of a bin only).
   for (int p0 = threadIdx.x - lane; p0 < n; p0 += kThreads) {  // warp-uniform
     const int p = p0 + lane;
     const unsigned long long a = p < n ? s.keys[s.idx[p]] : ~0ull;
@@ -441,19 +445,31 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
     if (lane == 31 && p + 1 < n) b = s.keys[s.idx[p + 1]];
     if (p + 1 < n && a > b) {
       const int bin = (int)((a - kmin) >> sh);
-      atomicOr(&flag[bin >> 5], 1u << (bin & 31));
+      const unsigned bit = 1u << (bin & 31);
+      if (!(atomicOr(&flag[bin >> 5], bit) & bit)) {
+        const int q = atomicAdd(&s_nflag, 1);
+        if (q < kFlagList) flist[q] = (uint16_t)bin;
+      }
     }
   }
   __syncthreads();
   if (maxbin <= 32) {
-    // a thread takes its kBinsPerThread consecutive bins; flagged ones are
-    // sorted by insertion
-    const int b0 = threadIdx.x * kBinsPerThread;
-    unsigned m = (flag[b0 >> 5] >> (b0 & 31)) & ((1u << kBinsPerThread) - 1u);
-    while (m) {
-      const int b = b0 + __ffs(m) - 1;
-      m &= m - 1;
-      insertion_sort_bin(s, (int)bin_get(s.bins, b), b + 1 < kBins ? (int)bin_get(s.bins, b + 1) : n);
+    // flagged bins are sorted by insertion: a thread per listed bin, or (list
+    // overflow) a thread per kBinsPerThread consecutive bins
+    const int nfl = s_nflag;
+    if (nfl <= kFlagList) {  // block-uniform
+      for (int q = threadIdx.x; q < nfl; q += kThreads) {
+        const int b = flist[q];
+        insertion_sort_bin(s, (int)bin_get(s.bins, b), b + 1 < kBins ? (int)bin_get(s.bins, b + 1) : n);
+      }
+    } else {
+      const int b0 = threadIdx.x * kBinsPerThread;
+      unsigned m = (flag[b0 >> 5] >> (b0 & 31)) & ((1u << kBinsPerThread) - 1u);
+      while (m) {
+        const int b = b0 + __ffs(m) - 1;
+        m &= m - 1;
+        insertion_sort_bin(s, (int)bin_get(s.bins, b), b + 1 < kBins ? (int)bin_get(s.bins, b + 1) : n);
+      }
     }
     __syncthreads();
     return false;
@@ -720,14 +736,16 @@ template <int OP>
 __device__ void fold_scan(const uint32_t* hm, const uint16_t* hpre, const long long* col, int n, int fh, int xe,
                           long long* dst, long long cap, long long base) {
   const int lane = threadIdx.x & 31;
+  const unsigned below = 0xffffffffu >> (31 - lane);  // lanes 0..lane
   long long carry = op_id<OP>(), lacc = op_id<OP>();
   bool pend = false;  // warp-uniform: lane partials not yet in carry
   for (int b = fh & ~31; b < xe; b += 32) {
     const unsigned hb = hm[b >> 5];
+    const unsigned hn = b + 32 < n ? hm[(b >> 5) + 1] : 1u;  // next window's heads (past n: a head)
     const int p = b + lane;
     const bool own = p >= fh && p < xe;
     const long long v0 = own ? col[p] : op_id<OP>();
-    if (hb == 0 && b >= fh && b + 32 < xe && !(hm[(b >> 5) + 1] & 1u)) {
+    if (hb == 0 && b >= fh && !(hn & 1u) && b + 32 < xe) {
       // warp-uniform: the window lies inside one group, which goes on after it
       lacc = op_do<OP>(lacc, v0);
       pend = true;
@@ -739,9 +757,9 @@ __device__ void fold_scan(const uint32_t* hm, const uint16_t* hpre, const long l
       lacc = op_id<OP>();
       pend = false;
     }
-    const unsigned le = hb & (0xffffffffu >> (31 - lane));  // heads at or below the lane
-    const int ss = 31 - __clz(le);                          // its group's head lane; -1: an earlier window
-    const int d = ss >= 0 ? lane - ss : lane;               // earlier lanes of its group in this window
+    const unsigned le = hb & below;  // heads at or below the lane
+    const int ss = 31 - __clz(le);   // its group's head lane; -1: an earlier window
+    const int d = lane - max(ss, 0); // earlier lanes of its group in this window
     const int dmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)d);
     long long v = v0;
     for (int o = 1; o <= dmax; o <<= 1) {
@@ -750,8 +768,9 @@ __device__ void fold_scan(const uint32_t* hm, const uint16_t* hpre, const long l
     }
     if (ss < 0) v = op_do<OP>(v, carry);
     carry = __shfl_sync(0xffffffffu, v, 31);
-    const bool nh = lane < 31 ? ((hb >> (lane + 1)) & 1u) != 0 : (b + 32 >= n || (hm[(b >> 5) + 1] & 1u));
-    if (own && (nh || p + 1 == xe)) {
+    // the last position of a group: the next one is a head (or the range ends)
+    const unsigned lastm = (hb >> 1) | (hn << 31);
+    if (own && (((lastm >> lane) & 1u) || p + 1 == xe)) {
       const long long pos = base + (long long)hpre[b >> 5] + __popc(le) - 1;
       if (pos < cap) dst[pos] = v;
     }
