@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -130,14 +131,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _code_only(text):
+    """C++ source without comments, blank lines or indentation."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(l.strip() for l in text.splitlines() if l.strip())
+
+
 def src_sha():
-    """Hash of the device code (the kernel headers): the DRAM counters in
-    profiles/traffic.json hold only for the kernels they were taken on."""
+    """Hash of the device code (the kernel headers, comments stripped): the
+    DRAM counters in profiles/traffic.json hold only for the kernels they
+    were taken on."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2010_00152_gb300", "csrc")
     for f in sorted(os.listdir(d)):
         if f.endswith(".cuh"):
-            h.update(open(os.path.join(d, f), "rb").read())
+            h.update(_code_only(open(os.path.join(d, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

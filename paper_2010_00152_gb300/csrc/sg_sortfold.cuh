@@ -620,11 +620,11 @@ __device__ __forceinline__ long long chunk_base(const LookBack& lb, const OutSin
 }
 
 // ---------------------------------------------------------------------------
-// Fold for small key groups (every group within one bin of <= 32 rows): each
-// warp takes a contiguous range of sorted positions, a lane per position; a
-// lane holding the first row of a group folds the group's rows and writes one
-// output row.  Heads come from a ballot, output positions from popc and one
-// scan over warps, so consecutive lanes write consecutive rows.
+// Fold.  Each warp takes a contiguous, 32-aligned range of sorted positions,
+// a lane per position; heads (first rows of key groups) come from a ballot,
+// output positions from popc and one scan over warps, so consecutive lanes
+// write consecutive rows.  The warp folds the groups whose heads lie in its
+// range, by a lane per group or by segmented scans (fold_scan).
 // ---------------------------------------------------------------------------
 __shared__ int g_lcnt[kWarps + 1];
 
