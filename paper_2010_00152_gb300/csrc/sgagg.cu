@@ -551,6 +551,13 @@ sgagg_status sync_read(sgagg_t h, void* dst, const void* src, size_t bytes) {
   return SGAGG_OK;
 }
 
+// Host -> device copy ordered on the call's stream, complete on return.
+sgagg_status sync_write(sgagg_t h, void* dst, const void* src, size_t bytes) {
+  CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return SGAGG_OK;
+}
+
 sgagg_status check_device_err(sgagg_t h) {
   HostSmall* hs = hsmall(h);
   TRY(sync_read(h, &hs->err, &dsmall(h)->err, sizeof(int)));
@@ -846,7 +853,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     std::vector<Chunk> bch(info.n_big);
     long long tot = 0;
     for (int i = 0; i < info.n_big; ++i) {
-      CU(cudaMemcpy(&bch[i], P<Chunk>(h->chunks[depth]) + big[i], sizeof(Chunk), cudaMemcpyDeviceToHost));
+      TRY(sync_read(h, &bch[i], P<Chunk>(h->chunks[depth]) + big[i], sizeof(Chunk)));
       tot += bch[i].hi - bch[i].lo;
     }
     const int S = fd.n_state;
@@ -876,7 +883,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
       bch[i].lo = at;
       bch[i].hi = end;
       at = end;
-      CU(cudaMemcpy(P<Chunk>(h->chunks[depth]) + big[i], &bch[i], sizeof(Chunk), cudaMemcpyHostToDevice));
+      TRY(sync_write(h, P<Chunk>(h->chunks[depth]) + big[i], &bch[i], sizeof(Chunk)));
     }
     copy.keys = co.keys;
     for (int s = 0; s < S; ++s) copy.cols[s] = co.cols[s];
@@ -1045,7 +1052,7 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
     std::vector<Chunk> bch(info.n_big);
     long long tot = 0;
     for (int i = 0; i < info.n_big; ++i) {
-      CU(cudaMemcpy(&bch[i], P<Chunk>(h->chunks[0]) + big[i], sizeof(Chunk), cudaMemcpyDeviceToHost));
+      TRY(sync_read(h, &bch[i], P<Chunk>(h->chunks[0]) + big[i], sizeof(Chunk)));
       tot += bch[i].hi - bch[i].lo;
     }
     TRY(grow(h, h->copykeys[0], (size_t)tot * 8));
@@ -1061,8 +1068,8 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
       long long m = bch[i].hi - bch[i].lo;
       std::vector<long long> lo(K), hi(K), pre(K + 1, 0);
       for (int r = 0; r < K; ++r) {
-        CU(cudaMemcpy(&lo[r], rr[r].offs + bch[i].f_lo, 8, cudaMemcpyDeviceToHost));
-        CU(cudaMemcpy(&hi[r], rr[r].offs + bch[i].f_hi, 8, cudaMemcpyDeviceToHost));
+        TRY(sync_read(h, &lo[r], rr[r].offs + bch[i].f_lo, 8));
+        TRY(sync_read(h, &hi[r], rr[r].offs + bch[i].f_hi, 8));
         pre[r + 1] = pre[r] + (hi[r] - lo[r]);
       }
       TRY(grow(h, h->gather_keys, (size_t)m * 8));
@@ -1072,8 +1079,8 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
       TRY(grow(h, h->gather_ptrs, (size_t)(std::max(1, S) + K + 1) * 8));
       long long* dpre = P<long long>(h->gather_ptrs);
       long long** dcols = reinterpret_cast<long long**>(dpre + K + 1);
-      CU(cudaMemcpy(dpre, pre.data(), (size_t)(K + 1) * 8, cudaMemcpyHostToDevice));
-      CU(cudaMemcpy(dcols, gcols.data(), (size_t)std::max(1, S) * 8, cudaMemcpyHostToDevice));
+      TRY(sync_write(h, dpre, pre.data(), (size_t)(K + 1) * 8));
+      TRY(sync_write(h, dcols, gcols.data(), (size_t)std::max(1, S) * 8));
       dim3 grid(std::max(1, std::min(64, (int)((m / K + 255) / 256))), K);
       kbegin(h, SGAGG_K_OTHER);
       k_gather_runs<<<grid, 256, 0, stream>>>(rset, bch[i].f_lo, bch[i].f_hi, dpre,
@@ -1097,7 +1104,7 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
       bch[i].lo = at;
       bch[i].hi = e;
       at = e;
-      CU(cudaMemcpy(P<Chunk>(h->chunks[0]) + big[i], &bch[i], sizeof(Chunk), cudaMemcpyHostToDevice));
+      TRY(sync_write(h, P<Chunk>(h->chunks[0]) + big[i], &bch[i], sizeof(Chunk)));
     }
     copy.keys = co.keys;
     for (int s = 0; s < S; ++s) copy.cols[s] = co.cols[s];
@@ -1815,8 +1822,8 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
       if (d.n <= kTileCap) continue;
       std::vector<const int64_t*> pay(std::max(1, d.n_payload), nullptr);
       std::vector<int64_t*> oa(std::max(1, S), nullptr);
-      if (d.n_payload > 0) CU(cudaMemcpy(pay.data(), d.payload, (size_t)d.n_payload * 8, cudaMemcpyDeviceToHost));
-      if (S > 0) CU(cudaMemcpy(oa.data(), d.out_aggs, (size_t)S * 8, cudaMemcpyDeviceToHost));
+      if (d.n_payload > 0) TRY(sync_read(h, pay.data(), d.payload, (size_t)d.n_payload * 8));
+      if (S > 0) TRY(sync_read(h, oa.data(), d.out_aggs, (size_t)S * 8));
       int32_t kb = d.key_bytes;
       const void* kc = d.keys;
       sgagg_keys k{1, &kb, &kc};
@@ -1918,8 +1925,8 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
                                                           kTileCap);
       kend(h);
       TRY(sync_read(h, cnt1.data(), h->bstartb.p, (size_t)(gi + 1) * 8));
-      CU(cudaMemcpy(rng.data(), kmin_d + i0, (size_t)gi * 8, cudaMemcpyDeviceToHost));
-      CU(cudaMemcpy(rng.data() + count, kmax_d + i0, (size_t)gi * 8, cudaMemcpyDeviceToHost));
+      TRY(sync_read(h, rng.data(), kmin_d + i0, (size_t)gi * 8));
+      TRY(sync_read(h, rng.data() + count, kmax_d + i0, (size_t)gi * 8));
       int Db = 0;
       for (long long per = kBucketRows;; per *= 2) {
         long long tot = 0;
