@@ -266,6 +266,14 @@ def test_handle_reuse_across_shapes():
         agg.close()
 
 
+def test_merge_big_groups():
+    """~100 runs that each hold nearly every one of 500 keys: merge tiles of
+    some 80 key groups of ~100 rows each (groups across scan windows)."""
+    c = datagen.config1(n=200_003, seed=17, D=500)
+    st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=2048)
+    assert st["runs"] == 98
+
+
 @pytest.mark.parametrize("cap", [2, 3, 7])
 def test_preliminary_merges(cap):
     """More runs than one wide merge may take: the smallest runs are merged
