@@ -100,8 +100,9 @@ struct SortSmem {
   uint16_t* idx;              // [kTileCap] sorted permutation
   uint32_t* bins;             // [kBins / 2] packed 16-bit bin starts; LSD ping-pong buffer;
                               // then the inverse permutation (sorted position of each row)
-  uint16_t* whist;            // [kWarps * 256] LSD per-warp digit counts; bin flags; then
-                              // the head bitmask and its word prefix
+  uint16_t* whist;            // [kWarps * 256] LSD per-warp digit counts; or the bin flags,
+                              // big-bin and flagged-bin lists; then the head bitmask and
+                              // its word prefix
   long long* slo;             // [kMaxFanIn] merge: slice start per run, less the chunk
                               // position of the slice's first row
   long long* spre;            // [kMaxFanIn + 1] merge: slice prefix
