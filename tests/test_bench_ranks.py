@@ -45,3 +45,13 @@ def test_two_ranks_max_time_sum_rows():
 def test_one_process_unchanged():
     import bench
     assert bench.reduce_over_ranks(3.5, 42, torch.device("cpu")) == (3.5, 42)
+
+
+def test_traffic_key_ignores_comments_only():
+    """The DRAM counters are keyed to the kernel code: comments and layout do
+    not change the key, a code change does."""
+    import bench
+    code = "int f(int a) {\n  return a + 1;  // one more\n}\n/* block\n   comment */\n"
+    assert bench._code_only(code) == bench._code_only("int f(int a) {\n\n    return a + 1;\n}\n")
+    assert bench._code_only(code) != bench._code_only("int f(int a) {\n  return a + 2;\n}\n")
+    assert len(bench.src_sha()) == 16
