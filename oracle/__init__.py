@@ -6,7 +6,8 @@ CPU-baseline leg of ``bench.py`` may import this package.  The product path
 
 The arithmetic lives in ``sgagg_oracle.c`` (plain C: normalize keys, sort the
 (key, row) pairs with ``qsort``, fold equal keys in one in-stream pass).  This
-module only marshals numpy arrays into it.  ``spill_model`` holds the paper's
+module only marshals numpy arrays into it, and composes those steps for the
+hybrid run generation of Sec. 5.2.3.  ``spill_model`` holds the paper's
 closed-form spill analysis.
 
 Aggregate codes follow the problem statement of Sec. 1 (count(*), sum, min,
@@ -162,6 +163,43 @@ def absorb_runs(keys, payload, aggs, M, B):
     if r < 0:
         raise ValueError("bad absorbing run-generation arguments")
     return [int(x) for x in run_rows[:r]], int(left.value)
+
+
+def hybrid_bound(keys, M, F, f):
+    """Resident key range of hybrid run generation (Sec. 5.2.3): the lowest
+    keys, as many distinct keys as the index's share (1 - f/F) * M of memory
+    holds.  Returns the bound b: keys < b stay in memory (b = 0: none)."""
+    resident = int((1.0 - f / F) * M) if f < F else 0
+    uk = np.unique(np.asarray(keys, dtype=np.uint64))
+    if resident <= 0 or len(uk) == 0:
+        return 0
+    if resident >= len(uk):
+        return int(uk[-1]) + 1 if int(uk[-1]) < (1 << 64) - 1 else (1 << 64) - 1
+    return int(uk[resident])
+
+
+def hybrid_runs(keys, payload, aggs, M, F, f, bound):
+    """Hybrid run generation with early aggregation, then one wide merge
+    (Sec. 5.2.3): memory fraction 1 - f/F is an index that absorbs the rows
+    of the resident key range (keys < bound) without spilling; fraction f/F
+    runs read-sort-write cycles over the other rows (runs of f/F * M input
+    rows, each folded); the final merge folds the runs, and the resident
+    groups precede the merged ones in key order.
+
+    Returns (run row counts, rows absorbed in memory, resident distinct keys,
+    (out keys, out aggs)).
+    """
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    payload = [np.ascontiguousarray(p, dtype=np.int64) for p in payload]
+    res = keys < np.uint64(bound)
+    rk_, ra_ = groupby(keys[res], [p[res] for p in payload], aggs)
+    spill = ~res
+    m_run = max(1, int(f / F * M)) if f > 0 else max(1, len(keys))
+    runs, sk, ss = run_generation(keys[spill], [p[spill] for p in payload], aggs, m_run)
+    mk, ma = fold_states(sk, ss, [op for op, _ in aggs])
+    out_k = np.concatenate([rk_, mk])
+    out_a = [np.concatenate([a, b]) for a, b in zip(ra_, ma)]
+    return runs, int(res.sum()), len(rk_), (out_k, out_a)
 
 
 def count_distinct(key_cols, ucol, payload, aggs):
