@@ -168,30 +168,30 @@ def absorb_runs(keys, payload, aggs, M, B):
 def hybrid_bound(keys, M, F, f):
     """Resident key range of hybrid run generation (Sec. 5.2.3): the lowest
     keys, as many distinct keys as the index's share (1 - f/F) * M of memory
-    holds.  Returns the bound b: keys < b stay in memory (b = 0: none)."""
+    holds.  Returns the last resident key t (keys <= t stay in memory), or
+    None when no key is resident."""
     resident = int((1.0 - f / F) * M) if f < F else 0
     uk = np.unique(np.asarray(keys, dtype=np.uint64))
     if resident <= 0 or len(uk) == 0:
-        return 0
-    if resident >= len(uk):
-        return int(uk[-1]) + 1 if int(uk[-1]) < (1 << 64) - 1 else (1 << 64) - 1
-    return int(uk[resident])
+        return None
+    return int(uk[min(resident, len(uk)) - 1])
 
 
-def hybrid_runs(keys, payload, aggs, M, F, f, bound):
+def hybrid_runs(keys, payload, aggs, M, F, f, last):
     """Hybrid run generation with early aggregation, then one wide merge
     (Sec. 5.2.3): memory fraction 1 - f/F is an index that absorbs the rows
-    of the resident key range (keys < bound) without spilling; fraction f/F
-    runs read-sort-write cycles over the other rows (runs of f/F * M input
-    rows, each folded); the final merge folds the runs, and the resident
-    groups precede the merged ones in key order.
+    of the resident key range (keys <= last; none when last is None)
+    without spilling; fraction f/F runs read-sort-write cycles over the
+    other rows (runs of f/F * M input rows, each folded); the final merge
+    folds the runs, and the resident groups precede the merged ones in key
+    order.
 
     Returns (run row counts, rows absorbed in memory, resident distinct keys,
     (out keys, out aggs)).
     """
     keys = np.ascontiguousarray(keys, dtype=np.uint64)
     payload = [np.ascontiguousarray(p, dtype=np.int64) for p in payload]
-    res = keys < np.uint64(bound)
+    res = keys <= np.uint64(last) if last is not None else np.zeros(len(keys), dtype=bool)
     rk_, ra_ = groupby(keys[res], [p[res] for p in payload], aggs)
     spill = ~res
     m_run = max(1, int(f / F * M)) if f > 0 else max(1, len(keys))

@@ -36,7 +36,7 @@ def test_hybrid_output_is_the_grouping(M, F, D, n):
     runs, absorbed, resident, out = oracle.hybrid_runs(k, pay, AGGS, M, F, f, b)
     assert same(out, oracle.groupby(k, pay, AGGS))
     assert resident <= (1 - f / F) * M  # the index never holds more than its share
-    assert absorbed == int((k < np.uint64(b)).sum())
+    assert absorbed == (int((k <= np.uint64(b)).sum()) if b is not None else 0)
 
 
 def test_hybrid_paper_example():
@@ -83,7 +83,7 @@ def test_hybrid_full_partitioning():
     k, pay = case(30_000, 5_000, 4)
     M, F = 700, 8
     b = oracle.hybrid_bound(k, M, F, F)
-    assert b == 0
+    assert b is None
     runs, absorbed, resident, out = oracle.hybrid_runs(k, pay, AGGS, M, F, F, b)
     assert absorbed == 0 and resident == 0
     assert len(runs) == math.ceil(len(k) / M)
@@ -97,8 +97,24 @@ def test_hybrid_runs_brute_force():
     M, F, f = 200, 5, 2
     b = oracle.hybrid_bound(k, M, F, f)
     runs, absorbed, resident, _ = oracle.hybrid_runs(k, pay, AGGS, M, F, f, b)
-    spilled = [int(x) for x in k if int(x) >= b]
+    spilled = [int(x) for x in k if int(x) > b]
     m = int(f / F * M)
     expect = [len(set(spilled[i:i + m])) for i in range(0, len(spilled), m)]
     assert runs == expect
-    assert resident == len({int(x) for x in k if int(x) < b}) == int((1 - f / F) * M)
+    assert resident == len({int(x) for x in k if int(x) <= b}) == int((1 - f / F) * M)
+
+
+def test_hybrid_top_key_stays_resident():
+    """Every key fits the index, the largest being 2^64 - 1: it stays
+    resident with the others, nothing spills, and the resident count is
+    the whole output."""
+    rng = np.random.default_rng(3)
+    k = rng.integers(0, 50, 5_000, dtype=np.uint64)
+    k[::97] = np.uint64((1 << 64) - 1)
+    pay = [rng.integers(-9, 9, 5_000), rng.integers(-9, 9, 5_000)]
+    M, F, f = 1000, 10, 1
+    b = oracle.hybrid_bound(k, M, F, f)
+    assert b == (1 << 64) - 1
+    runs, absorbed, resident, out = oracle.hybrid_runs(k, pay, AGGS, M, F, f, b)
+    assert runs == [] and absorbed == len(k) and resident == len(np.unique(k)) == 51
+    assert same(out, oracle.groupby(k, pay, AGGS))
