@@ -216,7 +216,9 @@ def run_reference(args):
             "ms_per_step": n / val * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOADS[name]["desc"], "rows": n,
-                       "note": "CPU oracle timed on a bounded sample; value scaled per row"},
+                       "note": "ms_per_step is a per-row extrapolation, not a timed run of the workload: "
+                               "the oracle's rows/s on a bounded sample (one batch, no runs or merge) "
+                               "scaled to the workload's rows"},
             "cpu_baseline": {"value": val, "unit": "rows/s", "cores": 1, "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": val, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -224,12 +226,16 @@ def run_reference(args):
     return 0
 
 
-def bench_batched(args, dev):
+def bench_batched(args, dev, steps=None, warmup=None, plain_steps=None):
     """Config 4: the batched call against the plain loop of one call per
-    instance over the same instances (both through the C ABI)."""
+    instance over the same instances (both through the C ABI).  Returns the
+    result line (a dict)."""
     import torch
     import datagen
     from paper_2010_00152_gb300 import sgagg
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    plain_steps = max(1, steps // 2) if plain_steps is None else plain_steps
     count = args.instances or WORKLOADS["c4"]["n"]
     specs = datagen.config4_instances(count=count, seed=1)
     insts = [datagen.config4_instance(sp, device=dev) for sp in specs]
@@ -286,23 +292,25 @@ def bench_batched(args, dev):
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
-    ms_b, rows_b = timed(batched, args.steps, args.warmup)
-    clk = clocks.stop()
+    ms_b, rows_b = timed(batched, steps, warmup)
     st = agg.stats()
-    ms_p, rows_p = timed(plain, max(1, args.steps // 2), 1)
+    ms_p, rows_p = timed(plain, plain_steps, 1)
+    clk = clocks.stop()
     assert rows_b == rows_p, (rows_b, rows_p)
     line = {"metric": "rows/s grouped (batched)", "value": n_total / (ms_b / 1e3), "unit": "rows/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms_b, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded)",
             "config": {"workload": WORKLOADS["c4"]["desc"], "instances": count, "rows": n_total},
-            "plain": {"value": n_total / (ms_p / 1e3), "ms_per_step": ms_p,
+            "plain": {"value": n_total / (ms_p / 1e3), "ms_per_step": ms_p, "steps": plain_steps,
                       "note": "one sgagg_aggregate call per instance, same instances"},
             "speedup_vs_plain": ms_p / ms_b, "out_rows": rows_b, "clocks": clk,
+            "timing": "CUDA events on the call stream around each form's timed steps",
             "kernels": {k: v for k, v in st["kernels"].items() if v["launches"]},
-            "gpu_launches": st["kernel_launches"] * args.steps}
-    print(json.dumps(line))
+            "gpu_launches": st["kernel_launches"] * steps}
     agg.close()
-    return 0
+    del insts, outs, keep, descs
+    torch.cuda.empty_cache()
+    return line
 
 
 def reduce_over_ranks(ms, rows, device):
@@ -371,16 +379,16 @@ def run_stream(srv_kw, specs, rate, dev, aggs, budget, pool):
     return lat, rows, (max(done_ns) - t0) / 1e9
 
 
-def bench_serving(args, dev):
+def bench_serving(args, dev, count=None, load_factors=(0.5, 0.8, 1.0, 1.5)):
     """Config 5: the request loop (slots, admission, continuous batching)
     against the plain form (one call per request, one after another) on the
-    same Poisson stream, at offered loads 0.5, 0.8 and 1.0 x the plain
-    form's measured capacity."""
+    same Poisson stream, at offered loads 0.5, 0.8, 1.0 (and 1.5) x the plain
+    form's measured capacity.  Returns the result line (a dict)."""
     import numpy as np
     import torch
     import datagen
     from paper_2010_00152_gb300 import sgagg
-    count = args.requests or WORKLOADS["c5"]["n"]
+    count = count or args.requests or WORKLOADS["c5"]["n"]
     specs = datagen.config5_requests(count=count, seed=1)
     aggs = [(0, 0), (1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (3, 1)]
     budget = 64 << 30
@@ -414,7 +422,7 @@ def bench_serving(args, dev):
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
     loads = []
-    for f in (0.5, 0.8, 1.0, 1.5):
+    for f in load_factors:
         entry = {"load": f, "rate_rps": round(f * plain_rps, 2)}
         for name, kw in (("plain", plain), ("served", served)):
             lat, rows, span = run_stream(kw, specs, f * plain_rps, dev, aggs, budget // 2, pool)
@@ -431,8 +439,9 @@ def bench_serving(args, dev):
             "note": "value = served capacity (rows/s, closed loop over the first capacity_requests requests); "
                     "loads = open-loop Poisson replays of all requests at the given multiple of the plain "
                     "form's capacity, latency from scheduled arrival to results final"}
-    print(json.dumps(line))
-    return 0
+    del pool
+    torch.cuda.empty_cache()
+    return line
 
 
 def main():
@@ -446,6 +455,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the batched and served sub-objects")
+    ap.add_argument("--sub-requests", type=int, default=4000,
+                    help="requests of the served sub-object's Poisson replays")
     ap.add_argument("--instances", type=int, default=None, help="c4: instance count")
     ap.add_argument("--requests", type=int, default=None, help="c5: request count")
     ap.add_argument("--capacity-requests", type=int, default=1000,
@@ -470,9 +482,11 @@ def main():
 
     name = args.config
     if name == "c4":
-        return bench_batched(args, dev)
+        print(json.dumps(bench_batched(args, dev)))
+        return 0
     if name == "c5":
-        return bench_serving(args, dev)
+        print(json.dumps(bench_serving(args, dev)))
+        return 0
     w = make_workload(name, dev, args.rows)
     n = int(w["key_cols"][0].numel())
     M = int(w["M"])
@@ -545,6 +559,18 @@ def main():
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(name)
 
+    # the batched (4,096 instances) and served (Poisson request stream)
+    # workloads on the same GPU, after the main workload's buffers are freed
+    sub = {}
+    temp_bytes = agg.temp_bytes()
+    if name == "c3" and world == 1 and not args.no_sub:
+        agg.close()
+        agg = None
+        del w, ok, oa
+        torch.cuda.empty_cache()
+        sub["batched"] = bench_batched(args, dev, steps=3, warmup=1, plain_steps=1)
+        sub["served"] = bench_serving(args, dev, count=args.sub_requests, load_factors=(0.5, 0.8, 1.0))
+
     if rank == 0:
         line = {
             "metric": "rows/s grouped", "value": value, "unit": "rows/s", "n_gpus": world,
@@ -561,13 +587,15 @@ def main():
                          "ms_per_launch": round(per_launch_ms, 4)},
             "method_bytes_per_step": int(alg),
             "method_hbm_frac": round(alg / (ms_max / 1e3) / 1e9 / hbm, 4),
-            "temp_bytes": agg.temp_bytes(), "output_bytes": int(out_b),
+            "temp_bytes": temp_bytes, "output_bytes": int(out_b),
             "runs": st["runs"], "run_rows": st["run_rows"], "out_rows": rows,
             "kernels": kernels, "clocks": clk, "gpu_launches": launches,
             "e2e": e2e, "cpu_baseline": cpu,
         }
+        line.update(sub)
         print(json.dumps(line))
-    agg.close()
+    if agg is not None:
+        agg.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -104,9 +104,14 @@ typedef struct {
     /* Per kernel class (see SGAGG_K_*): launches, compulsory bytes (every
      * input of the launch read once, every output written once) and, with
      * SGAGG_OPT_TIMING, the summed CUDA-event time of the launches in ms. */
-    int64_t class_launches[8];
-    int64_t class_bytes[8];
-    double class_ms[8];
+    int64_t class_launches[9];
+    int64_t class_bytes[9];
+    double class_ms[9];
+    /* SGAGG_OPT_POLICY 2 (hybrid run generation): rows absorbed by the
+     * in-memory index, its distinct keys, and the fan-out f used. */
+    int64_t resident_rows;
+    int64_t resident_keys;
+    int64_t hybrid_f;
 } sgagg_stats_t;
 
 /* Kernel classes of sgagg_stats_t. */
@@ -118,9 +123,11 @@ enum {
     SGAGG_K_PREFOLD = 4,    /* tile sort+fold before partitioning */
     SGAGG_K_RUNGEN = 5,     /* chunk sort+fold writing a run (or the output) */
     SGAGG_K_MERGE = 6,      /* wide merge: sort+fold of merge tiles */
-    SGAGG_K_OTHER = 7       /* copies: gathers of split key ranges, the batched call's
+    SGAGG_K_OTHER = 7,      /* copies: gathers of split key ranges, the batched call's
                                output copy, the absorbing index's runs, the
                                count(distinct) regroup */
+    SGAGG_K_STREAM = 8      /* one streaming fold of a batch whose keys take few values
+                               (at most 16 distinct keys in the planner's sample) */
 };
 
 /* Options for sgagg_set_option. */
@@ -135,10 +142,11 @@ typedef enum {
                                      merges of the smallest runs first (Sec. 4.3). 0 = auto */
     SGAGG_OPT_FAULT_ALLOC = 5,    /* test hook: fail the k-th internal allocation (0 = off) */
     SGAGG_OPT_TIMING = 6,         /* 1: time every kernel class with CUDA events (class_ms) */
-    SGAGG_OPT_TEST_STALL = 7,     /* test hook: in the next sort+fold launch the first chunk
-                                     never publishes its row count, so the bounded waits of
-                                     the others run out -> SGAGG_ETIMEOUT (no hang) */
-    SGAGG_OPT_POLICY = 8,         /* run generation: 0 (default) one run per batch of
+    SGAGG_OPT_TEST_STALL = 7,     /* test hook: 1 -- in the next sort+fold or merge launch
+                                     the first chunk never publishes its row count, so the
+                                     bounded waits of the others run out -> SGAGG_ETIMEOUT
+                                     (no hang); 2 -- the same in the next merge launch */
+    SGAGG_OPT_POLICY = 8,         /* run generation (2: hybrid, below): 0 (default) one run per batch of
                                      memory_budget_rows rows, holding the batch's distinct
                                      keys; 1 an absorbing index of at most memory_budget_rows
                                      distinct keys (Sec. 3, Sec. 6.1): each batch is sorted
@@ -146,8 +154,22 @@ typedef enum {
                                      or inserted in ascending order, and when the index is
                                      full it is written as a run and emptied -- no run at all
                                      when the output fits memory_budget_rows */
-    SGAGG_OPT_ABSORB_BATCH = 9    /* rows per batch of policy 1 (0 = min(memory_budget_rows,
+    SGAGG_OPT_ABSORB_BATCH = 9,   /* rows per batch of policy 1 (0 = min(memory_budget_rows,
                                      2^22)); the runs depend on it, the result does not */
+    SGAGG_OPT_LOWCARD = 10,       /* one batch whose key sample holds at most 16 distinct
+                                     keys is grouped by one streaming fold (SGAGG_K_STREAM)
+                                     unless this is 0; -1 (default) auto.  Same result. */
+    SGAGG_OPT_MERGE_THREADS = 11, /* threads of one wide-merge CTA (a tile of 2048 rows):
+                                     128, 256 or 512; 0 (default) = 256.  Same result. */
+    SGAGG_OPT_HYBRID_FANIN = 12,  /* policy 2: the maximal fan-in F (default 10) */
+    SGAGG_OPT_HYBRID_F = 13,      /* policy 2: the actual fan-out f, 0..F; -1 (default):
+                                     ceil((O - M) / (M - 1)) from the output size O
+                                     estimated on the key sample, at most F */
+    SGAGG_OPT_HYBRID_LAST = 14,   /* policy 2: the last key of the resident range (the
+                                     normalized key's 64 bits); keys at or below it stay in
+                                     the in-memory index.  Default: estimated on the key
+                                     sample so that the range holds (1 - f/F) M keys */
+    SGAGG_OPT_HYBRID_LAST_AUTO = 15  /* policy 2: back to the estimated resident range */
 } sgagg_option;
 
 /*
@@ -275,6 +297,25 @@ sgagg_status sgagg_aggregate_batched(sgagg_t h, const sgagg_instance *inst, int3
                                      const sgagg_spec *spec, void *stream);
 
 /*
+ * Hybrid run generation (SGAGG_OPT_POLICY 2, Sec. 5.2.3): memory fraction
+ * 1 - f/F of the budget M is an in-memory index that absorbs the rows of the
+ * lowest keys -- the resident range, (1 - f/F) M distinct keys -- without
+ * spilling; the other rows are grouped in read-sort-write runs of f/F * M
+ * rows each, and one wide merge folds the runs.  The output is the same as
+ * with any other policy.  f = 0: everything resident, no run; f = F: no
+ * index, runs of M rows.  sgagg_stats gives the resident rows and keys.
+ */
+
+/*
+ * Rows of each run the last call wrote (the paper's spill volume, run by run),
+ * in the order written: run generation's runs, then those of preliminary
+ * merges.  Copies min(*count, max_runs) entries to rows (host memory) and sets
+ * *count to the number of runs.  Synchronizes with the last call's stream.
+ * SGAGG_EINVAL for a null handle or count, or rows null with max_runs > 0.
+ */
+sgagg_status sgagg_run_sizes(sgagg_t h, int64_t *rows, int64_t max_runs, int64_t *count);
+
+/*
  * Group at most SGAGG_NOALLOC_MAX_ROWS rows without allocating any memory.
  * The paper has no counterpart; this exists for callers that cannot allocate
  * device memory at all, e.g. code running inside a memory pool or allocator
@@ -291,9 +332,12 @@ sgagg_status sgagg_aggregate_batched(sgagg_t h, const sgagg_instance *inst, int3
  * (SGAGG_NOALLOC_SCRATCH_BYTES), held by every GPU that loads the library
  * until the process exits.  Every call shares it and overwrites it, so calls
  * whose work overlaps on the GPU (other streams, other host threads) race:
- * serialize them.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.
+ * serialize them.  The first call on a device does a one-time set-up with
+ * that device current: it looks up the array's device address
+ * (cudaGetSymbolAddress) and loads every kernel this call launches (with
+ * lazy module loading a kernel's first launch may load its module, which
+ * allocates).  Make that first call before any stream capture and outside
+ * the code that cannot allocate; every later call allocates nothing.
  *
  * Errors: n > SGAGG_NOALLOC_MAX_ROWS, or any argument error of
  * sgagg_aggregate, returns SGAGG_EINVAL before any GPU work;

@@ -232,17 +232,29 @@ __device__ __forceinline__ void err_raise(int* p, int code) {
   atomicCAS(p, 0, code);
 }
 
-// Called by one full warp.  Publishes `count` for chunk `id` and returns the
-// exclusive prefix, or -1 after raising ERR_TIMEOUT (or seeing another error).
-__device__ long long lookback_warp(const LookBack& lb, int id, long long count) {
+// Publishes chunk `id`'s row count (lane 0 of the calling warp stores):
+// chunk 0 its inclusive prefix (base + count), every other chunk its
+// aggregate.  Returns chunk 0's base (0 for other chunks), read here once:
+// base_in may be the same word as total_out, which the last chunk writes as
+// soon as chunk 0's prefix is out.
+__device__ __forceinline__ long long lookback_publish(const LookBack& lb, int id, long long count) {
+  const long long b0 = (id == 0 && lb.base_in) ? *lb.base_in : 0;
+  if ((threadIdx.x & 31) != 0) return b0;
+  if (id == 0) {
+    if (!lb.stall) lb_store(&lb.status[0], kFlagPre | (unsigned long long)(b0 + count));
+  } else {
+    lb_store(&lb.status[id], kFlagAgg | (unsigned long long)count);
+  }
+  return b0;
+}
+
+// Called by one full warp after lookback_publish (b0: what it returned).
+// Returns the exclusive prefix of chunk `id` and publishes its inclusive
+// prefix, or returns -1 after raising ERR_TIMEOUT (or seeing another error).
+__device__ long long lookback_resolve(const LookBack& lb, int id, long long count, long long b0) {
   const int lane = threadIdx.x & 31;
   long long excl = 0;
-  if (id == 0) {
-    excl = lb.base_in ? *lb.base_in : 0;
-    if (lane == 0 && !lb.stall) lb_store(&lb.status[0], kFlagPre | (unsigned long long)(excl + count));
-    return excl;
-  }
-  if (lane == 0) lb_store(&lb.status[id], kFlagAgg | (unsigned long long)count);
+  if (id == 0) return b0;
   int j = id - 1;  // highest predecessor not yet folded into excl
   long long spins = 0;
   while (true) {
@@ -279,10 +291,17 @@ __device__ long long lookback_warp(const LookBack& lb, int id, long long count) 
       if (lane == 0) err_raise(lb.err, ERR_TIMEOUT);
       return -1;
     }
-    __nanosleep(64);
+    __nanosleep(spins < 4 ? 64u : 512u);  // back off once a wait is not short
   }
   if (lane == 0) lb_store(&lb.status[id], kFlagPre | (unsigned long long)(excl + count));
   return excl;
+}
+
+// Called by one full warp.  Publishes `count` for chunk `id` and returns the
+// exclusive prefix, or -1 after raising ERR_TIMEOUT (or seeing another error).
+__device__ __forceinline__ long long lookback_warp(const LookBack& lb, int id, long long count) {
+  const long long b0 = lookback_publish(lb, id, count);
+  return lookback_resolve(lb, id, count, b0);
 }
 
 }  // namespace sg

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <memory>
 #include <cmath>
 #include <cstdio>
@@ -25,6 +26,9 @@
 
 #include "../../include/sgagg.h"
 #include "sg_part.cuh"
+#include "sg_merge.cuh"
+#include "sg_lowcard.cuh"
+#include "sg_hybrid.cuh"
 
 using namespace sg;
 
@@ -38,6 +42,17 @@ namespace {
 constexpr long long kBigBucket = 2048;
 constexpr long long kChunkTarget = kTileCap - kBigBucket;
 constexpr long long kBucketRows = 1024;
+constexpr int kClasses = SGAGG_K_STREAM + 1;
+// The streaming fold of few keys (k_lowcard) is taken for one batch of at
+// least this many rows.
+constexpr long long kLowCardMinRows = 1ll << 16;
+// Merge tiles (k_merge): at most kMergeTile rows over all runs; fine buckets
+// of the runs' sparse indexes average at most kMergeFineRows rows, so tiles
+// are packed close to the cap.
+constexpr long long kMergeFineRows = 256;
+// Runs are allocated with this many bytes past their last row: a merge
+// tile's bulk copy of a slice may read one row past the slice.
+constexpr size_t kRunSlack = 16;
 constexpr int kMaxDepth = 70;
 constexpr long long kMaxBatch = 1ll << 30;
 constexpr int kSample = 16384;
@@ -63,6 +78,7 @@ struct RunRef {
   const long long* cols[sg::kMaxCols];
   long long* offs;   // nf + 1 fine-bucket offsets (absolute rows of its arrays)
   long long rows;
+  int host = 0;      // arrays in pinned host memory (no bulk copies from them)
 };
 
 }  // namespace
@@ -104,6 +120,15 @@ struct sgagg_ctx {
   int test_stall = 0;
   int policy = 0;                // 0: a run per batch, 1: absorbing index
   long long absorb_batch = 0;    // rows per batch of the absorbing policy (0: auto)
+  int lowcard = -1;              // streaming fold of few keys: -1 auto, 0 off
+  int merge_threads = 0;         // threads of a merge CTA (128, 256, 512; 0 = default)
+  int hybrid_fanin = 10;         // hybrid run generation (policy 2): F
+  int hybrid_f = -1;             // f (-1: from the estimated output size)
+  bool hybrid_last_given = false;
+  unsigned long long hybrid_last = 0;   // last key of the resident range, when given
+  std::vector<long long> run_sizes;     // rows of each run of the last call, in the order written
+  DevBuf hsplit_keys[2];               // hybrid: resident / spilled rows (SoA)
+  std::vector<DevBuf> hsplit_cols[2];
   std::string err;
   // per-launch event pairs (SGAGG_OPT_TIMING)
   struct KT { cudaEvent_t a = nullptr, b = nullptr; int cls = 0; };
@@ -146,6 +171,8 @@ struct sgagg_ctx {
   DevBuf ab_keys[3], ab_offs[3], ab_tmp;   // absorbing policy: index, batch, merged index
   DevBuf dk_keys, rg_heads;                // count(distinct): (g, u) rows, regroup block heads
   DevBuf plan_tmp;                         // chunk planner: per-block sums and starts
+  DevBuf lc_part;                          // streaming fold of few keys: per-block partials
+  DevBuf tslo;                             // wide merge: every tile's slice start in every run
   std::vector<DevBuf> dk_cols;
   std::vector<DevBuf> ab_cols[3];
   DevBuf marena_keys;            // runs written by preliminary merges
@@ -195,7 +222,11 @@ struct Small {
   long long total;              // total_out of the final sort+fold
   long long pftot;              // total_out of a pre-fold pass
   long long dsum;               // rows of the one-chunk instances of a batched call
+  int lc_over;                  // streaming fold of few keys: a key outside the sample
+  int lc_pad;
   long long part_tot[kMergeParts];  // final merge in parts: output end of every part
+  long long hy_rows;            // hybrid: resident rows (split total)
+  long long hy_keys;            // hybrid: resident groups = output base of the merged runs
   long long dtot[kMaxDepth + 2];  // base/total of the sub-solves under depth d
 };
 
@@ -439,13 +470,28 @@ bool want_prefold(sgagg_t h, long long sample_n, long long distinct) {
   return per_tile * 2.0 <= (double)kTileCap;
 }
 
+// Kernel attributes belong to one device's context: each kind of setup
+// keeps a bit per device index (set once the attributes are in place; two
+// threads racing on a new device both set them, which is harmless).
+struct DeviceOnce {
+  std::atomic<unsigned long long> mask{0};
+  bool need(int* dev) {
+    if (cudaGetDevice(dev) != cudaSuccess) *dev = 0;
+    return *dev >= 64 || !((mask.load(std::memory_order_acquire) >> *dev) & 1ull);
+  }
+  void done(int dev) {
+    if (dev < 64) mask.fetch_or(1ull << dev, std::memory_order_release);
+  }
+};
+
 template <int MODE, int KS>
 void set_smem_attr() {
-  static bool done = false;
-  if (!done) {
+  static DeviceOnce once;
+  int dev = 0;
+  if (once.need(&dev)) {
     cudaFuncSetAttribute(k_sortfold<MODE, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kSortSmemBytes);
-    done = true;
+    once.done(dev);
   }
 }
 
@@ -462,8 +508,9 @@ void launch_ks(int grid, cudaStream_t st, const Chunk* dchunks, const RowSrc& sr
 constexpr int kMaxCoarseBits = 15;  // per-tile histogram / cursors: 2^15 x 4 B of shared memory
 
 void set_part_attrs() {
-  static bool done = false;
-  if (!done) {
+  static DeviceOnce once;
+  int dev = 0;
+  if (once.need(&dev)) {
     cudaFuncSetAttribute(k_hist<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
     cudaFuncSetAttribute(k_hist<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
     cudaFuncSetAttribute(k_hist<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << kMaxCoarseBits) * 4);
@@ -482,7 +529,7 @@ void set_part_attrs() {
                          (int)staged_smem_bytes(1 << kMaxCoarseBits > 1024 ? 1024 : 1 << kMaxCoarseBits, kStageCols));
     cudaFuncSetAttribute(k_hist2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_hist2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    done = true;
+    once.done(dev);
   }
 }
 
@@ -527,8 +574,8 @@ sgagg_status launch_sortfold(sgagg_t h, int cls, const Chunk* dchunks, int n_chu
   lb.err = &dsmall(h)->err;
   lb.spin_limit = h->spin_limit;
   lb.n_chunks = n_chunks;
-  lb.stall = h->test_stall;
-  h->test_stall = 0;
+  lb.stall = h->test_stall == 1 ? 1 : 0;  // 2 waits for the next merge launch
+  if (h->test_stall == 1) h->test_stall = 0;
   kbegin(h, cls);
   if (fd.n_state <= 2)
     launch_ks<MODE, 2>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
@@ -540,6 +587,75 @@ sgagg_status launch_sortfold(sgagg_t h, int cls, const Chunk* dchunks, int n_chu
     launch_ks<MODE, 16>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
   else
     launch_ks<MODE, 32>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
+  kend(h);
+  CU(cudaGetLastError());
+  return SGAGG_OK;
+}
+
+// Launch the wide-merge kernel over n_chunks merge tiles of at most
+// kMergeTile rows.  bulk: every run array is device memory with a 16-byte
+// aligned start and kRunSlack bytes past its rows (slices are bulk-copied).
+sgagg_status launch_merge(sgagg_t h, const Chunk* dchunks, int n_chunks, const long long* tslo, const RunSet& runs,
+                          bool bulk, const CopySrc& copy, const FoldDesc& fd, const OutSink& out,
+                          const long long* base_in, long long* total_out) {
+  if (n_chunks <= 0) {
+    if (total_out) {
+      if (base_in) CU(cudaMemcpyAsync(total_out, base_in, 8, cudaMemcpyDeviceToDevice, h->stream));
+      else CU(cudaMemsetAsync(total_out, 0, 8, h->stream));
+    }
+    return SGAGG_OK;
+  }
+  TRY(grow(h, h->status, (size_t)(n_chunks + 2) * 8));
+  CU(cudaMemsetAsync(h->status.p, 0, (size_t)(n_chunks + 2) * 8, h->stream));
+  MergeArgs a{};
+  a.lb.ticket = reinterpret_cast<unsigned int*>(P<unsigned long long>(h->status));
+  a.lb.status = P<unsigned long long>(h->status) + 2;
+  a.lb.base_in = reinterpret_cast<const long long*>(base_in);
+  a.lb.total_out = reinterpret_cast<long long*>(total_out);
+  a.lb.err = &dsmall(h)->err;
+  a.lb.spin_limit = h->spin_limit;
+  a.lb.n_chunks = n_chunks;
+  a.lb.stall = h->test_stall != 0 ? 1 : 0;
+  h->test_stall = 0;
+  a.chunks = dchunks;
+  a.tslo = tslo;
+  a.runs = runs;
+  a.copy = copy;
+  a.fd = fd;
+  a.out = out;
+  a.bulk = bulk ? 1 : 0;
+  const int k = runs.k, S = runs.ncols;
+  a.capk = (int)(((kMergeTile + 2ll * k) + 15) / 16 * 16);
+  const int threads = h->merge_threads > 0 ? h->merge_threads : 256;
+  if (a.capk > kMergeCapMax) return fail(h, SGAGG_ECUDA, "merge fan-in exceeds the tile layout");
+  // state columns staged at once: all of them (at least two buffers) within
+  // three CTAs per SM, else all within two, else as many as fit two
+  constexpr size_t kBudget3 = 74 * 1024, kBudget2 = 112 * 1024;
+  const int want = std::max(2, S);
+  int scol;
+  if (merge_smem_bytes(a.capk, want, k, threads) <= kBudget3) {
+    scol = want;
+  } else if (merge_smem_bytes(a.capk, want, k, threads) <= kBudget2) {
+    scol = want;
+  } else {
+    scol = 2;
+    while (scol + 1 < want && merge_smem_bytes(a.capk, scol + 1, k, threads) <= kBudget2) ++scol;
+  }
+  a.scol = scol;
+  const size_t smem = merge_smem_bytes(a.capk, a.scol, k, threads);
+  if (smem > 200 * 1024) return fail(h, SGAGG_ECUDA, "merge tile does not fit shared memory");
+  static DeviceOnce once;
+  int dev = 0;
+  if (once.need(&dev)) {
+    CU(cudaFuncSetAttribute(k_merge<128, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CU(cudaFuncSetAttribute(k_merge<256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CU(cudaFuncSetAttribute(k_merge<512, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    once.done(dev);
+  }
+  kbegin(h, SGAGG_K_MERGE);
+  if (threads == 128) k_merge<128, 16><<<n_chunks, 128 + 32, smem, h->stream>>>(a);
+  else if (threads == 512) k_merge<512, 4><<<n_chunks, 512 + 32, smem, h->stream>>>(a);
+  else k_merge<256, 8><<<n_chunks, 256 + 32, smem, h->stream>>>(a);
   kend(h);
   CU(cudaGetLastError());
   return SGAGG_OK;
@@ -576,7 +692,8 @@ struct Solver {
 // The chunk planner over nb bucket counts w: six small launches over up to
 // 1024 blocks (k_plan_*), one bucket per thread up to 2^18 buckets.
 sgagg_status run_plan(sgagg_t h, const long long* w, int nb, int fine_shift, long long* bstart, Chunk* chunks,
-                      int* biglist, PlanInfo* info) {
+                      int* biglist, PlanInfo* info, long long cap = kTileCap, long long target = kChunkTarget,
+                      long long big = kBigBucket) {
   cudaStream_t st = h->stream;
   const int sub = std::max(1, (nb + kPlanThreads * 1024 - 1) / (kPlanThreads * 1024));
   const int per = sub * kPlanThreads;
@@ -584,11 +701,11 @@ sgagg_status run_plan(sgagg_t h, const long long* w, int nb, int fine_shift, lon
   TRY(grow(h, h->plan_tmp, (size_t)(4 * g + 4) * 8));
   long long* part = P<long long>(h->plan_tmp);
   long long* starts = part + 3 * g;
-  k_plan_sums<<<g, kPlanThreads, 0, st>>>(w, nb, per, sub, kBigBucket, kTileCap, part);
+  k_plan_sums<<<g, kPlanThreads, 0, st>>>(w, nb, per, sub, big, cap, part);
   k_plan_scan3<<<1, 1024, 0, st>>>(part, g, nb, bstart, info);
-  k_plan_starts<<<g, kPlanThreads, 0, st>>>(w, nb, per, sub, kChunkTarget, kBigBucket, part, starts);
+  k_plan_starts<<<g, kPlanThreads, 0, st>>>(w, nb, per, sub, target, big, part, starts);
   k_plan_scan1<<<1, 1024, 0, st>>>(starts, g, info);
-  k_plan_apply<<<g, kPlanThreads, 0, st>>>(w, nb, per, sub, kChunkTarget, kBigBucket, kTileCap, part, starts,
+  k_plan_apply<<<g, kPlanThreads, 0, st>>>(w, nb, per, sub, target, big, cap, part, starts,
                                            bstart, chunks, biglist);
   k_plan_finish<<<std::max(1, std::min(4 * h->num_sms, (nb + 255) / 256)), 256, 0, st>>>(nb, fine_shift, bstart,
                                                                                         chunks, info);
@@ -1039,12 +1156,23 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
   TRY(grow(h, h->biglist[0], (size_t)nf * 4));
   kbegin(h, SGAGG_K_PLAN);
   TRY(run_plan(h, P<long long>(h->fsizes), nf, 0, P<long long>(h->bstart[0]), P<Chunk>(h->chunks[0]),
-               P<int>(h->biglist[0]), &ds->info));
+               P<int>(h->biglist[0]), &ds->info, kMergeTile, kMergeTile - kMergeTile / 4, kMergeTile / 4));
   kend(h);
   CU(cudaGetLastError());
   TRY(sync_read(h, &hs->info, &ds->info, sizeof(PlanInfo)));
   PlanInfo info = hs->info;
   if (final_merge) h->st.merge_tiles = info.n_chunks;
+  // every tile's slice of every run (the merge kernel reads one row of it)
+  TRY(grow(h, h->tslo, (size_t)(info.n_chunks + 1) * K * 8));
+  if (info.n_chunks > 0) {
+    kbegin(h, SGAGG_K_PLAN);
+    const long long tot = (long long)(info.n_chunks + 1) * K;
+    k_tile_slices<<<(int)std::max(1ll, std::min<long long>((tot + 255) / 256, 8ll * h->num_sms)), 256, 0, stream>>>(
+        P<Chunk>(h->chunks[0]), info.n_chunks, rset.offs, K, P<long long>(h->tslo));
+    kend(h);
+    CU(cudaGetLastError());
+    kbytes(h, SGAGG_K_PLAN, tot * 16);
+  }
   CopySrc copy{};
   if (info.n_big > 0) {
     std::vector<int> big(info.n_big);
@@ -1109,16 +1237,19 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
     copy.keys = co.keys;
     for (int s = 0; s < S; ++s) copy.cols[s] = co.cols[s];
   }
-  RowSrc nosrc{};
-  nosrc.ncols = 0;
+  bool bulk = true;
+  for (const RunRef& r : rr) {
+    bulk = bulk && !r.host && (reinterpret_cast<unsigned long long>(r.keys) & 15ull) == 0;
+    for (int s = 0; s < S; ++s) bulk = bulk && (reinterpret_cast<unsigned long long>(r.cols[s]) & 15ull) == 0;
+  }
   if (final_merge && h->hio && info.n_chunks >= 2) {
     // host buffers: merge in parts; each part's output is copied back while
     // the following parts merge
     const int parts = std::min(kMergeParts, info.n_chunks);
     for (int p = 0; p < parts; ++p) {
       const int c0 = (int)((long long)info.n_chunks * p / parts), c1 = (int)((long long)info.n_chunks * (p + 1) / parts);
-      TRY(launch_sortfold<MODE_RUNS>(h, SGAGG_K_MERGE, P<Chunk>(h->chunks[0]) + c0, c1 - c0, 0, nosrc, rset, copy,
-                                     fid, out, p ? &ds->part_tot[p - 1] : base_in, &ds->part_tot[p]));
+      TRY(launch_merge(h, P<Chunk>(h->chunks[0]) + c0, c1 - c0, P<long long>(h->tslo) + (long long)c0 * K, rset,
+                       bulk, copy, fid, out, p ? &ds->part_tot[p - 1] : base_in, &ds->part_tot[p]));
       CU(cudaMemcpyAsync(&hs->part_end[p], &ds->part_tot[p], 8, cudaMemcpyDeviceToHost, stream));
       if (!h->part_events[p]) CU(cudaEventCreateWithFlags(&h->part_events[p], cudaEventDisableTiming));
       CU(cudaEventRecord(h->part_events[p], stream));
@@ -1133,8 +1264,8 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
     h->hio->copied_out = prev;
     CU(cudaMemcpyAsync(total_out, &ds->part_tot[parts - 1], 8, cudaMemcpyDeviceToDevice, stream));
   } else {
-    TRY(launch_sortfold<MODE_RUNS>(h, SGAGG_K_MERGE, P<Chunk>(h->chunks[0]), info.n_chunks, 0, nosrc, rset, copy,
-                                   fid, out, base_in, total_out));
+    TRY(launch_merge(h, P<Chunk>(h->chunks[0]), info.n_chunks, P<long long>(h->tslo), rset, bulk, copy, fid, out,
+                     base_in, total_out));
   }
   TRY(sync_read(h, &hs->v[0], total_out, 8));
   TRY(check_device_err(h));
@@ -1149,7 +1280,7 @@ sgagg_status merge_runs(sgagg_t h, const std::vector<RunRef>& rr, int S, const F
 // preliminary merges of the smallest runs when they exceed the fan-in
 // (Sec. 4.3).
 sgagg_status merge_all(sgagg_t h, std::vector<RunRef> rr, int S, const FoldDesc& fd, int nf, long long stride,
-                       const Digit& gd, const OutSink& user) {
+                       const Digit& gd, const OutSink& user, const long long* base_in = nullptr) {
   cudaStream_t stream = h->stream;
   Small* ds = dsmall(h);
   HostSmall* hs = hsmall(h);
@@ -1177,8 +1308,8 @@ sgagg_status merge_all(sgagg_t h, std::vector<RunRef> rr, int S, const FoldDesc&
         ++extra;
       }
     }
-    TRY(grow(h, h->marena_keys, (size_t)std::max(1ll, need) * 8));
-    TRY(grow_cols(h, h->marena_cols, S, (size_t)std::max(1ll, need) * 8));
+    TRY(grow(h, h->marena_keys, (size_t)std::max(1ll, need) * 8 + kRunSlack));
+    TRY(grow_cols(h, h->marena_cols, S, (size_t)std::max(1ll, need) * 8 + kRunSlack));
     TRY(grow(h, h->moffs, (size_t)extra * stride * 8));
     long long used = 0;
     int made = 0;
@@ -1206,6 +1337,7 @@ sgagg_status merge_all(sgagg_t h, std::vector<RunRef> rr, int S, const FoldDesc&
       used = end;
       ++made;
       h->st.run_rows += nr.rows;
+      h->run_sizes.push_back(nr.rows);
       h->st.run_bytes_device += nr.rows * row_bytes;
       ++h->st.runs;
       rr.erase(rr.begin(), rr.begin() + g);
@@ -1213,7 +1345,7 @@ sgagg_status merge_all(sgagg_t h, std::vector<RunRef> rr, int S, const FoldDesc&
     }
   }
   long long rows = 0;
-  TRY(merge_runs(h, rr, S, fid, nf, user, nullptr, &ds->total, &rows, true));
+  TRY(merge_runs(h, rr, S, fid, nf, user, base_in, &ds->total, &rows, true));
   h->last_rows = rows;
   h->st.out_rows = rows;
   return SGAGG_OK;
@@ -1257,14 +1389,14 @@ sgagg_status absorb_device(sgagg_t h, const RowSrc& raw, long long n, const Fold
   const long long stride = nf + 1;
   const long long cap3 = M + std::min(Bz, n);
   for (int i = 0; i < 3; ++i) {
-    TRY(grow(h, h->ab_keys[i], (size_t)cap3 * 8));
-    TRY(grow_cols(h, h->ab_cols[i], S1, (size_t)cap3 * 8));
+    TRY(grow(h, h->ab_keys[i], (size_t)cap3 * 8 + kRunSlack));
+    TRY(grow_cols(h, h->ab_cols[i], S1, (size_t)cap3 * 8 + kRunSlack));
     TRY(grow(h, h->ab_offs[i], (size_t)stride * 8));
   }
   TRY(grow(h, h->ab_tmp, (size_t)(1024 + 8) * 8));
   const long long max_runs = n / M + 2;  // every run but the last holds M rows
-  TRY(grow(h, h->arena_keys, (size_t)n * 8));
-  TRY(grow_cols(h, h->arena_cols, S, (size_t)n * 8));
+  TRY(grow(h, h->arena_keys, (size_t)n * 8 + kRunSlack));
+  TRY(grow_cols(h, h->arena_cols, S, (size_t)n * 8 + kRunSlack));
   h->arena_keys.arena = true;
   for (auto& b : h->arena_cols) b.arena = true;
   TRY(grow(h, h->offs, (size_t)max_runs * stride * 8));
@@ -1302,6 +1434,7 @@ sgagg_status absorb_device(sgagg_t h, const RowSrc& raw, long long n, const Fold
     CU(cudaGetLastError());
     runs.push_back(Run{rstart, m, 0});
     h->st.run_rows += m;
+    h->run_sizes.push_back(m);
     h->st.run_bytes_device += m * row_bytes;
     rstart = acur;
     return SGAGG_OK;
@@ -1421,6 +1554,305 @@ sgagg_status absorb_device(sgagg_t h, const RowSrc& raw, long long n, const Fold
   return merge_all(h, rr, S, fd, nf, stride, gd, user);
 }
 
+// One batch whose keys take few values (Example 1, Sec. 3.2): one streaming
+// pass folds every row into accumulators of the sampled distinct keys
+// (kd <= kLowCardKeys, ascending).  *done is false when some row's key is
+// not among them; the caller then groups the input by the general path.
+sgagg_status lowcard_device(sgagg_t h, const RowSrc& raw, long long n, const FoldDesc& fd,
+                            const unsigned long long* keys, int kd, const OutSink& user, bool* done) {
+  *done = false;
+  const int S = fd.n_state;
+  LowCardArgs a{};
+  a.src = raw;
+  a.n = n;
+  a.kd = kd;
+  for (int g = 0; g < kd; ++g) a.keys[g] = keys[g];
+  a.fd = fd;
+  // aggregates by source column: count(*) first, then column 0, 1, ...
+  int q = 0;
+  for (int ag = 0; ag < S; ++ag)
+    if (fd.src[ag] < 0) a.order[q++] = (int8_t)ag;
+  a.col_end[0] = (int8_t)q;
+  for (int c = 0; c < raw.ncols; ++c) {
+    for (int ag = 0; ag < S; ++ag)
+      if (fd.src[ag] == c) a.order[q++] = (int8_t)ag;
+    a.col_end[c + 1] = (int8_t)q;
+  }
+  a.n_col = raw.ncols;
+  const int T = (size_t)kd * S * 8 * 256 <= 110 * 1024 ? 256 : 128;
+  const size_t smem = (size_t)kd * S * 8 * T;
+  const int blocks = h->num_sms * (T == 256 && smem <= 110 * 1024 ? 2 : 1);
+  TRY(grow(h, h->lc_part, (size_t)blocks * kd * std::max(1, S) * 8));
+  a.partial = P<long long>(h->lc_part);
+  Small* ds = dsmall(h);
+  a.overflow = &ds->lc_over;
+  static DeviceOnce once;
+  int dev = 0;
+  if (once.need(&dev)) {
+    CU(cudaFuncSetAttribute(k_lowcard<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024));
+    CU(cudaFuncSetAttribute(k_lowcard<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024));
+    CU(cudaFuncSetAttribute(k_lowcard<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024));
+    CU(cudaFuncSetAttribute(k_lowcard<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024));
+    CU(cudaFuncSetAttribute(k_lowcard<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024));
+    once.done(dev);
+  }
+  CU(cudaMemsetAsync(&ds->lc_over, 0, sizeof(int), h->stream));
+  kbegin(h, SGAGG_K_STREAM);
+  if (S <= 2) k_lowcard<2><<<blocks, T, smem, h->stream>>>(a);
+  else if (S <= 4) k_lowcard<4><<<blocks, T, smem, h->stream>>>(a);
+  else if (S <= 8) k_lowcard<8><<<blocks, T, smem, h->stream>>>(a);
+  else if (S <= 16) k_lowcard<16><<<blocks, T, smem, h->stream>>>(a);
+  else k_lowcard<32><<<blocks, T, smem, h->stream>>>(a);
+  OutSinkLite ol{};
+  ol.kout = user.kout;
+  for (int s = 0; s < S; ++s) ol.cols[s] = user.cols[s];
+  ol.capacity = user.capacity;
+  k_lowcard_finish<<<1, 256, 0, h->stream>>>(a, blocks, ol, &ds->total);
+  kend(h);
+  ++h->st.class_launches[SGAGG_K_STREAM];
+  ++h->st.kernel_launches;
+  CU(cudaGetLastError());
+  HostSmall* hs = hsmall(h);
+  TRY(sync_read(h, hs->v, &ds->total, 8));
+  int over = 0;
+  TRY(sync_read(h, &over, &ds->lc_over, sizeof(int)));
+  long long rb = 0;
+  for (int c = 0; c < raw.key.n_cols; ++c) rb += raw.key.bytes[c];
+  kbytes(h, SGAGG_K_STREAM, n * (rb + 8ll * raw.ncols));
+  if (over) return SGAGG_OK;  // not done: the general path takes the input
+  if (kd > user.capacity) return fail(h, SGAGG_ECAPACITY, "out_capacity is smaller than the number of distinct keys");
+  kbytes(h, SGAGG_K_STREAM, kd * (h->key_bytes + 8ll * S));
+  h->last_rows = kd;
+  h->st.out_rows = kd;
+  *done = true;
+  return SGAGG_OK;
+}
+
+// Run generation in read-sort-write cycles of M rows of src (one run per
+// batch, Sec. 3 and Sec. 6.1), then one wide merge of all runs into the
+// caller's output at *base_in (Sec. 4; nullptr: 0).  stage_io: src is the
+// host-buffer call's staged input, copied batch by batch.
+sgagg_status batch_runs(sgagg_t h, const RowSrc& src, long long n, long long M, const FoldDesc& fd, int S,
+                        const OutSink& user, const Digit& gd, const long long* base_in, bool stage_io) {
+  cudaStream_t stream = h->stream;
+  const long long B = (n + M - 1) / M;
+  const int nf = 1 << gd.fbits;
+  const long long stride = nf + 1;
+  const long long row_bytes = 8ll * (1 + S);
+  long long dev_rows_cap = n;
+  if (h->arena_cap >= 0) dev_rows_cap = std::min<long long>(n, h->arena_cap / row_bytes);
+  TRY(grow(h, h->arena_keys, (size_t)std::max(1ll, dev_rows_cap) * 8 + kRunSlack));
+  TRY(grow_cols(h, h->arena_cols, S, (size_t)std::max(1ll, dev_rows_cap) * 8 + kRunSlack));
+  h->arena_keys.arena = true;
+  for (auto& b : h->arena_cols) b.arena = true;
+  TRY(grow(h, h->offs, (size_t)B * stride * 8));
+  TRY(grow(h, h->runstarts, (size_t)(2 * (B + 1)) * 8));
+  long long* rs_dev = P<long long>(h->runstarts);          // device arena cursor per batch
+  long long* rs_host = rs_dev + (B + 1);                   // host arena cursor per batch
+  CU(cudaMemsetAsync(rs_dev, 0, (size_t)(2 * (B + 1)) * 8, stream));
+  bool any_host = false;
+  std::vector<int> run_host(B, 0);
+  {
+    long long ub = 0;  // upper bound of device rows so far
+    for (long long b = 0; b < B; ++b) {
+      long long m = std::min(M, n - b * M);
+      if (ub + m > dev_rows_cap) { run_host[b] = 1; any_host = true; }
+      else ub += m;
+    }
+  }
+  if (any_host) TRY(alloc_host_arena(h, (size_t)n, S));
+
+  long long dev_cursor_idx = 0, host_cursor_idx = 0;
+  // run b reads its base from the previous run of the same arena
+  std::vector<long long*> base_ptr(B), end_ptr(B);
+  {
+    long long* last_dev = rs_dev;      // rs_dev[0] = 0
+    long long* last_host = rs_host;    // rs_host[0] = 0
+    for (long long b = 0; b < B; ++b) {
+      if (run_host[b]) {
+        base_ptr[b] = last_host;
+        end_ptr[b] = rs_host + 1 + (++host_cursor_idx) - 1;
+        last_host = end_ptr[b];
+      } else {
+        base_ptr[b] = last_dev;
+        end_ptr[b] = rs_dev + 1 + (++dev_cursor_idx) - 1;
+        last_dev = end_ptr[b];
+      }
+    }
+  }
+  if (stage_io) TRY(stage_rows(h, 0, std::min<long long>(M, n), 0));
+  for (long long b = 0; b < B; ++b) {
+    long long m = std::min(M, n - b * M);
+    if (stage_io) {  // copy batch b + 1 while batch b is grouped
+      if (b + 1 < B) TRY(stage_rows(h, (b + 1) * M, std::min<long long>(n, (b + 2) * M), (size_t)b + 1));
+      TRY(wait_rows(h, (size_t)b));
+    }
+    RowSrc bs = src;
+    // shift the source to the batch: offset applies to every column
+    bs.offset = src.offset + b * M;
+    OutSink o{};
+    o.user = 0;
+    if (run_host[b]) {
+      o.keys = host_dev_ptr<unsigned long long>(h, h->harena_keys);
+      for (int s = 0; s < S; ++s) o.cols[s] = host_dev_ptr<long long>(h, h->harena_cols[s]);
+      o.capacity = (long long)h->harena_rows;
+    } else {
+      o.keys = P<unsigned long long>(h->arena_keys);
+      for (int s = 0; s < S; ++s) o.cols[s] = P<long long>(h->arena_cols[s]);
+      o.capacity = dev_rows_cap;
+    }
+    o.offs = P<long long>(h->offs) + b * stride;
+    o.dig = gd;
+    TRY(solve(h, bs, m, fd, o, base_ptr[b], end_ptr[b], &gd, 0));
+  }
+  TRY(check_device_err(h));
+
+  // run bookkeeping (the paper's spill volume)
+  std::vector<long long> rsd(2 * (B + 1));
+  TRY(sync_read(h, rsd.data(), rs_dev, rsd.size() * 8));
+  std::vector<Run> runs(B);
+  {
+    long long di = 0, hi = 0;
+    for (long long b = 0; b < B; ++b) {
+      if (run_host[b]) {
+        runs[b] = Run{rsd[(B + 1) + hi], rsd[(B + 1) + hi + 1] - rsd[(B + 1) + hi], 1};
+        ++hi;
+      } else {
+        runs[b] = Run{rsd[di], rsd[di + 1] - rsd[di], 0};
+        ++di;
+      }
+      h->st.run_rows += runs[b].rows;
+      h->run_sizes.push_back(runs[b].rows);
+      kbytes(h, SGAGG_K_RUNGEN, runs[b].rows * row_bytes);
+      if (runs[b].host) h->st.run_bytes_host += runs[b].rows * row_bytes;
+      else h->st.run_bytes_device += runs[b].rows * row_bytes;
+    }
+  }
+  h->st.runs = B;
+
+  // ---- wide merge ----
+  std::vector<RunRef> rr(B);
+  for (long long b2 = 0; b2 < B; ++b2) {
+    RunRef& r = rr[b2];
+    r.host = runs[b2].host;
+    if (runs[b2].host) {
+      r.keys = host_dev_ptr<long long>(h, h->harena_keys);
+      for (int s = 0; s < S; ++s) r.cols[s] = host_dev_ptr<long long>(h, h->harena_cols[s]);
+    } else {
+      r.keys = P<long long>(h->arena_keys);
+      for (int s = 0; s < S; ++s) r.cols[s] = P<long long>(h->arena_cols[s]);
+    }
+    r.offs = P<long long>(h->offs) + b2 * stride;
+    r.rows = runs[b2].rows;
+  }
+  return merge_all(h, rr, S, fd, nf, stride, gd, user, base_in);
+}
+
+// Hybrid run generation (SGAGG_OPT_POLICY 2, Sec. 5.2.3): memory fraction
+// 1 - f/F is an in-memory index for the lowest keys, which absorbs their rows
+// without spilling; fraction f/F runs read-sort-write cycles of f/F * M rows
+// over the other rows, and one wide merge folds those runs.  F is
+// SGAGG_OPT_HYBRID_FANIN; f is SGAGG_OPT_HYBRID_F, or, as the paper sizes the
+// fan-out of hybrid hashing, f = ceil((O - M) / (M - 1)) (page of one row)
+// from the output size O estimated on the key sample, at most F.  The index
+// holds the (1 - f/F) * M lowest distinct keys: the resident range ends at
+// the key given by SGAGG_OPT_HYBRID_LAST, or else at the sampled distinct
+// key whose estimated rank among all distinct keys is that count.  The
+// resident groups lead the output (their keys are the lowest); the merged
+// runs follow them.
+sgagg_status hybrid_device(sgagg_t h, const RowSrc& raw, long long n, const FoldDesc& fd, int S, const OutSink& user,
+                           const Digit& gd, double O_est, const unsigned long long* sdist_keys, long long sdist) {
+  cudaStream_t stream = h->stream;
+  Small* ds = dsmall(h);
+  HostSmall* hs = hsmall(h);
+  const long long M = h->M;
+  const int F = std::max(1, h->hybrid_fanin);
+  int f = h->hybrid_f;
+  if (f < 0) f = O_est <= (double)M ? 0 : (int)std::min<double>(F, std::ceil((O_est - M) / std::max(1.0, M - 1.0)));
+  f = std::min(std::max(f, 0), F);
+  const long long R = f < F ? (long long)((1.0 - (double)f / F) * M) : 0;
+  const long long m_run = f > 0 ? std::max(1ll, (long long)((double)f / F * M)) : std::max(1ll, n);
+  bool has_last = false;
+  unsigned long long last = 0;
+  if (R > 0) {
+    if (h->hybrid_last_given) {
+      has_last = true;
+      last = h->hybrid_last;
+    } else {
+      const double q = O_est > 0 ? (double)R / O_est : 1.0;
+      if (q >= 1.0) {
+        has_last = true;
+        last = ~0ull;
+      } else {
+        const long long i = (long long)(q * (double)sdist) - 1;
+        if (i >= 0) {
+          has_last = true;
+          last = sdist_keys[std::min(i, sdist - 1)];
+        }
+      }
+    }
+  }
+  h->st.hybrid_f = f;
+  // split the rows by the resident range, each side in input order
+  const int C = raw.ncols;
+  SplitOut so{};
+  for (int side = 0; side < 2; ++side) {
+    TRY(grow(h, h->hsplit_keys[side], (size_t)n * 8));
+    TRY(grow_cols(h, h->hsplit_cols[side], C, (size_t)n * 8));
+    so.keys[side] = P<unsigned long long>(h->hsplit_keys[side]);
+    for (int c = 0; c < C; ++c) so.cols[side][c] = P<long long>(h->hsplit_cols[side][c]);
+  }
+  const int tiles = (int)((n + kSplitTile - 1) / kSplitTile);
+  TRY(grow(h, h->status, (size_t)(tiles + 2) * 8));
+  CU(cudaMemsetAsync(h->status.p, 0, (size_t)(tiles + 2) * 8, stream));
+  LookBack lb{};
+  lb.ticket = reinterpret_cast<unsigned int*>(P<unsigned long long>(h->status));
+  lb.status = P<unsigned long long>(h->status) + 2;
+  lb.base_in = nullptr;
+  lb.total_out = &ds->hy_rows;
+  lb.err = &ds->err;
+  lb.spin_limit = h->spin_limit;
+  lb.n_chunks = tiles;
+  kbegin(h, SGAGG_K_SCATTER);
+  k_split_range<<<tiles, kSplitThreads, 0, stream>>>(raw, n, last, has_last ? 1 : 0, so, lb);
+  kend(h);
+  CU(cudaGetLastError());
+  kbytes(h, SGAGG_K_SCATTER, n * (src_row_bytes(raw) + 8ll * (1 + C)));
+  TRY(sync_read(h, &hs->v[0], &ds->hy_rows, 8));
+  TRY(check_device_err(h));
+  const long long Rn = hs->v[0], Sn = n - Rn;
+  RowSrc part[2];
+  for (int side = 0; side < 2; ++side) {
+    part[side] = RowSrc{};
+    part[side].kind = SRC_SOA;
+    part[side].ncols = C;
+    part[side].keys = so.keys[side];
+    for (int c = 0; c < C; ++c) part[side].cols[c] = so.cols[side][c];
+  }
+  // the index: the resident rows grouped in memory, written first
+  long long Rk = 0;
+  if (Rn > 0) {
+    TRY(solve(h, part[0], Rn, fd, user, nullptr, &ds->hy_keys, nullptr, 0));
+    TRY(sync_read(h, &hs->v[0], &ds->hy_keys, 8));
+    TRY(check_device_err(h));
+    Rk = hs->v[0];
+  } else {
+    CU(cudaMemsetAsync(&ds->hy_keys, 0, 8, stream));
+  }
+  h->st.resident_rows = Rn;
+  h->st.resident_keys = Rk;
+  h->st.batches = Sn > 0 ? (Sn + m_run - 1) / m_run : 0;
+  if (Sn == 0) {
+    h->last_rows = Rk;
+    h->st.out_rows = Rk;
+    return SGAGG_OK;
+  }
+  // the other rows: runs of f/F * M rows, one wide merge after the index's groups
+  TRY(batch_runs(h, part[1], Sn, m_run, fd, S, user, gd, &ds->hy_keys, false));
+  h->st.batches = (Sn + m_run - 1) / m_run;
+  return SGAGG_OK;
+}
+
 // The whole operation on device-resident inputs.
 sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* const* payload_cols,
                               int32_t n_payload, int64_t n, const sgagg_spec* spec, void* const* out_keys,
@@ -1429,6 +1861,7 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
   h->stream = stream;
   h->have_call = true;
   h->st = sgagg_stats_t{};
+  h->run_sizes.clear();
   h->scratch_bytes = 0;
   h->last_rows = 0;
   h->st.n_rows = n;
@@ -1510,7 +1943,7 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
   if (mb > kTileCap) Db = std::min(kMaxCoarseBits, std::max(1, ilog2_ceil((mb + kBucketRows - 1) / kBucketRows)));
   if (h->radix_bits > 0 && mb > kTileCap) Db = std::min(kMaxCoarseBits, h->radix_bits);
   int Fb = Db;
-  if (B > 1) Fb = std::max(Db, std::min(22, ilog2_ceil((n + kBucketRows - 1) / kBucketRows)));
+  if (B > 1) Fb = std::max(Db, std::min(22, ilog2_ceil((n + kMergeFineRows - 1) / kMergeFineRows)));
   int L = bitlen(smax - smin);
   Digit gd{};
   gd.base = smin;
@@ -1518,7 +1951,7 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
   gd.fshift = L - gd.fbits;
   gd.ebits = std::max(0, gd.fbits - Db);
 
-  if (h->hio && (h->policy == 1 || B == 1)) {  // host buffers: the whole input first
+  if (h->hio && (h->policy != 0 || B == 1)) {  // host buffers: the whole input first
     TRY(stage_rows(h, 0, n, 0));
     TRY(wait_rows(h, 0));
   }
@@ -1526,13 +1959,29 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
     // absorbing index: the digit's fine buckets index the index, the
     // batches and the runs (sized by n, as for several batches)
     Digit ad = gd;
-    const int afb = std::max(Db, std::min(22, ilog2_ceil((n + kBucketRows - 1) / kBucketRows)));
+    const int afb = std::max(Db, std::min(22, ilog2_ceil((n + kMergeFineRows - 1) / kMergeFineRows)));
     ad.fbits = std::min(afb, L);
     ad.fshift = L - ad.fbits;
     ad.ebits = std::max(0, ad.fbits - Db);
     return absorb_device(h, raw, n, fd, S, user, ad);
   }
+  if (h->policy == 2) {
+    Digit hd = gd;  // runs of the spilled rows: fine buckets sized by n
+    const int hfb = std::max(Db, std::min(22, ilog2_ceil((n + kMergeFineRows - 1) / kMergeFineRows)));
+    hd.fbits = std::min(hfb, L);
+    hd.fshift = L - hd.fbits;
+    hd.ebits = std::max(0, hd.fbits - Db);
+    const double O_est = std::min<double>((double)n, estimate_domain((double)scount, (double)sdist));
+    return hybrid_device(h, raw, n, fd, S, user, hd, O_est, hs->sample, sdist);
+  }
 
+  if (B == 1 && sdist <= kLowCardKeys && n >= kLowCardMinRows && h->lowcard != 0 &&
+      sdist * std::max(1, S) <= kLowCardMaxSlots && raw.ncols <= kMaxCols) {
+    bool done = false;
+    TRY(lowcard_device(h, raw, n, fd, hs->sample, (int)sdist, user, &done));
+    if (done) return SGAGG_OK;
+    ++h->st.split_segments;  // the sample missed a key: the general path regroups the input
+  }
   if (B == 1) {
     long long* tot = &ds->total;
     TRY(solve(h, raw, n, fd, user, nullptr, tot, &gd, 0));
@@ -1544,116 +1993,7 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
     return SGAGG_OK;
   }
 
-  // ---- run generation: one run per batch ----
-  const int nf = 1 << gd.fbits;
-  const long long stride = nf + 1;
-  const long long row_bytes = 8ll * (1 + S);
-  long long dev_rows_cap = n;
-  if (h->arena_cap >= 0) dev_rows_cap = std::min<long long>(n, h->arena_cap / row_bytes);
-  TRY(grow(h, h->arena_keys, (size_t)std::max(1ll, dev_rows_cap) * 8));
-  TRY(grow_cols(h, h->arena_cols, S, (size_t)std::max(1ll, dev_rows_cap) * 8));
-  h->arena_keys.arena = true;
-  for (auto& b : h->arena_cols) b.arena = true;
-  TRY(grow(h, h->offs, (size_t)B * stride * 8));
-  TRY(grow(h, h->runstarts, (size_t)(2 * (B + 1)) * 8));
-  long long* rs_dev = P<long long>(h->runstarts);          // device arena cursor per batch
-  long long* rs_host = rs_dev + (B + 1);                   // host arena cursor per batch
-  CU(cudaMemsetAsync(rs_dev, 0, (size_t)(2 * (B + 1)) * 8, stream));
-  bool any_host = false;
-  std::vector<int> run_host(B, 0);
-  {
-    long long ub = 0;  // upper bound of device rows so far
-    for (long long b = 0; b < B; ++b) {
-      long long m = std::min(M, n - b * M);
-      if (ub + m > dev_rows_cap) { run_host[b] = 1; any_host = true; }
-      else ub += m;
-    }
-  }
-  if (any_host) TRY(alloc_host_arena(h, (size_t)n, S));
-
-  long long dev_cursor_idx = 0, host_cursor_idx = 0;
-  // run b reads its base from the previous run of the same arena
-  std::vector<long long*> base_ptr(B), end_ptr(B);
-  {
-    long long* last_dev = rs_dev;      // rs_dev[0] = 0
-    long long* last_host = rs_host;    // rs_host[0] = 0
-    for (long long b = 0; b < B; ++b) {
-      if (run_host[b]) {
-        base_ptr[b] = last_host;
-        end_ptr[b] = rs_host + 1 + (++host_cursor_idx) - 1;
-        last_host = end_ptr[b];
-      } else {
-        base_ptr[b] = last_dev;
-        end_ptr[b] = rs_dev + 1 + (++dev_cursor_idx) - 1;
-        last_dev = end_ptr[b];
-      }
-    }
-  }
-  if (h->hio) TRY(stage_rows(h, 0, std::min<long long>(M, n), 0));
-  for (long long b = 0; b < B; ++b) {
-    long long m = std::min(M, n - b * M);
-    if (h->hio) {  // copy batch b + 1 while batch b is grouped
-      if (b + 1 < B) TRY(stage_rows(h, (b + 1) * M, std::min<long long>(n, (b + 2) * M), (size_t)b + 1));
-      TRY(wait_rows(h, (size_t)b));
-    }
-    RowSrc bs = raw;
-    bs.key = raw.key;
-    // shift the raw source to the batch: offset applies to every column
-    bs.offset = b * M;
-    OutSink o{};
-    o.user = 0;
-    if (run_host[b]) {
-      o.keys = host_dev_ptr<unsigned long long>(h, h->harena_keys);
-      for (int s = 0; s < S; ++s) o.cols[s] = host_dev_ptr<long long>(h, h->harena_cols[s]);
-      o.capacity = (long long)h->harena_rows;
-    } else {
-      o.keys = P<unsigned long long>(h->arena_keys);
-      for (int s = 0; s < S; ++s) o.cols[s] = P<long long>(h->arena_cols[s]);
-      o.capacity = dev_rows_cap;
-    }
-    o.offs = P<long long>(h->offs) + b * stride;
-    o.dig = gd;
-    TRY(solve(h, bs, m, fd, o, base_ptr[b], end_ptr[b], &gd, 0));
-  }
-  TRY(check_device_err(h));
-
-  // run bookkeeping (the paper's spill volume)
-  std::vector<long long> rsd(2 * (B + 1));
-  TRY(sync_read(h, rsd.data(), rs_dev, rsd.size() * 8));
-  std::vector<Run> runs(B);
-  {
-    long long di = 0, hi = 0;
-    for (long long b = 0; b < B; ++b) {
-      if (run_host[b]) {
-        runs[b] = Run{rsd[(B + 1) + hi], rsd[(B + 1) + hi + 1] - rsd[(B + 1) + hi], 1};
-        ++hi;
-      } else {
-        runs[b] = Run{rsd[di], rsd[di + 1] - rsd[di], 0};
-        ++di;
-      }
-      h->st.run_rows += runs[b].rows;
-      kbytes(h, SGAGG_K_RUNGEN, runs[b].rows * row_bytes);
-      if (runs[b].host) h->st.run_bytes_host += runs[b].rows * row_bytes;
-      else h->st.run_bytes_device += runs[b].rows * row_bytes;
-    }
-  }
-  h->st.runs = B;
-
-  // ---- wide merge ----
-  std::vector<RunRef> rr(B);
-  for (long long b2 = 0; b2 < B; ++b2) {
-    RunRef& r = rr[b2];
-    if (runs[b2].host) {
-      r.keys = host_dev_ptr<long long>(h, h->harena_keys);
-      for (int s = 0; s < S; ++s) r.cols[s] = host_dev_ptr<long long>(h, h->harena_cols[s]);
-    } else {
-      r.keys = P<long long>(h->arena_keys);
-      for (int s = 0; s < S; ++s) r.cols[s] = P<long long>(h->arena_cols[s]);
-    }
-    r.offs = P<long long>(h->offs) + b2 * stride;
-    r.rows = runs[b2].rows;
-  }
-  return merge_all(h, rr, S, fd, nf, stride, gd, user);
+  return batch_runs(h, raw, n, M, fd, S, user, gd, nullptr, h->hio != nullptr);
 }
 
 }  // namespace
@@ -1720,6 +2060,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
   h->stream = stream;
   h->have_call = true;
   h->st = sgagg_stats_t{};
+  h->run_sizes.clear();
   h->st.n_rows = total;
   ++h->gen;
   h->touched.clear();
@@ -1842,7 +2183,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
       acc.out_rows += c.out_rows; acc.prefold_passes += c.prefold_passes;
       acc.split_segments += c.split_segments; acc.merge_tiles += c.merge_tiles;
       acc.kernel_launches += c.kernel_launches;
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < kClasses; ++k) {
         acc.class_launches[k] += c.class_launches[k];
         acc.class_bytes[k] += c.class_bytes[k];
         acc.class_ms[k] += c.class_ms[k];
@@ -2023,7 +2364,7 @@ namespace {
 constexpr int kNaTicket = 0, kNaStatus = 8, kNaErr = 16, kNaTotal = 24, kNaZeroBytes = 24;
 
 constexpr int kNaMaxDevices = 64;
-unsigned char* g_na_ptr[kNaMaxDevices];   // device address of the array, per device
+std::atomic<unsigned char*> g_na_ptr[kNaMaxDevices];   // device address of the array, per device
 thread_local char g_na_msg[256];
 
 __global__ void k_noalloc_finish(const int* err, const long long* total, long long* out_rows) {
@@ -2051,13 +2392,30 @@ extern "C" sgagg_status sgagg_aggregate_noalloc(const sgagg_keys* keys, const in
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
     return na_fail(SGAGG_ECUDA, "sgagg_aggregate_noalloc: no usable current device");
-  if (!g_na_ptr[dev]) {
+  if (!g_na_ptr[dev].load(std::memory_order_acquire)) {
+    // set-up, once per device: the array's device address, and every kernel
+    // this entry point launches loaded now (with lazy module loading a
+    // kernel's first launch may load its module, which allocates), with its
+    // shared-memory limit set
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return na_fail(SGAGG_ECUDA, cudaGetErrorString(e));
-    g_na_ptr[dev] = reinterpret_cast<unsigned char*>(p);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_noalloc_finish);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_sortfold<MODE_TILES, 2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_sortfold<MODE_TILES, 4>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_sortfold<MODE_TILES, 8>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_sortfold<MODE_TILES, 16>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_sortfold<MODE_TILES, 32>);
+    if (e != cudaSuccess) return na_fail(SGAGG_ECUDA, cudaGetErrorString(e));
+    set_smem_attr<MODE_TILES, 2>();
+    set_smem_attr<MODE_TILES, 4>();
+    set_smem_attr<MODE_TILES, 8>();
+    set_smem_attr<MODE_TILES, 16>();
+    set_smem_attr<MODE_TILES, 32>();
+    g_na_ptr[dev].store(reinterpret_cast<unsigned char*>(p), std::memory_order_release);
   }
-  unsigned char* base = g_na_ptr[dev];
+  unsigned char* base = g_na_ptr[dev].load(std::memory_order_acquire);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // ticket, status word and error word must start at zero; the count is written
   if (cudaMemsetAsync(base, 0, kNaZeroBytes, st) != cudaSuccess)
@@ -2165,14 +2523,36 @@ sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
       h->alloc_count = 0;
       return SGAGG_OK;
     case SGAGG_OPT_TIMING: h->timing = (int)value; return SGAGG_OK;
-    case SGAGG_OPT_TEST_STALL: h->test_stall = value ? 1 : 0; return SGAGG_OK;
+    case SGAGG_OPT_TEST_STALL: h->test_stall = value == 2 ? 2 : (value ? 1 : 0); return SGAGG_OK;
     case SGAGG_OPT_POLICY:
-      if (value != 0 && value != 1) return fail(h, SGAGG_EINVAL, "policy must be 0 or 1");
+      if (value < 0 || value > 2) return fail(h, SGAGG_EINVAL, "policy must be 0, 1 or 2");
       h->policy = (int)value;
       return SGAGG_OK;
     case SGAGG_OPT_ABSORB_BATCH:
       if (value < 0) return fail(h, SGAGG_EINVAL, "absorbing batch must be >= 0");
       h->absorb_batch = value;
+      return SGAGG_OK;
+    case SGAGG_OPT_LOWCARD:
+      h->lowcard = value == 0 ? 0 : -1;
+      return SGAGG_OK;
+    case SGAGG_OPT_HYBRID_FANIN:
+      if (value < 1) return fail(h, SGAGG_EINVAL, "hybrid fan-in must be >= 1");
+      h->hybrid_fanin = (int)std::min<int64_t>(value, 1 << 20);
+      return SGAGG_OK;
+    case SGAGG_OPT_HYBRID_F:
+      h->hybrid_f = value < 0 ? -1 : (int)std::min<int64_t>(value, 1 << 20);
+      return SGAGG_OK;
+    case SGAGG_OPT_HYBRID_LAST:
+      h->hybrid_last_given = true;
+      h->hybrid_last = (unsigned long long)value;
+      return SGAGG_OK;
+    case SGAGG_OPT_HYBRID_LAST_AUTO:
+      h->hybrid_last_given = false;
+      return SGAGG_OK;
+    case SGAGG_OPT_MERGE_THREADS:
+      if (value != 0 && value != 128 && value != 256 && value != 512)
+        return fail(h, SGAGG_EINVAL, "merge threads must be 0, 128, 256 or 512");
+      h->merge_threads = (int)value;
       return SGAGG_OK;
     default: return fail(h, SGAGG_EINVAL, "unknown option");
   }
@@ -2406,6 +2786,14 @@ sgagg_status sgagg_stats(sgagg_t h, sgagg_stats_t* out) {
   return SGAGG_OK;
 }
 
+sgagg_status sgagg_run_sizes(sgagg_t h, int64_t* rows, int64_t max_runs, int64_t* count) {
+  if (!h || !count || max_runs < 0 || (max_runs > 0 && !rows)) return SGAGG_EINVAL;
+  if (h->have_call) cudaStreamSynchronize(h->stream);
+  *count = (int64_t)h->run_sizes.size();
+  for (int64_t i = 0; i < max_runs && i < *count; ++i) rows[i] = h->run_sizes[(size_t)i];
+  return SGAGG_OK;
+}
+
 sgagg_status sgagg_aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t count, const sgagg_spec* spec,
                                      void* stream) {
   if (!h) return SGAGG_EINVAL;
@@ -2434,7 +2822,8 @@ void sgagg_destroy(sgagg_t h) {
     free_buf(h->ab_keys[i]); free_buf(h->ab_offs[i]); fv(h->ab_cols[i]);
   }
   free_buf(h->ab_tmp);
-  free_buf(h->dk_keys); free_buf(h->rg_heads); fv(h->dk_cols); free_buf(h->plan_tmp);
+  free_buf(h->dk_keys); free_buf(h->rg_heads); fv(h->dk_cols); free_buf(h->plan_tmp); free_buf(h->lc_part); free_buf(h->tslo);
+  for (int i = 0; i < 2; ++i) { free_buf(h->hsplit_keys[i]); fv(h->hsplit_cols[i]); }
   free_buf(h->binst); free_buf(h->bchunks); free_buf(h->bkeys); free_buf(h->bout_keys);
   free_buf(h->bseg); free_buf(h->brange); free_buf(h->bstartb); free_buf(h->bdirect);
   fv(h->bcols); fv(h->bout_cols);

@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "SGAGG_OK", 1: "SGAGG_EINVAL", 2: "SGAGG_ENOMEM", 3: "SGAGG_E
 SGAGG_COUNT, SGAGG_SUM, SGAGG_MIN, SGAGG_MAX = range(4)
 (SGAGG_OPT_PREFOLD, SGAGG_OPT_ARENA_CAP, SGAGG_OPT_RADIX_BITS, SGAGG_OPT_SPIN_LIMIT,
  SGAGG_OPT_FANIN_CAP, SGAGG_OPT_FAULT_ALLOC, SGAGG_OPT_TIMING, SGAGG_OPT_TEST_STALL,
- SGAGG_OPT_POLICY, SGAGG_OPT_ABSORB_BATCH) = range(10)
+ SGAGG_OPT_POLICY, SGAGG_OPT_ABSORB_BATCH, SGAGG_OPT_LOWCARD, SGAGG_OPT_MERGE_THREADS,
+ SGAGG_OPT_HYBRID_FANIN, SGAGG_OPT_HYBRID_F, SGAGG_OPT_HYBRID_LAST, SGAGG_OPT_HYBRID_LAST_AUTO) = range(16)
 
 
 class sgagg_agg(ctypes.Structure):
@@ -36,7 +37,7 @@ class sgagg_keys(ctypes.Structure):
                 ("cols", ctypes.POINTER(ctypes.c_void_p))]
 
 
-KERNEL_CLASSES = ("probe", "hist", "plan", "scatter", "prefold", "rungen", "merge", "other")
+KERNEL_CLASSES = ("probe", "hist", "plan", "scatter", "prefold", "rungen", "merge", "other", "stream")
 
 
 class sgagg_stats_t(ctypes.Structure):
@@ -44,14 +45,15 @@ class sgagg_stats_t(ctypes.Structure):
         "n_rows", "batches", "runs", "run_rows", "run_bytes_device", "run_bytes_host",
         "peak_scratch_bytes", "out_rows", "out_bytes", "prefold_passes", "split_segments",
         "merge_tiles", "kernel_launches")] + [
-        ("class_launches", ctypes.c_int64 * 8), ("class_bytes", ctypes.c_int64 * 8),
-        ("class_ms", ctypes.c_double * 8)]
+        ("class_launches", ctypes.c_int64 * 9), ("class_bytes", ctypes.c_int64 * 9),
+        ("class_ms", ctypes.c_double * 9), ("resident_rows", ctypes.c_int64), ("resident_keys", ctypes.c_int64),
+        ("hybrid_f", ctypes.c_int64)]
 
     def as_dict(self):
         d = {n: int(getattr(self, n)) for n, t in self._fields_ if t is ctypes.c_int64}
         d["kernels"] = {KERNEL_CLASSES[i]: dict(launches=int(self.class_launches[i]),
                                                 bytes=int(self.class_bytes[i]),
-                                                ms=float(self.class_ms[i])) for i in range(8)}
+                                                ms=float(self.class_ms[i])) for i in range(9)}
         return d
 
 
@@ -111,6 +113,8 @@ def lib():
         L.sgagg_aggregate_noalloc.argtypes = [ctypes.POINTER(sgagg_keys), vp, i32, i64,
                                               ctypes.POINTER(sgagg_spec), vp, vp, i64, vp, vp]
         L.sgagg_aggregate_noalloc.restype = i32
+        L.sgagg_run_sizes.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+        L.sgagg_run_sizes.restype = i32
         L.sgagg_destroy.argtypes = [vp]
         L.sgagg_destroy.restype = None
         L.sgagg_last_error.argtypes = [vp]
@@ -190,6 +194,15 @@ def sgagg_stats(h):
     s = sgagg_stats_t()
     _check(h, lib().sgagg_stats(h, ctypes.byref(s)))
     return s.as_dict()
+
+
+def sgagg_run_sizes(h):
+    """Rows of each run the last call wrote, in the order written."""
+    cnt = ctypes.c_int64()
+    _check(h, lib().sgagg_run_sizes(h, None, 0, ctypes.byref(cnt)))
+    buf = (ctypes.c_int64 * max(1, cnt.value))()
+    _check(h, lib().sgagg_run_sizes(h, buf, cnt.value, ctypes.byref(cnt)))
+    return [int(buf[i]) for i in range(cnt.value)]
 
 
 class _Args:
@@ -275,9 +288,12 @@ class Aggregator:
                  "radix_bits": SGAGG_OPT_RADIX_BITS, "spin_limit": SGAGG_OPT_SPIN_LIMIT,
                  "fanin_cap": SGAGG_OPT_FANIN_CAP, "fault_alloc": SGAGG_OPT_FAULT_ALLOC,
                  "timing": SGAGG_OPT_TIMING, "test_stall": SGAGG_OPT_TEST_STALL,
-                 "policy": SGAGG_OPT_POLICY, "absorb_batch": SGAGG_OPT_ABSORB_BATCH}
+                 "policy": SGAGG_OPT_POLICY, "absorb_batch": SGAGG_OPT_ABSORB_BATCH,
+                 "lowcard": SGAGG_OPT_LOWCARD, "merge_threads": SGAGG_OPT_MERGE_THREADS,
+                 "hybrid_fanin": SGAGG_OPT_HYBRID_FANIN, "hybrid_f": SGAGG_OPT_HYBRID_F,
+                 "hybrid_last": SGAGG_OPT_HYBRID_LAST}
         for k, v in options.items():
-            sgagg_set_option(self.h, names[k], v)
+            self.set_option(names[k], v)
 
     def close(self):
         if self.h is not None:
@@ -291,6 +307,8 @@ class Aggregator:
             pass
 
     def set_option(self, key, value):
+        if key == SGAGG_OPT_HYBRID_LAST and value >= 1 << 63:
+            value -= 1 << 64  # the key's 64 bits through the int64 argument
         sgagg_set_option(self.h, key, value)
 
     def aggregate(self, key_cols, payload, aggs, capacity=None, out=None, stream=None, sync=True):
@@ -352,6 +370,9 @@ class Aggregator:
 
     def stats(self):
         return sgagg_stats(self.h)
+
+    def run_sizes(self):
+        return sgagg_run_sizes(self.h)
 
     def temp_bytes(self):
         return sgagg_temp_bytes(self.h)

@@ -42,6 +42,46 @@ def test_device_wait_times_out_and_handle_recovers():
     torch.cuda.synchronize()  # the context is still usable
 
 
+def test_merge_wait_times_out_and_handle_recovers():
+    """The stall hits the wide merge (16 runs): its first tile never
+    publishes, the others' bounded look-back waits run out."""
+    c, ref = case(M=1 << 14)
+    agg = sgagg.Aggregator(1 << 14, spin_limit=1 << 12, test_stall=2)
+    try:
+        with pytest.raises(sgagg.SgaggError) as e:
+            agg.aggregate(c["key_cols"], c["payload"], c["aggs"])
+        assert e.value.status == sgagg.SGAGG_ETIMEOUT
+        assert agg.stats()["runs"] > 1  # run generation finished; the merge timed out
+        same(agg.aggregate(c["key_cols"], c["payload"], c["aggs"]), ref)
+    finally:
+        agg.close()
+    torch.cuda.synchronize()
+
+
+def test_batched_wait_times_out_and_handle_recovers():
+    """The stall hits the first sort+fold launch inside a batched call."""
+    insts, refs = [], []
+    for i, (n, D) in enumerate([(50_000, 3000), (120_000, 40_000), (9_000, 50)]):
+        c = datagen.config4_instance(dict(rows=n, D=D, seed=70 + i))
+        insts.append((c["key_cols"][0], [c["payload"][0]]))
+        refs.append(oracle.aggregate([c["key_cols"][0].numpy()], [c["payload"][0].numpy()], c["aggs"]))
+    aggs = datagen.config4_instance(dict(rows=10, D=2, seed=1))["aggs"]
+    dev = [(k.to(DEV), [p.to(DEV) for p in pay]) for k, pay in insts]
+    agg = sgagg.Aggregator(1 << 20, spin_limit=1 << 12, test_stall=1)
+    try:
+        with pytest.raises(sgagg.SgaggError) as e:
+            agg.aggregate_batched(dev, aggs)
+        assert e.value.status == sgagg.SGAGG_ETIMEOUT
+        res = agg.aggregate_batched(dev, aggs)
+        for r, (rk, ra) in zip(res, refs):
+            np.testing.assert_array_equal(r[0].cpu().numpy(), rk[0])
+            for a in range(len(ra)):
+                np.testing.assert_array_equal(r[1][a].cpu().numpy(), ra[a])
+    finally:
+        agg.close()
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("budget", [1 << 20, 1 << 14])
 def test_injected_allocation_failure(budget):
     c, ref = case(M=budget)

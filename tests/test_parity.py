@@ -124,8 +124,44 @@ def test_c1_full_size_and_run_rows():
 
 def test_c2_report_shape_prefold():
     c = datagen.config2(n=1 << 22, seed=2)
-    st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=c["M"])
+    st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=c["M"], lowcard=0)
     assert st["out_rows"] == 4 and st["prefold_passes"] >= 1
+
+
+def test_c2_report_shape_streaming():
+    """Four key combinations in one batch: one streaming fold (no sort)."""
+    c = datagen.config2(n=1 << 22, seed=3)
+    st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=c["M"])
+    assert st["out_rows"] == 4 and st["kernels"]["stream"]["launches"] == 2
+    assert st["prefold_passes"] == 0 and st["kernel_launches"] <= 4
+
+
+@pytest.mark.parametrize("nkeys", [1, 2, 7, 16, 17])
+@pytest.mark.parametrize("n", [1 << 16, 300_007])
+def test_few_keys_streaming_or_general(nkeys, n):
+    """Up to 16 distinct keys take the streaming fold, 17 the sort; both give
+    the oracle's result, with every aggregate kind on two payloads."""
+    vals = datagen.uniform_int(31, 1, nkeys, 0, (1 << 62))
+    r = datagen.uniform_int(31, 2, n, 0, nkeys - 1)
+    keys = vals[r].view(torch.uint64)
+    pay = [datagen.uniform_int(31, 3, n, -10**15, 10**15), datagen.uniform_int(31, 4, n, -5, 5)]
+    aggs = [(0, 0), (1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (3, 1)]
+    st, _ = check([keys], pay, aggs, M=1 << 30)
+    streamed = st["kernels"]["stream"]["launches"] > 0
+    kd = len(np.unique(keys.numpy()))
+    assert streamed == (kd <= 16 and kd * len(aggs) <= 104)  # accumulators per thread
+
+
+def test_few_keys_sample_misses_a_key():
+    """A key the planner's sample does not see (one row, off the sampled
+    positions) makes the streaming fold give up; the general path groups the
+    input and the result is exact."""
+    n = 1 << 17  # the sample reads rows i * n / 16384, multiples of 8
+    keys = torch.tensor([11, 22, 33], dtype=torch.int64)[datagen.uniform_int(5, 1, n, 0, 2)]
+    keys[12_345] = 99  # an odd row: never sampled
+    pay = [datagen.uniform_int(5, 2, n, -1000, 1000)]
+    st, _ = check([keys.view(torch.uint64)], pay, AGG4, M=1 << 30)
+    assert st["out_rows"] == 4 and st["split_segments"] >= 1
 
 
 def test_c3_shape_reduced():
