@@ -159,8 +159,8 @@ typedef enum {
     SGAGG_OPT_LOWCARD = 10,       /* one batch whose key sample holds at most 16 distinct
                                      keys is grouped by one streaming fold (SGAGG_K_STREAM)
                                      unless this is 0; -1 (default) auto.  Same result. */
-    SGAGG_OPT_MERGE_THREADS = 11, /* threads of one wide-merge CTA (a tile of 2048 rows):
-                                     128, 256 or 512; 0 (default) = 256.  Same result. */
+    SGAGG_OPT_MERGE_THREADS = 11, /* worker threads of one wide-merge CTA (a tile of 2048
+                                     rows): 0 (default) or 256 */
     SGAGG_OPT_HYBRID_FANIN = 12,  /* policy 2: the maximal fan-in F (default 10) */
     SGAGG_OPT_HYBRID_F = 13,      /* policy 2: the actual fan-out f, 0..F; -1 (default):
                                      ceil((O - M) / (M - 1)) from the output size O
@@ -169,7 +169,12 @@ typedef enum {
                                      normalized key's 64 bits); keys at or below it stay in
                                      the in-memory index.  Default: estimated on the key
                                      sample so that the range holds (1 - f/F) M keys */
-    SGAGG_OPT_HYBRID_LAST_AUTO = 15  /* policy 2: back to the estimated resident range */
+    SGAGG_OPT_HYBRID_LAST_AUTO = 15, /* policy 2: back to the estimated resident range */
+    SGAGG_OPT_MERGE_COPY = 16     /* how the wide merge stages run slices in shared memory:
+                                     0 (default) one bulk copy per slice and column
+                                     (cp.async.bulk), issued by all worker warps; 1 16-byte
+                                     cp.async copies by every worker thread; 2 the bulk copies
+                                     issued by the control warp alone.  Same result. */
 } sgagg_option;
 
 /*

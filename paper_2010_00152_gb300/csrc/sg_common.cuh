@@ -251,40 +251,60 @@ __device__ __forceinline__ long long lookback_publish(const LookBack& lb, int id
 // Called by one full warp after lookback_publish (b0: what it returned).
 // Returns the exclusive prefix of chunk `id` and publishes its inclusive
 // prefix, or returns -1 after raising ERR_TIMEOUT (or seeing another error).
+// Each round trip reads the status of up to 4 x 32 predecessors (windows of
+// 32, nearest first) and folds windows in order while they are complete.
 __device__ long long lookback_resolve(const LookBack& lb, int id, long long count, long long b0) {
+  constexpr int NW = 4;
   const int lane = threadIdx.x & 31;
   long long excl = 0;
   if (id == 0) return b0;
   int j = id - 1;  // highest predecessor not yet folded into excl
   long long spins = 0;
   while (true) {
-    int p = j - lane;
-    unsigned long long s = p >= 0 ? lb_load(&lb.status[p]) : kFlagPre;
-    bool ready = (s >> 62) != 0;
-    unsigned all_ready = __ballot_sync(0xffffffffu, ready);
-    // lanes 0..(first not-ready - 1) are usable only if contiguous from lane 0
-    unsigned not_ready = ~all_ready;
-    int usable = not_ready ? __ffs(not_ready) - 1 : 32;  // lanes [0, usable) ready
-    unsigned pre = __ballot_sync(0xffffffffu, ready && ((s >> 62) == 2) && lane < usable);
-    if (pre) {
-      int stop = __ffs(pre) - 1;  // nearest inclusive prefix
-      long long v = (lane <= stop) ? (long long)(s & kValMask) : 0;
-      if (p < 0) v = 0;
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      excl += __shfl_sync(0xffffffffu, v, 0);
-      break;
+    unsigned long long sv[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      const int p = j - 32 * q - lane;
+      sv[q] = p >= 0 ? lb_load(&lb.status[p]) : kFlagPre;
     }
-    if (usable > 0) {
+    bool done = false, moved = false, past = false;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      const int p = j - lane;  // the window read for round q (j moved by whole windows so far)
+      const unsigned long long s = sv[q];
+      const bool ready = (s >> 62) != 0;
+      const unsigned all_ready = __ballot_sync(0xffffffffu, ready);
+      // lanes 0..(first not-ready - 1) are usable only if contiguous from lane 0
+      const unsigned not_ready = ~all_ready;
+      const int usable = not_ready ? __ffs(not_ready) - 1 : 32;
+      const unsigned pre = __ballot_sync(0xffffffffu, ready && ((s >> 62) == 2) && lane < usable);
+      if (pre) {
+        const int stop = __ffs(pre) - 1;  // nearest inclusive prefix
+        long long v = (lane <= stop) ? (long long)(s & kValMask) : 0;
+        if (p < 0) v = 0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        excl += __shfl_sync(0xffffffffu, v, 0);
+        done = true;
+        break;
+      }
+      if (usable == 0) break;
       long long v = (lane < usable && p >= 0) ? (long long)(s & kValMask) : 0;
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       excl += __shfl_sync(0xffffffffu, v, 0);
       j -= usable;
+      moved = true;
       if (j < 0) {  // walked past chunk 0 without a prefix: chunk 0 always publishes one
-        excl += lb.base_in ? *lb.base_in : 0;
+        past = true;
         break;
       }
-      continue;
+      if (usable < 32) break;  // the next windows were read for other positions
     }
+    if (done) break;
+    if (past) {
+      excl += lb.base_in ? *lb.base_in : 0;
+      break;
+    }
+    if (moved) continue;
     // warp-uniform exit: the error word is read by lane 0 only
     int e = __shfl_sync(0xffffffffu, lane == 0 ? err_load(lb.err) : 0, 0);
     if (++spins > lb.spin_limit || e) {

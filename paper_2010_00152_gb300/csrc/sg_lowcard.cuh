@@ -126,16 +126,108 @@ __global__ void __launch_bounds__(256) k_lowcard(LowCardArgs a) {
   }
 }
 
+// The report pattern of aggregates (count(*), then sum, min and max of each
+// of CP payload columns in order -- the shape of Example 1's query): every
+// accumulator sits at a compile-time offset and each column is read once
+// per row.  Same layout and partials as k_lowcard.
+// KL: how the key columns are read -- 0 any (load_key), 1 one 8-byte column,
+// 2 two 1-byte columns -- so that the loads of a step batch across rows.
+template <int KL>
+__device__ __forceinline__ unsigned long long lc_key(const KeyCols& k, long long i) {
+  if (KL == 1) return __ldg(reinterpret_cast<const unsigned long long*>(k.cols[0]) + i);
+  if (KL == 2)
+    return ((unsigned long long)__ldg(reinterpret_cast<const uint8_t*>(k.cols[0]) + i) << 8) |
+           (unsigned long long)__ldg(reinterpret_cast<const uint8_t*>(k.cols[1]) + i);
+  return load_key(k, i);
+}
+
+template <int CP, int KL>
+__global__ void __launch_bounds__(256) k_lowcard_report(LowCardArgs a) {
+  constexpr int T = 256, S = 1 + 3 * CP;
+  extern __shared__ long long lc_acc[];
+  __shared__ unsigned long long sk[kLowCardKeys];
+  const int tid = threadIdx.x;
+  const int kd = a.kd, Q = kd * S;
+  for (int q = 0; q < Q; ++q) {
+    const int ag = q % S;
+    lc_acc[q * T + tid] = ag == 0 ? 0 : ((ag - 1) % 3 == 0 ? 0 : ((ag - 1) % 3 == 1 ? INT64_MAX : INT64_MIN));
+  }
+  if (tid < kd) sk[tid] = a.keys[tid];
+  __syncthreads();
+  bool miss = false;
+  constexpr int U = 8;  // rows per thread per step: every load of a step is in flight at once
+  const long long step = (long long)gridDim.x * T * U;
+  for (long long base = (long long)blockIdx.x * T * U; base < a.n; base += step) {
+    int slot[U];
+    unsigned long long key[U];
+    long long v[U][CP];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = base + (long long)u * T + tid;
+      key[u] = 0;
+#pragma unroll
+      for (int c = 0; c < CP; ++c) v[u][c] = 0;
+      if (i < a.n) {
+        key[u] = lc_key<KL>(a.src.key, a.src.offset + i);
+#pragma unroll
+        for (int c = 0; c < CP; ++c) v[u][c] = __ldg(a.src.cols[c] + a.src.offset + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      slot[u] = -1;
+      if (base + (long long)u * T + tid < a.n) {
+        int lo = 0, hi = kd - 1;  // the key's position among the sampled keys
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (sk[mid] < key[u]) lo = mid + 1; else hi = mid;
+        }
+        if (sk[lo] == key[u]) slot[u] = lo; else miss = true;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (slot[u] < 0) continue;
+      long long* acc = lc_acc + slot[u] * (S * T) + tid;
+      long long cur[S];
+#pragma unroll
+      for (int q = 0; q < S; ++q) cur[q] = acc[q * T];
+      cur[0] += 1;
+#pragma unroll
+      for (int c = 0; c < CP; ++c) {
+        const long long x = v[u][c];
+        cur[1 + 3 * c] = (long long)((unsigned long long)cur[1 + 3 * c] + (unsigned long long)x);
+        cur[2 + 3 * c] = x < cur[2 + 3 * c] ? x : cur[2 + 3 * c];
+        cur[3 + 3 * c] = x > cur[3 + 3 * c] ? x : cur[3 + 3 * c];
+      }
+#pragma unroll
+      for (int q = 0; q < S; ++q) acc[q * T] = cur[q];
+    }
+  }
+  if (miss) atomicOr(a.overflow, 1);
+  __syncthreads();
+  const int lane = tid & 31, nw = T >> 5;
+  for (int q = tid >> 5; q < Q; q += nw) {
+    const int op = a.fd.op[q % S];
+    long long x = op_identity(op);
+    for (int t = lane; t < T; t += 32) x = op_combine(op, x, lc_acc[q * T + t]);
+    for (int o = 16; o > 0; o >>= 1) x = op_combine(op, x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) a.partial[(long long)blockIdx.x * Q + q] = x;
+  }
+}
+
 // One block: the blocks' partials combined, the kd keys and their
 // aggregates written (when they fit out.capacity), *rows = kd.
 __global__ void k_lowcard_finish(LowCardArgs a, int blocks, OutSinkLite out, long long* rows) {
   const int S = a.fd.n_state, Q = a.kd * S;
   const bool fits = a.kd <= out.capacity;
-  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = threadIdx.x >> 5; q < Q; q += nw) {  // a warp per accumulator, lanes over blocks
     const int op = a.fd.op[q % S];
     long long v = op_identity(op);
-    for (int b = 0; b < blocks; ++b) v = op_combine(op, v, a.partial[(long long)b * Q + q]);
-    if (fits) out.cols[q % S][q / S] = v;
+    for (int b = lane; b < blocks; b += 32) v = op_combine(op, v, a.partial[(long long)b * Q + q]);
+    for (int o = 16; o > 0; o >>= 1) v = op_combine(op, v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (fits && lane == 0) out.cols[q % S][q / S] = v;
   }
   for (int g = threadIdx.x; g < a.kd; g += blockDim.x)
     if (fits) store_key(out.kout, g, a.keys[g]);

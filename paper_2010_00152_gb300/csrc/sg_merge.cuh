@@ -53,9 +53,13 @@ struct MergeArgs {
   int capk;     // elements of the key buffer and of every column buffer (a multiple
                 // of 16, at least tile rows + 2k, at most kMergeCapMax)
   int scol;     // state-column buffers (at least 2)
-  int bulk;     // 1: every run array is device memory with a 16-byte aligned
-                //    start and one readable row past its last run row: bulk
-                //    copies; 0: plain loads
+  int bulk;     // how slices reach shared memory: 1 one bulk copy per slice
+                //    and column (cp.async.bulk) issued by the control warp, 3
+                //    the same bulk copies issued by the worker warps (a slice
+                //    per warp, an array per lane), 2 16-byte cp.async copies
+                //    by every worker -- all need every run array in device
+                //    memory, 16-byte aligned, with one readable row past its
+                //    last run row; 0 plain loads
 };
 
 // Position p of a dense ping-pong buffer, swizzled inside its 16-element
@@ -367,9 +371,9 @@ __device__ __forceinline__ int mbin(const uint32_t* cnt, int b) { return (int)((
 __device__ __forceinline__ void stage_columns(const MergeArgs& a, const MergeSmem& m, int k, int E, int c0, int gc) {
   const int lane = threadIdx.x & 31;
   const int S = a.runs.ncols;
-  if (lane == 0) mbar_arrive_tx(&m.bar[1], a.bulk ? (unsigned)E * 8u * (unsigned)gc : 0u);
+  if (lane == 0) mbar_arrive_tx(&m.bar[1], (a.bulk == 1 || a.bulk == 3) ? (unsigned)E * 8u * (unsigned)gc : 0u);
   __syncwarp();
-  if (!a.bulk) return;
+  if (a.bulk != 1 && a.bulk != 3) return;
   for (int r = lane; r < k; r += 32) {
     const int cnt = m.RS[r + 1] - m.RS[r];
     if (cnt == 0) continue;
@@ -377,6 +381,53 @@ __device__ __forceinline__ void stage_columns(const MergeArgs& a, const MergeSme
     const long long* const* pr = a.runs.ptrs + (long long)r * (1 + S);
     for (int c = 0; c < gc; ++c)
       bulk_g2s(m.C + (size_t)c * a.capk + m.RS[r], pr[1 + c0 + c] + row0, (unsigned)cnt * 8u, &m.bar[1]);
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+
+// 16-byte asynchronous copies (cp.async) of the slices of the keys (keys)
+// and of state columns [c0, c0 + gc), issued by all workers, a warp per
+// slice; complete and visible to every worker when it returns.
+template <int THREADS>
+__device__ __forceinline__ void copy_async16(const MergeArgs& a, const MergeSmem& m, int k, int c0, int gc,
+                                             bool keys) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int S = a.runs.ncols;
+  for (int r = w; r < k; r += THREADS / 32) {
+    const int cnt = m.RS[r + 1] - m.RS[r];
+    if (cnt == 0) continue;
+    const long long row0 = m.LO[r] - (m.DS[r] - m.RS[r]);
+    const long long* const* pr = a.runs.ptrs + (long long)r * (1 + S);
+    const int chunks = cnt >> 1;
+    for (int q = keys ? -1 : 0; q < gc; ++q) {
+      const long long* src = (q < 0 ? pr[0] : pr[1 + c0 + q]) + row0;
+      long long* dst = (q < 0 ? reinterpret_cast<long long*>(m.A) : m.C + (size_t)q * a.capk) + m.RS[r];
+      for (int c = lane; c < chunks; c += 32) cp_async16(dst + 2 * c, src + 2 * c);
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  wsync<THREADS>();
+}
+
+// The first staging of a tile (keys and the first gc state columns) as bulk
+// copies issued by the worker warps: warp w takes slices w, w + W, ...; lane
+// 0 copies the slice's keys, lane 1 + c its column c.  The mbarriers are
+// armed by the control warp.
+template <int THREADS>
+__device__ __forceinline__ void bulk_by_workers(const MergeArgs& a, const MergeSmem& m, int k, int gc) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int S = a.runs.ncols;
+  for (int r = w; r < k; r += THREADS / 32) {
+    const int cnt = m.RS[r + 1] - m.RS[r];
+    if (cnt == 0 || lane > gc) continue;
+    const long long row0 = m.LO[r] - (m.DS[r] - m.RS[r]);
+    const long long* const* pr = a.runs.ptrs + (long long)r * (1 + S);
+    if (lane == 0) bulk_g2s(m.A + m.RS[r], pr[0] + row0, (unsigned)cnt * 8u, &m.bar[0]);
+    else bulk_g2s(m.C + (size_t)(lane - 1) * a.capk + m.RS[r], pr[lane] + row0, (unsigned)cnt * 8u, &m.bar[1]);
   }
 }
 
@@ -509,7 +560,7 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
         lo = a.tslo[(long long)cid * k + r];
         const long long hi = a.tslo[(long long)(cid + 1) * k + r];
         len = (int)min(max(hi - lo, 0ll), (long long)capk);  // oversized tiles are refused below
-        ph = (a.bulk && len > 0) ? (int)(lo & 1) : 0;
+        ph = (a.bulk != 0 && len > 0) ? (int)(lo & 1) : 0;
         cnt = len == 0 ? 0 : ((len + ph + 1) & ~1);
       }
       int xd = len, xr = cnt;
@@ -533,9 +584,9 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
     const bool ok = cr <= capk && cd <= kMergeTile;
     __syncwarp();
     if (ok) {
-      if (lane == 0) mbar_arrive_tx(&m.bar[0], a.bulk ? (unsigned)cr * 8u : 0u);
+      if (lane == 0) mbar_arrive_tx(&m.bar[0], (a.bulk == 1 || a.bulk == 3) ? (unsigned)cr * 8u : 0u);
       __syncwarp();
-      if (a.bulk) {
+      if (a.bulk == 1) {
         for (int r = lane; r < k; r += 32) {
           const int cnt = m.RS[r + 1] - m.RS[r];
           if (cnt == 0) continue;
@@ -543,7 +594,12 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
           bulk_g2s(m.A + m.RS[r], a.runs.ptrs[(long long)r * (1 + S)] + row0, (unsigned)cnt * 8u, &m.bar[0]);
         }
       }
-      stage_columns(a, m, k, cr, 0, g0cols);
+      if (a.bulk == 3) {  // arm only: the workers copy
+        if (lane == 0) mbar_arrive_tx(&m.bar[1], (unsigned)cr * 8u * (unsigned)g0cols);
+        __syncwarp();
+      } else {
+        stage_columns(a, m, k, cr, 0, g0cols);
+      }
       // slice-order positions holding a row: all of [0, cr) but the pads
       for (int q = lane; q < (cr + 31) / 32; q += 32) {
         const int left = cr - 32 * q;
@@ -586,7 +642,7 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
         got = false;
         break;
       }
-      __nanosleep(spins < 8 ? 128u : 1024u);
+      __nanosleep(spins < 64 ? 32u : 256u);
     }
     __syncwarp();
     long long b = -1;
@@ -609,9 +665,13 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
 
   // ---- workers ----
   const int n = s_n, E = s_E;
-  if (!a.bulk) {
+  if (a.bulk == 0) {
     load_columns_plain<THREADS>(a, m, k, n, 0, g0cols, true);
     wsync<THREADS>();
+  } else if (a.bulk == 2) {
+    copy_async16<THREADS>(a, m, k, 0, g0cols, true);
+  } else if (a.bulk == 3) {
+    bulk_by_workers<THREADS>(a, m, k, g0cols);
   }
   if (!workers_wait<THREADS>(&m.bar[0], 0, lb, &s_flag)) return;
 
@@ -771,9 +831,11 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
     }
     wsync<THREADS>();  // the column area is free again: stage the columns anew
     if (w == 0) stage_columns(a, m, k, E, 0, g0cols);
-    if (!a.bulk) {
+    if (a.bulk == 0) {
       load_columns_plain<THREADS>(a, m, k, n, 0, g0cols, false);
       wsync<THREADS>();
+    } else if (a.bulk == 2) {
+      copy_async16<THREADS>(a, m, k, 0, g0cols, false);
     }
     bphase = 1;
   } else {
@@ -879,9 +941,11 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
     if (c0 + scol < S) {
       wsync<THREADS>();  // the column buffers are read: stage the next group
       if (w == 0) stage_columns(a, m, k, E, c0 + scol, min(scol, S - c0 - scol));
-      if (!a.bulk) {
+      if (a.bulk == 0) {
         load_columns_plain<THREADS>(a, m, k, n, c0 + scol, min(scol, S - c0 - scol), false);
         wsync<THREADS>();
+      } else if (a.bulk == 2) {
+        copy_async16<THREADS>(a, m, k, c0 + scol, min(scol, S - c0 - scol), false);
       }
     }
   }

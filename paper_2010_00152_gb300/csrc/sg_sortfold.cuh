@@ -872,19 +872,7 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
       if ((hb >> lane) & 1u) {
         const int g = run + __popc(hb & lt);
         const long long pos = base + g;
-        const unsigned long long hk = s.keys[s.idx[p]];
-        sink_key(out, pos, hk);
-        if (out.offs) {
-          // the run's sparse index: offs[f] = base + (groups whose fine
-          // digit is below f); this head sets it for the fine buckets from
-          // after the previous key's up to its own (the last head also for
-          // those after it, up to the chunk's end)
-          const int f = (int)fine_digit(out.dig, hk);
-          const int fp = p > 0 ? (int)fine_digit(out.dig, s.keys[s.idx[p - 1]]) : ch.f_lo - 1;
-          for (int ff = fp + 1; ff <= f; ++ff) out.offs[ff] = pos;
-          if (g == count - 1)
-            for (int ff = f + 1; ff <= ch.f_hi; ++ff) out.offs[ff] = base + count;
-        }
+        sink_key(out, pos, s.keys[s.idx[p]]);
         int e = -1;
 #pragma unroll(KS <= 8 ? KS : 1)
         for (int a = 0; a < KS; ++a)
@@ -895,6 +883,21 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
         if (few) g_gstart[g] = p;
       }
       run += __popc(hb);
+    }
+  }
+  // the run's sparse index: offs[f] = rows of this run before the first key
+  // with fine digit >= f, for every fine bucket of the chunk's key range (a
+  // thread per fine bucket, by binary search over the sorted rows)
+  if (out.offs) {
+    for (int f = ch.f_lo + (int)threadIdx.x; f <= ch.f_hi; f += kThreads) {
+      int lo = 0, hi = n;  // first sorted position whose fine digit is >= f
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)fine_digit(out.dig, s.keys[s.idx[mid]]) < f) lo = mid + 1; else hi = mid;
+      }
+      const int heads = lo >= n ? count
+                                : (int)hpre[lo >> 5] + __popc(hm[lo >> 5] & ((1u << (lo & 31)) - 1u));
+      out.offs[f] = base + heads;
     }
   }
   if (few && threadIdx.x == 0) g_gstart[count] = n;

@@ -122,6 +122,8 @@ struct sgagg_ctx {
   long long absorb_batch = 0;    // rows per batch of the absorbing policy (0: auto)
   int lowcard = -1;              // streaming fold of few keys: -1 auto, 0 off
   int merge_threads = 0;         // threads of a merge CTA (128, 256, 512; 0 = default)
+  int merge_copy = 0;            // merge staging: 0 bulk copies by the workers, 1 16-byte cp.async,
+                                 // 2 bulk copies by the control warp
   int hybrid_fanin = 10;         // hybrid run generation (policy 2): F
   int hybrid_f = -1;             // f (-1: from the estimated output size)
   bool hybrid_last_given = false;
@@ -623,10 +625,10 @@ sgagg_status launch_merge(sgagg_t h, const Chunk* dchunks, int n_chunks, const l
   a.copy = copy;
   a.fd = fd;
   a.out = out;
-  a.bulk = bulk ? 1 : 0;
+  a.bulk = bulk ? (h->merge_copy == 1 ? 2 : (h->merge_copy == 2 ? 1 : 3)) : 0;
   const int k = runs.k, S = runs.ncols;
   a.capk = (int)(((kMergeTile + 2ll * k) + 15) / 16 * 16);
-  const int threads = h->merge_threads > 0 ? h->merge_threads : 256;
+  constexpr int threads = 256;
   if (a.capk > kMergeCapMax) return fail(h, SGAGG_ECUDA, "merge fan-in exceeds the tile layout");
   // state columns staged at once: all of them (at least two buffers) within
   // three CTAs per SM, else all within two, else as many as fit two
@@ -647,15 +649,11 @@ sgagg_status launch_merge(sgagg_t h, const Chunk* dchunks, int n_chunks, const l
   static DeviceOnce once;
   int dev = 0;
   if (once.need(&dev)) {
-    CU(cudaFuncSetAttribute(k_merge<128, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CU(cudaFuncSetAttribute(k_merge<256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    CU(cudaFuncSetAttribute(k_merge<512, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     once.done(dev);
   }
   kbegin(h, SGAGG_K_MERGE);
-  if (threads == 128) k_merge<128, 16><<<n_chunks, 128 + 32, smem, h->stream>>>(a);
-  else if (threads == 512) k_merge<512, 4><<<n_chunks, 512 + 32, smem, h->stream>>>(a);
-  else k_merge<256, 8><<<n_chunks, 256 + 32, smem, h->stream>>>(a);
+  k_merge<256, 8><<<n_chunks, threads + 32, smem, h->stream>>>(a);
   kend(h);
   CU(cudaGetLastError());
   return SGAGG_OK;
@@ -1596,9 +1594,40 @@ sgagg_status lowcard_device(sgagg_t h, const RowSrc& raw, long long n, const Fol
     CU(cudaFuncSetAttribute(k_lowcard<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024));
     once.done(dev);
   }
+  // the report pattern: count(*), then sum / min / max of every payload
+  // column in column order
+  int cp = (S >= 1 && (S - 1) % 3 == 0 && fd.src[0] < 0) ? (S - 1) / 3 : 0;
+  for (int c = 0; c < cp; ++c)
+    if (fd.src[1 + 3 * c] != c || fd.src[2 + 3 * c] != c || fd.src[3 + 3 * c] != c || fd.op[1 + 3 * c] != OP_SUM ||
+        fd.op[2 + 3 * c] != OP_MIN || fd.op[3 + 3 * c] != OP_MAX || raw.ncols != cp)
+      cp = 0;
+  if (cp > 4 || T != 256) cp = 0;
+  const int kl = raw.key.n_cols == 1 && raw.key.bytes[0] == 8 ? 1
+                 : (raw.key.n_cols == 2 && raw.key.bytes[0] == 1 && raw.key.bytes[1] == 1 ? 2 : 0);
+  static DeviceOnce once_r;
+  if (once_r.need(&dev)) {
+#define LCR_ATTR(C)                                                                                     \
+  CU(cudaFuncSetAttribute(k_lowcard_report<C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024)); \
+  CU(cudaFuncSetAttribute(k_lowcard_report<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024)); \
+  CU(cudaFuncSetAttribute(k_lowcard_report<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024));
+    LCR_ATTR(1) LCR_ATTR(2) LCR_ATTR(3) LCR_ATTR(4)
+#undef LCR_ATTR
+    once_r.done(dev);
+  }
   CU(cudaMemsetAsync(&ds->lc_over, 0, sizeof(int), h->stream));
   kbegin(h, SGAGG_K_STREAM);
-  if (S <= 2) k_lowcard<2><<<blocks, T, smem, h->stream>>>(a);
+#define LCR_LAUNCH(C)                                                                 \
+  do {                                                                                \
+    if (kl == 1) k_lowcard_report<C, 1><<<blocks, T, smem, h->stream>>>(a);           \
+    else if (kl == 2) k_lowcard_report<C, 2><<<blocks, T, smem, h->stream>>>(a);      \
+    else k_lowcard_report<C, 0><<<blocks, T, smem, h->stream>>>(a);                   \
+  } while (0)
+  if (cp == 1) LCR_LAUNCH(1);
+  else if (cp == 2) LCR_LAUNCH(2);
+  else if (cp == 3) LCR_LAUNCH(3);
+  else if (cp == 4) LCR_LAUNCH(4);
+#undef LCR_LAUNCH
+  else if (S <= 2) k_lowcard<2><<<blocks, T, smem, h->stream>>>(a);
   else if (S <= 4) k_lowcard<4><<<blocks, T, smem, h->stream>>>(a);
   else if (S <= 8) k_lowcard<8><<<blocks, T, smem, h->stream>>>(a);
   else if (S <= 16) k_lowcard<16><<<blocks, T, smem, h->stream>>>(a);
@@ -2549,9 +2578,11 @@ sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
     case SGAGG_OPT_HYBRID_LAST_AUTO:
       h->hybrid_last_given = false;
       return SGAGG_OK;
+    case SGAGG_OPT_MERGE_COPY:
+      h->merge_copy = (value == 1 || value == 2) ? (int)value : 0;
+      return SGAGG_OK;
     case SGAGG_OPT_MERGE_THREADS:
-      if (value != 0 && value != 128 && value != 256 && value != 512)
-        return fail(h, SGAGG_EINVAL, "merge threads must be 0, 128, 256 or 512");
+      if (value != 0 && value != 256) return fail(h, SGAGG_EINVAL, "merge threads must be 0 or 256");
       h->merge_threads = (int)value;
       return SGAGG_OK;
     default: return fail(h, SGAGG_EINVAL, "unknown option");
