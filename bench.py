@@ -538,8 +538,10 @@ def main():
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
     dom = max(cls_ms, key=lambda k: cls_ms[k])
-    per_launch_bytes = cls_bytes[dom] / max(1, cls_n[dom])
-    per_launch_ms = cls_ms[dom] / max(1, cls_n[dom])
+    # the dominant class's work in one call (the wide merge is one launch of
+    # its count pass and scan and one of the merge kernel per call)
+    per_launch_bytes = cls_bytes[dom] / args.steps
+    per_launch_ms = cls_ms[dom] / args.steps
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
     kernels = {k: {"launches_per_step": cls_n[k] / args.steps,
                    "ms_per_step": round(cls_ms[k] / args.steps, 4),
@@ -583,8 +585,9 @@ def main():
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                          "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                          "peak_kind": peak_kind, "traffic": traffic_for(dom),
-                         "bytes_per_launch": int(per_launch_bytes),
-                         "ms_per_launch": round(per_launch_ms, 4)},
+                         "bytes_per_call": int(per_launch_bytes),
+                         "ms_per_call": round(per_launch_ms, 4),
+                         "launches_per_call": cls_n[dom] / args.steps},
             "method_bytes_per_step": int(alg),
             "method_hbm_frac": round(alg / (ms_max / 1e3) / 1e9 / hbm, 4),
             "temp_bytes": temp_bytes, "output_bytes": int(out_b),

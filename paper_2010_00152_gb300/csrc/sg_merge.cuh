@@ -18,15 +18,14 @@
 //      k) levels of pairwise merges of the sorted slices, split across
 //      threads by merge-path diagonals;
 //   3. each worker thread takes IPT consecutive sorted rows into registers;
-//      heads (first rows of equal keys) and their ranks come from one scan,
-//      and the tile's distinct-key count goes to the control warp, which
-//      publishes it and resolves the decoupled look-back (the wait for
-//      predecessors) while the workers fold;
+//      heads (first rows of equal keys) and their ranks come from one scan;
 //   4. every state column is folded from registers (segmented by the heads;
 //      the group open at a thread's end takes the leading partials of the
 //      next threads) and staged in output order in its own column buffer;
-//   5. the look-back gives the tile's output offset, and every output column
-//      leaves in coalesced 16-byte stores.
+//   5. every output column leaves in coalesced 16-byte stores at the tile's
+//      output base, which a count pass before the merge (k_merge_count: each
+//      tile's distinct keys through a shared-memory hash set) and a scan of
+//      the counts (k_merge_scan) fixed: no tile waits on another.
 #pragma once
 #include "sg_sortfold.cuh"
 
@@ -43,13 +42,14 @@ constexpr int kMergeFixMax = 32;                           // rows of a bucket s
 // column s folds run column s by fd.op[s].
 struct MergeArgs {
   const Chunk* chunks;
+  const long long* tbase;  // [tiles]: output row of every tile's first group (k_merge_scan)
   const long long* tslo;   // [(tiles + 1) * k]: tile t's slice of run r starts at row tslo[t * k + r]
                            // and ends where tile t + 1's starts
   RunSet runs;
   CopySrc copy;
   FoldDesc fd;
   OutSink out;
-  LookBack lb;
+  LookBack lb;   // the error word and the wait limit (tiles do not wait on one another)
   int capk;     // elements of the key buffer and of every column buffer (a multiple
                 // of 16, at least tile rows + 2k, at most kMergeCapMax)
   int scol;     // state-column buffers (at least 2)
@@ -290,15 +290,11 @@ __device__ __forceinline__ long long mop(long long a, long long b) {
   return b > a ? b : a;
 }
 
-// Named barriers of a merge CTA: 1 -- the worker threads (threads 0 ..
-// THREADS - 1) among themselves; 2 -- the control warp (the last warp)
-// hands the workers the tile's output base.  (The workers hand it the
-// tile's count through a flag it polls with a bound, so no thread ever waits
-// on a barrier that a thread gone after a timeout would never reach.)
+// Named barrier 1 of a merge CTA: the worker threads (threads 0 .. THREADS
+// - 1) among themselves (the control warp, the last warp, leaves after the
+// prologue).
 template <int NT>
 __device__ __forceinline__ void wsync() { asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory"); }
-__device__ __forceinline__ void nb_arrive(int id, int nt) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nt) : "memory"); }
-__device__ __forceinline__ void nb_sync(int id, int nt) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nt) : "memory"); }
 
 // Fold one state column over the IPT sorted rows a thread holds (slice-
 // order indexes X, heads hm): R[j] is the fold from the row's group head (or
@@ -483,6 +479,106 @@ __global__ void k_tile_slices(const Chunk* chunks, int n_chunks, const long long
   }
 }
 
+// ---------------------------------------------------------------------------
+// Every tile's output rows before the merge: a tile's distinct keys are
+// counted by inserting its keys into an open-addressing hash set in shared
+// memory (no sort), and a scan of the counts gives every tile its output
+// base -- so merge tiles never wait on one another.
+// ---------------------------------------------------------------------------
+constexpr int kCountThreads = 256;
+constexpr int kCountSlotBits = 12;   // 4,096 slots for at most 2,048 keys
+constexpr int kCountSlots = 1 << kCountSlotBits;
+
+// count[t] = distinct keys of tile t (its rows, for a tile solved apart).
+__global__ void __launch_bounds__(kCountThreads) k_merge_count(const Chunk* __restrict__ chunks,
+                                                               const long long* __restrict__ tslo, RunSet runs,
+                                                               long long* count, int* err) {
+  __shared__ unsigned long long tab[kCountSlots];
+  __shared__ int s_cnt, s_top;
+  const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const Chunk ch = chunks[t];
+  if (ch.kind == CH_COPY) {
+    if (tid == 0) count[t] = ch.hi - ch.lo;
+    return;
+  }
+  for (int i = tid; i < kCountSlots; i += kCountThreads) tab[i] = ~0ull;  // empty; key ~0 is counted apart
+  if (tid == 0) {
+    s_cnt = 0;
+    s_top = 0;
+  }
+  __syncthreads();
+  const int k = runs.k;
+  int mine = 0;
+  for (int r = w; r < k; r += kCountThreads / 32) {  // a warp per slice
+    const long long lo = tslo[(long long)t * k + r], hi = tslo[(long long)(t + 1) * k + r];
+    const long long* keys = runs.ptrs[(long long)r * (1 + runs.ncols)];
+    for (long long i = lo + lane; i < hi; i += 32) {
+      const unsigned long long key = (unsigned long long)__ldg(keys + i);
+      if (key == ~0ull) {
+        if (atomicExch(&s_top, 1) == 0) ++mine;
+        continue;
+      }
+      unsigned slot = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCountSlotBits));
+      int probes = 0;
+      while (true) {  // a tile has at most 2,048 keys in 4,096 slots: a free slot is near
+        const unsigned long long old = atomicCAS(&tab[slot], ~0ull, key);
+        if (old == ~0ull) { ++mine; break; }
+        if (old == key) break;
+        slot = (slot + 1) & (kCountSlots - 1);
+        if (++probes == kCountSlots) {  // the planner never makes such tiles
+          err_raise(err, ERR_INTERNAL);
+          break;
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if (lane == 0) atomicAdd(&s_cnt, mine);
+  __syncthreads();
+  if (tid == 0) count[t] = s_cnt;
+}
+
+// base[t] = *base_in + count[0] + ... + count[t - 1]; *total_out = the end;
+// ERR_CAPACITY when the end exceeds the output capacity.  Blocks of 1,024
+// tiles in ticket order, chained by decoupled look-back.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_merge_scan(const long long* count, int n, long long* base,
+                                                             LookBack lb, long long capacity) {
+  __shared__ int s_id;
+  __shared__ long long s_w[kScanThreads / 32];
+  __shared__ long long s_pre;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) s_id = (int)atomicAdd(lb.ticket, 1u);
+  __syncthreads();
+  const int b = s_id;
+  const int i = b * kScanThreads + tid;
+  const long long v = i < n ? count[i] : 0;
+  long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[w] = x;
+  __syncthreads();
+  long long before = 0, total = 0;
+  for (int q = 0; q < kScanThreads / 32; ++q) {
+    before += q < w ? s_w[q] : 0;
+    total += s_w[q];
+  }
+  if (tid < 32) {
+    const long long pre = lookback_warp(lb, b, total);
+    if (tid == 0) {
+      s_pre = pre;
+      if (pre >= 0 && b == lb.n_chunks - 1) {
+        if (lb.total_out) *lb.total_out = pre + total;
+        if (pre + total > capacity) err_raise(lb.err, ERR_CAPACITY);
+      }
+    }
+  }
+  __syncthreads();
+  if (s_pre >= 0 && i < n) base[i] = s_pre + before + x - v;
+}
+
 // One CTA per merge tile: THREADS worker threads and one control warp.
 template <int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merge(MergeArgs a) {
@@ -493,9 +589,7 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
   static_assert(BPT % 2 == 0 && BPT * THREADS == kMergeBuckets, "bucket scan layout");
   static_assert(IPT * THREADS == kMergeTile, "tile layout");
   extern __shared__ __align__(128) unsigned char msmem[];
-  __shared__ int s_cid, s_err, s_ok, s_n, s_E, s_flag, s_crowd, s_nflag;
-  __shared__ volatile int s_cready, s_count;
-  __shared__ long long s_base;
+  __shared__ int s_err, s_ok, s_n, s_E, s_flag, s_crowd, s_nflag;
   __shared__ unsigned long long s_kmin, s_kmax, s_wlast[W];
   __shared__ int s_wcnt[W];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -503,29 +597,15 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
   const LookBack& lb = a.lb;
   const OutSink& out = a.out;
 
-  if (tid == THREADS) {
-    s_cid = (int)atomicAdd(lb.ticket, 1u);
-    s_err = err_load(lb.err);
-    s_cready = 0;
-  }
+  if (tid == THREADS) s_err = err_load(lb.err);
   __syncthreads();
-  const int cid = s_cid;
-  if (cid >= lb.n_chunks || s_err) return;  // block-uniform
+  const int cid = blockIdx.x;
+  if (s_err) return;  // block-uniform
   const Chunk ch = a.chunks[cid];
 
   if (ch.kind == CH_COPY) {  // a key range solved apart: its rows are copied verbatim
     const long long n = ch.hi - ch.lo;
-    if (control) {
-      const long long b = lookback_warp(lb, cid, n);
-      if (lane == 0) {
-        s_base = b;
-        if (b >= 0 && lb.total_out && cid == lb.n_chunks - 1) *lb.total_out = b + n;
-        if (b >= 0 && b + n > out.capacity) err_raise(lb.err, ERR_CAPACITY);
-      }
-    }
-    __syncthreads();
-    const long long base = s_base;
-    if (base < 0) return;
+    const long long base = a.tbase[cid];
     for (long long g = tid; g < n; g += NALL) {
       const unsigned long long key = a.copy.keys[ch.lo + g];
       sink_key(out, base + g, key);
@@ -632,36 +712,7 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
     return;
   }
 
-  if (control) {
-    // ---- control warp: the tile's count from the workers (a polled flag,
-    // bounded), its publication, the look-back for the output base ----
-    long long spins = 0;
-    bool got = true;
-    while (!s_cready) {
-      if (++spins > lb.spin_limit || err_load(lb.err)) {
-        got = false;
-        break;
-      }
-      __nanosleep(spins < 64 ? 32u : 256u);
-    }
-    __syncwarp();
-    long long b = -1;
-    if (got) {
-      const long long count = s_count;
-      const long long b0 = lookback_publish(lb, cid, count);
-      b = lookback_resolve(lb, cid, count, b0);
-      if (lane == 0 && b >= 0) {
-        if (lb.total_out && cid == lb.n_chunks - 1) *lb.total_out = b + count;
-        if (b + count > out.capacity) err_raise(lb.err, ERR_CAPACITY);
-      }
-    } else if (lane == 0) {
-      err_raise(lb.err, ERR_TIMEOUT);
-    }
-    if (lane == 0) s_base = b;
-    __syncwarp();
-    nb_arrive(2, NALL);
-    return;
-  }
+  if (control) return;  // the control warp's part is done
 
   // ---- workers ----
   const int n = s_n, E = s_E;
@@ -875,11 +926,6 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
     count += c;
   }
   const int g0 = wpre + x - hc;
-  if (tid == 0) {  // the count to the control warp
-    s_count = count;
-    __threadfence_block();
-    s_cready = 1;
-  }
   {  // output keys, staged in A
     int r = g0;
 #pragma unroll
@@ -904,11 +950,10 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
         par ^= 1;
       }
     }
+    wsync<THREADS>();  // staged outputs complete
+    const long long base = a.tbase[cid];
     if (!resolved) {
-      nb_sync(2, NALL);  // staged outputs complete; the control warp's output base
       resolved = true;
-      const long long base = s_base;
-      if (base < 0) return;
       // keys
       if (!out.user) {
         store_staged<THREADS>(reinterpret_cast<long long*>(out.keys), reinterpret_cast<const long long*>(m.A),
@@ -932,10 +977,7 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
           out.offs[f] = base + lo;
         }
       }
-    } else {
-      wsync<THREADS>();  // staged outputs complete
     }
-    const long long base = s_base;
     for (int cl = 0; cl < gc; ++cl)
       store_staged<THREADS>(out.cols[c0 + cl], m.C + (size_t)cl * capk, count, base, out.capacity);
     if (c0 + scol < S) {

@@ -175,6 +175,7 @@ struct sgagg_ctx {
   DevBuf plan_tmp;                         // chunk planner: per-block sums and starts
   DevBuf lc_part;                          // streaming fold of few keys: per-block partials
   DevBuf tslo;                             // wide merge: every tile's slice start in every run
+  DevBuf tcount, tbase;                    // wide merge: every tile's distinct keys, output base
   std::vector<DevBuf> dk_cols;
   std::vector<DevBuf> ab_cols[3];
   DevBuf marena_keys;            // runs written by preliminary merges
@@ -607,8 +608,12 @@ sgagg_status launch_merge(sgagg_t h, const Chunk* dchunks, int n_chunks, const l
     }
     return SGAGG_OK;
   }
-  TRY(grow(h, h->status, (size_t)(n_chunks + 2) * 8));
-  CU(cudaMemsetAsync(h->status.p, 0, (size_t)(n_chunks + 2) * 8, h->stream));
+  // every tile's distinct keys (a count pass), their scan: the tiles' output bases
+  const int sblocks = (n_chunks + kScanThreads - 1) / kScanThreads;
+  TRY(grow(h, h->status, (size_t)(sblocks + 2) * 8));
+  TRY(grow(h, h->tcount, (size_t)n_chunks * 8));
+  TRY(grow(h, h->tbase, (size_t)n_chunks * 8));
+  CU(cudaMemsetAsync(h->status.p, 0, (size_t)(sblocks + 2) * 8, h->stream));
   MergeArgs a{};
   a.lb.ticket = reinterpret_cast<unsigned int*>(P<unsigned long long>(h->status));
   a.lb.status = P<unsigned long long>(h->status) + 2;
@@ -616,10 +621,20 @@ sgagg_status launch_merge(sgagg_t h, const Chunk* dchunks, int n_chunks, const l
   a.lb.total_out = reinterpret_cast<long long*>(total_out);
   a.lb.err = &dsmall(h)->err;
   a.lb.spin_limit = h->spin_limit;
-  a.lb.n_chunks = n_chunks;
+  a.lb.n_chunks = sblocks;
   a.lb.stall = h->test_stall != 0 ? 1 : 0;
   h->test_stall = 0;
+  kbegin(h, SGAGG_K_MERGE);
+  k_merge_count<<<n_chunks, kCountThreads, 0, h->stream>>>(dchunks, tslo, runs, P<long long>(h->tcount),
+                                                           &dsmall(h)->err);
+  k_merge_scan<<<sblocks, kScanThreads, 0, h->stream>>>(P<long long>(h->tcount), n_chunks, P<long long>(h->tbase),
+                                                        a.lb, out.capacity);
+  kend(h);
+  CU(cudaGetLastError());
+  h->st.class_launches[SGAGG_K_MERGE] += 1;  // kbegin counted one of the two
+  h->st.kernel_launches += 1;
   a.chunks = dchunks;
+  a.tbase = P<long long>(h->tbase);
   a.tslo = tslo;
   a.runs = runs;
   a.copy = copy;
@@ -2853,7 +2868,7 @@ void sgagg_destroy(sgagg_t h) {
     free_buf(h->ab_keys[i]); free_buf(h->ab_offs[i]); fv(h->ab_cols[i]);
   }
   free_buf(h->ab_tmp);
-  free_buf(h->dk_keys); free_buf(h->rg_heads); fv(h->dk_cols); free_buf(h->plan_tmp); free_buf(h->lc_part); free_buf(h->tslo);
+  free_buf(h->dk_keys); free_buf(h->rg_heads); fv(h->dk_cols); free_buf(h->plan_tmp); free_buf(h->lc_part); free_buf(h->tslo); free_buf(h->tcount); free_buf(h->tbase);
   for (int i = 0; i < 2; ++i) { free_buf(h->hsplit_keys[i]); fv(h->hsplit_cols[i]); }
   free_buf(h->binst); free_buf(h->bchunks); free_buf(h->bkeys); free_buf(h->bout_keys);
   free_buf(h->bseg); free_buf(h->brange); free_buf(h->bstartb); free_buf(h->bdirect);

@@ -43,15 +43,17 @@ def test_device_wait_times_out_and_handle_recovers():
 
 
 def test_merge_wait_times_out_and_handle_recovers():
-    """The stall hits the wide merge (16 runs): its first tile never
-    publishes, the others' bounded look-back waits run out."""
-    c, ref = case(M=1 << 14)
-    agg = sgagg.Aggregator(1 << 14, spin_limit=1 << 12, test_stall=2)
+    """The stall hits the wide merge (32 runs, some 2,000 merge tiles): the
+    first block of the scan of the tiles' row counts never publishes, the
+    other blocks' bounded look-back waits run out; no merge tile writes."""
+    c, ref = case(n=4_000_000, D=2_000_000, M=1 << 17)
+    agg = sgagg.Aggregator(1 << 17, spin_limit=1 << 12, test_stall=2)
     try:
         with pytest.raises(sgagg.SgaggError) as e:
             agg.aggregate(c["key_cols"], c["payload"], c["aggs"])
         assert e.value.status == sgagg.SGAGG_ETIMEOUT
-        assert agg.stats()["runs"] > 1  # run generation finished; the merge timed out
+        st = agg.stats()
+        assert st["runs"] > 1 and st["merge_tiles"] > 1024  # run generation finished; the merge timed out
         same(agg.aggregate(c["key_cols"], c["payload"], c["aggs"]), ref)
     finally:
         agg.close()
