@@ -490,45 +490,95 @@ constexpr int kCountSlotBits = 12;   // 4,096 slots for at most 2,048 keys
 constexpr int kCountSlots = 1 << kCountSlotBits;
 
 // count[t] = distinct keys of tile t (its rows, for a tile solved apart).
+// Warp 0 lays the tile's slices end to end (a prefix over their lengths)
+// while the others clear the table; then every thread takes kCountPer rows
+// of the tile, finds each row's slice by binary search over the prefix and
+// issues all its key loads before inserting any, so a tile costs about one
+// memory round trip.
+constexpr int kCountPer = (kMergeTile + kCountThreads - 1) / kCountThreads;
 __global__ void __launch_bounds__(kCountThreads) k_merge_count(const Chunk* __restrict__ chunks,
                                                                const long long* __restrict__ tslo, RunSet runs,
                                                                long long* count, int* err) {
   __shared__ unsigned long long tab[kCountSlots];
-  __shared__ int s_cnt, s_top;
+  __shared__ int pre[kMaxFanIn + 1];       // tile rows before slice r
+  __shared__ long long slo[kMaxFanIn];     // first row of slice r in its run
+  __shared__ int s_cnt, s_top, s_n;
   const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const Chunk ch = chunks[t];
   if (ch.kind == CH_COPY) {
     if (tid == 0) count[t] = ch.hi - ch.lo;
     return;
   }
-  for (int i = tid; i < kCountSlots; i += kCountThreads) tab[i] = ~0ull;  // empty; key ~0 is counted apart
-  if (tid == 0) {
-    s_cnt = 0;
-    s_top = 0;
+  const int k = runs.k;
+  if (w == 0) {
+    int run = 0;
+    for (int b = 0; b < k; b += 32) {
+      const int r = b + lane;
+      long long lo = 0, hi = 0;
+      if (r < k) {
+        lo = tslo[(long long)t * k + r];
+        hi = tslo[(long long)(t + 1) * k + r];
+      }
+      const int len = (int)min(max(hi - lo, 0ll), (long long)kMergeTile + 1);
+      int x = len;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (r < k) {
+        slo[r] = lo;
+        pre[r + 1] = run + x;
+      }
+      run = min(run + __shfl_sync(0xffffffffu, x, 31), kMergeTile + 1);
+    }
+    if (lane == 0) {
+      pre[0] = 0;
+      s_n = run;
+      s_cnt = 0;
+      s_top = 0;
+    }
+  } else {
+    for (int i = tid - 32; i < kCountSlots; i += kCountThreads - 32) tab[i] = ~0ull;  // empty; key ~0 apart
   }
   __syncthreads();
-  const int k = runs.k;
-  int mine = 0;
-  for (int r = w; r < k; r += kCountThreads / 32) {  // a warp per slice
-    const long long lo = tslo[(long long)t * k + r], hi = tslo[(long long)(t + 1) * k + r];
-    const long long* keys = runs.ptrs[(long long)r * (1 + runs.ncols)];
-    for (long long i = lo + lane; i < hi; i += 32) {
-      const unsigned long long key = (unsigned long long)__ldg(keys + i);
-      if (key == ~0ull) {
-        if (atomicExch(&s_top, 1) == 0) ++mine;
-        continue;
+  const int n = s_n;
+  if (n > kMergeTile) {  // the planner never makes such tiles
+    if (tid == 0) err_raise(err, ERR_INTERNAL);
+    return;
+  }
+  unsigned long long key[kCountPer];
+#pragma unroll
+  for (int j = 0; j < kCountPer; ++j) {
+    const int i = tid + j * kCountThreads;
+    key[j] = ~0ull;
+    if (i < n) {
+      int lo = 0, hi = k - 1;  // the slice r with pre[r] <= i < pre[r + 1]
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= i) lo = mid; else hi = mid - 1;
       }
-      unsigned slot = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCountSlotBits));
-      int probes = 0;
-      while (true) {  // a tile has at most 2,048 keys in 4,096 slots: a free slot is near
-        const unsigned long long old = atomicCAS(&tab[slot], ~0ull, key);
-        if (old == ~0ull) { ++mine; break; }
-        if (old == key) break;
-        slot = (slot + 1) & (kCountSlots - 1);
-        if (++probes == kCountSlots) {  // the planner never makes such tiles
-          err_raise(err, ERR_INTERNAL);
-          break;
-        }
+      key[j] = (unsigned long long)__ldg(runs.ptrs[(long long)lo * (1 + runs.ncols)] + slo[lo] + (i - pre[lo]));
+    }
+  }
+  int mine = 0;
+#pragma unroll
+  for (int j = 0; j < kCountPer; ++j) {
+    if (tid + j * kCountThreads >= n) continue;
+    const unsigned long long kk = key[j];
+    if (kk == ~0ull) {
+      if (atomicExch(&s_top, 1) == 0) ++mine;
+      continue;
+    }
+    unsigned slot = (unsigned)((kk * 0x9E3779B97F4A7C15ull) >> (64 - kCountSlotBits));
+    int probes = 0;
+    while (true) {  // a tile has at most kMergeTile keys in twice as many slots: a free slot is near
+      const unsigned long long old = atomicCAS(&tab[slot], ~0ull, kk);
+      if (old == ~0ull) { ++mine; break; }
+      if (old == kk) break;
+      slot = (slot + 1) & (kCountSlots - 1);
+      if (++probes == kCountSlots) {  // cannot happen with at most half the slots taken
+        err_raise(err, ERR_INTERNAL);
+        break;
       }
     }
   }
