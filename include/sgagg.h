@@ -170,11 +170,19 @@ typedef enum {
                                      the in-memory index.  Default: estimated on the key
                                      sample so that the range holds (1 - f/F) M keys */
     SGAGG_OPT_HYBRID_LAST_AUTO = 15, /* policy 2: back to the estimated resident range */
-    SGAGG_OPT_MERGE_COPY = 16     /* how the wide merge stages run slices in shared memory:
+    SGAGG_OPT_MERGE_COPY = 16,    /* how the wide merge stages run slices in shared memory:
                                      0 (default) one bulk copy per slice and column
                                      (cp.async.bulk), issued by all worker warps; 1 16-byte
                                      cp.async copies by every worker thread; 2 the bulk copies
                                      issued by the control warp alone.  Same result. */
+    SGAGG_OPT_PREFOLD_BINS = 17,  /* tile pre-aggregation (before runs of partial rows are
+                                     sorted): 0 (default) bins a tile's rows by key range, 1 by
+                                     a hash of the key.  Equal keys are adjacent either way;
+                                     hashing keeps keys crowded at one end of their range
+                                     (e.g. Zipf ranks used as keys) from filling a few bins.
+                                     Same result. */
+    SGAGG_OPT_PREFOLD_ROWS = 18   /* rows per pre-aggregation tile of sgagg_aggregate_batched,
+                                     1024..8192 (default 8192).  Same result. */
 } sgagg_option;
 
 /*

@@ -358,6 +358,113 @@ __global__ void k_plan_finish(int nb, int fine_shift, const long long* bstart, C
     atomicMax(reinterpret_cast<unsigned long long*>(&info->max_chunk), (unsigned long long)mx);
 }
 
+// The same plan in one launch of one block, for at most kPlanSmallMax
+// buckets (small batches and merges, where launches, not rows, cost).  With
+// thist given it first does k_tilescan's work (per-tile offsets in place,
+// bucket totals into w); then the sums and their prefixes, the chunk starts,
+// the chunk list and the finishing pass, separated by barriers.
+constexpr int kPlanSmallThreads = 1024;
+constexpr int kPlanSmallMax = 8192;
+
+__global__ void __launch_bounds__(kPlanSmallThreads)
+k_plan_small(unsigned int* thist, int ntiles, long long* w, int nb, int fine_shift, long long target, long long big,
+             long long cap, long long* bstart, Chunk* chunks, int* big_list, PlanInfo* info) {
+  __shared__ long long red[32];
+  __shared__ long long s_tot[3];
+  const int lane = threadIdx.x & 31;
+  if (thist) {  // a warp per bucket
+    for (int d = threadIdx.x >> 5; d < nb; d += kPlanSmallThreads / 32) {
+      unsigned int* row = thist + (long long)d * ntiles;
+      unsigned int run = 0;
+      for (int b = 0; b < ntiles; b += 32) {
+        const int t = b + lane;
+        const unsigned int v = t < ntiles ? row[t] : 0u;
+        unsigned int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (t < ntiles) row[t] = run + x - v;
+        run += __shfl_sync(0xffffffffu, x, 31);
+      }
+      if (lane == 0) w[d] = run;
+    }
+    __syncthreads();
+  }
+  const int sub = (nb + kPlanSmallThreads - 1) / kPlanSmallThreads;
+  const int d0 = min(nb, (int)threadIdx.x * sub), d1 = min(nb, d0 + sub);
+  long long ta = 0, tb = 0, tc = 0;
+  for (int d = d0; d < d1; ++d) {
+    const long long x = w[d];
+    ta += x;
+    if (x > cap) tc += 1;
+    if (x <= big) tb += x;
+  }
+  const long long A0 = block_excl_ll(ta, red);
+  const long long B0 = block_excl_ll(tb, red);
+  long long nbig = block_excl_ll(tc, red);
+  bool pbig;
+  long long pq;
+  plan_prev(w, d0, B0, big, target, &pbig, &pq);
+  long long st = 0;
+  {
+    bool pb2 = pbig;
+    long long pq2 = pq, pB2 = B0;
+    for (int d = d0; d < d1; ++d) {
+      const long long x = w[d];
+      st += plan_is_start(x, big, pB2, target, &pb2, &pq2);
+      if (x <= big) pB2 += x;
+    }
+  }
+  const long long cex = block_excl_ll(st, red);
+  if (threadIdx.x == kPlanSmallThreads - 1) {
+    s_tot[0] = A0 + ta;
+    s_tot[1] = nbig + tc;
+    s_tot[2] = cex + st;
+  }
+  long long cidx = cex - 1, pA = A0, pB = B0;
+  for (int d = d0; d < d1; ++d) {
+    const long long x = w[d];
+    bstart[d] = pA;
+    if (plan_is_start(x, big, pB, target, &pbig, &pq)) {
+      ++cidx;
+      chunks[cidx].pad = d;
+      chunks[cidx].kind = x > cap ? CH_COPY : CH_NORMAL;
+      if (x > cap) big_list[nbig++] = (int)cidx;
+    }
+    if (x <= big) pB += x;
+    pA += x;
+  }
+  __syncthreads();  // every chunk's first bucket and every bucket start is written
+  const int nc = (int)s_tot[2];
+  if (threadIdx.x == 0) {
+    bstart[nb] = s_tot[0];
+    info->total = s_tot[0];
+    info->n_big = (int)s_tot[1];
+    info->n_chunks = nc;
+  }
+  long long mx = 0;
+  for (int c = threadIdx.x; c < nc; c += kPlanSmallThreads) {
+    const int dlo = chunks[c].pad;
+    const int dhi = (c + 1 < nc) ? chunks[c + 1].pad : nb;
+    Chunk& ch = chunks[c];
+    ch.lo = bstart[dlo];
+    ch.hi = dhi == nb ? s_tot[0] : bstart[dhi];
+    ch.f_lo = dlo << fine_shift;
+    ch.f_hi = dhi << fine_shift;
+    if (ch.kind == CH_NORMAL) mx = max(mx, ch.hi - ch.lo);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if (lane == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m = 0;
+    for (int k = 0; k < kPlanSmallThreads / 32; ++k) m = max(m, red[k]);
+    info->max_chunk = m;
+  }
+}
+
 // Scatter rows [0, n) of src into buckets: row i goes to
 // bstart[d] + (its tile's offset in bucket d) + (rank inside the tile).
 // Output rows are 1 + ncols int64 words: key, then the carried columns.

@@ -58,6 +58,9 @@ struct InstSet {
   int8_t colsel[kMaxCols];   // carried column c -> the instance's payload column
   unsigned long long* kmin;  // per instance: least key (preset ~0), or null
   unsigned long long* kmax;  // per instance: greatest key (preset 0)
+  int grouped;               // MODE_TILES / MODE_INST tile pre-aggregation: equal keys
+                             // need only be adjacent (partial rows are sorted later),
+                             // so the chunk is binned by a hash of the key
 };
 
 struct Chunk {
@@ -331,9 +334,18 @@ __device__ __forceinline__ void insertion_sort_bin(const SortSmem& s, int st, in
 __shared__ unsigned long long g_kmin, g_kmax;
 __shared__ int g_maxbin;
 
+// Multiplicative (Fibonacci) hashing of a key to one of kBins bins.
+__device__ __forceinline__ int hash_bin(unsigned long long key) {
+  return (int)((key * 0x9E3779B97F4A7C15ull) >> (64 - kBinBits));
+}
+
 // Sort s.idx by key (the keys just loaded; lmin / lmax: the thread's least
 // and greatest); returns whether a key group may hold more than 32 rows.
-__device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, unsigned long long lmax) {
+// hashed: bin by hash_bin instead of key range -- equal keys still end up
+// adjacent (each bin is sorted), but bins are not in key order; a skewed key
+// distribution then spreads over the bins instead of crowding a few.
+__device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, unsigned long long lmax,
+                           bool hashed = false) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // zero the bins while the key range is combined: one barrier for the
   // loaded keys, the range and the bins
@@ -362,7 +374,7 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
   for (int j = 0; j < EPT; ++j) {
     const int i = threadIdx.x + j * kThreads;
     if (i < n) {
-      const int b = (int)((s.keys[i] - kmin) >> sh);
+      const int b = hashed ? hash_bin(s.keys[i]) : (int)((s.keys[i] - kmin) >> sh);
       const unsigned sft = (b & 1) * 16;
       const unsigned old = atomicAdd(&s.bins[b >> 1], 1u << sft);
       br[j] = ((unsigned)b << 16) | ((old >> sft) & 0xFFFFu);
@@ -420,7 +432,7 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
   uint16_t* flist = s.whist + kBins / 16 * 2;             // [kFlagList] the flagged bins
   constexpr int kFlagList = kWarps * 256 - kBins / 16 * 2;
   __shared__ int s_nbig, s_over, s_nflag;
-  if (sh != 0) {  // block-uniform
+  if (hashed || sh != 0) {  // block-uniform
     for (int i = threadIdx.x; i < kBins / 32; i += kThreads) flag[i] = 0;
     if (threadIdx.x == 0) {
       s_nbig = 0;
@@ -434,7 +446,7 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
     if (i < n) s.idx[(int)bin_get(s.bins, (int)(br[j] >> 16)) + (int)(br[j] & 0xFFFFu)] = (uint16_t)i;
   }
   __syncthreads();
-  if (sh == 0) return maxbin > 32;  // every bin is one key value
+  if (!hashed && sh == 0) return maxbin > 32;  // every bin is one key value
   // Bins are key ranges in key order, so two adjacent positions out of key
   // order lie in one bin: only the bins holding such an inversion need
   // sorting.  One pass over adjacent positions flags them (a bit per bin)
@@ -444,8 +456,10 @@ __device__ bool chunk_sort(const SortSmem& s, int n, unsigned long long lmin, un
     const unsigned long long a = p < n ? s.keys[s.idx[p]] : ~0ull;
     unsigned long long b = __shfl_down_sync(0xffffffffu, a, 1);
     if (lane == 31 && p + 1 < n) b = s.keys[s.idx[p + 1]];
-    if (p + 1 < n && a > b) {
-      const int bin = (int)((a - kmin) >> sh);
+    // (range bins are in key order: an inversion lies inside one bin; hash
+    // bins are compared as well)
+    if (p + 1 < n && a > b && (!hashed || hash_bin(a) == hash_bin(b))) {
+      const int bin = hashed ? hash_bin(a) : (int)((a - kmin) >> sh);
       const unsigned bit = 1u << (bin & 31);
       if (!(atomicOr(&flag[bin >> 5], bit) & bit)) {
         const int q = atomicAdd(&s_nflag, 1);
@@ -1093,13 +1107,14 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
   }
   unsigned long long lmin = ~0ull, lmax = 0ull;
   load_keys<MODE>(s, src, runs, cv, &lmin, &lmax);
-  const bool bigs = chunk_sort(s, cv.n, lmin, lmax);  // its first barrier completes the load
+  // its first barrier completes the load
+  const bool bigs = chunk_sort(s, cv.n, lmin, lmax, (MODE == MODE_TILES || MODE == MODE_INST) && is.grouped);
   if (MODE == MODE_INST && is.kmin && threadIdx.x == 0 && cv.n > 0) {
-    // key range of the instance (its tiles' sorted ends), for the digit
-    // that partitions the partial rows
+    // key range of the instance (the tile's least and greatest keys, all
+    // of one instance), for the digit that partitions the partial rows
     const unsigned long long m = (1ull << is.key_bits) - 1;
-    atomicMin(is.kmin + ch.pad, s.keys[s.idx[0]] & m);
-    atomicMax(is.kmax + ch.pad, s.keys[s.idx[cv.n - 1]] & m);
+    atomicMin(is.kmin + ch.pad, g_kmin & m);
+    atomicMax(is.kmax + ch.pad, g_kmax & m);
   }
   if (bigs) fold_sorted<MODE, KS, true>(s, src, runs, cv, fd, dst, lb, ch, cid, &s_base);
   else fold_sorted<MODE, KS, false>(s, src, runs, cv, fd, dst, lb, ch, cid, &s_base);

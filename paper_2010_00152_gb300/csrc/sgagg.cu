@@ -124,6 +124,8 @@ struct sgagg_ctx {
   int merge_threads = 0;         // threads of a merge CTA (128, 256, 512; 0 = default)
   int merge_copy = 0;            // merge staging: 0 bulk copies by the workers, 1 16-byte cp.async,
                                  // 2 bulk copies by the control warp
+  int prefold_bins = 0;          // tile pre-aggregation binning: 0 key range, 1 hash of the key
+  long long prefold_rows = kTileCap;  // rows per pre-aggregation tile of a batched call
   int hybrid_fanin = 10;         // hybrid run generation (policy 2): F
   int hybrid_f = -1;             // f (-1: from the estimated output size)
   bool hybrid_last_given = false;
@@ -702,12 +704,26 @@ struct Solver {
   int n_state;
 };
 
-// The chunk planner over nb bucket counts w: six small launches over up to
-// 1024 blocks (k_plan_*), one bucket per thread up to 2^18 buckets.
-sgagg_status run_plan(sgagg_t h, const long long* w, int nb, int fine_shift, long long* bstart, Chunk* chunks,
+// The chunk planner over nb bucket counts w: up to kPlanSmallMax buckets one
+// launch of one block (k_plan_small, which with thist given also turns the
+// per-tile histograms into per-tile offsets and fills w), else six small
+// launches over up to 1024 blocks (k_plan_*), one bucket per thread up to
+// 2^18 buckets (after k_tilescan when thist is given).
+sgagg_status run_plan(sgagg_t h, long long* w, int nb, int fine_shift, long long* bstart, Chunk* chunks,
                       int* biglist, PlanInfo* info, long long cap = kTileCap, long long target = kChunkTarget,
-                      long long big = kBigBucket) {
+                      long long big = kBigBucket, unsigned int* thist = nullptr, int ntiles = 0) {
   cudaStream_t st = h->stream;
+  if (nb <= kPlanSmallMax) {
+    k_plan_small<<<1, kPlanSmallThreads, 0, st>>>(thist, ntiles, w, nb, fine_shift, target, big, cap, bstart, chunks,
+                                                  biglist, info);
+    CU(cudaGetLastError());
+    return SGAGG_OK;
+  }
+  if (thist) {
+    k_tilescan<<<(nb * 32 + 255) / 256, 256, 0, st>>>(thist, nb, ntiles, w);
+    h->st.class_launches[SGAGG_K_PLAN] += 1;
+    h->st.kernel_launches += 1;
+  }
   const int sub = std::max(1, (nb + kPlanThreads * 1024 - 1) / (kPlanThreads * 1024));
   const int per = sub * kPlanThreads;
   const int g = (nb + per - 1) / per;
@@ -762,8 +778,10 @@ sgagg_status prefold(sgagg_t h, RowSrc* src, long long* n, FoldDesc* fd, int for
     RunSet rs{};
     CopySrc cs{};
     long long* tot = &dsmall(h)->pftot;
+    InstSet grp{};
+    grp.grouped = h->prefold_bins;
     TRY(launch_sortfold<MODE_TILES>(h, SGAGG_K_PREFOLD, nullptr, (int)ntile, *n, *src, rs, cs, *fd, o,
-                                    nullptr, tot));
+                                    nullptr, tot, 0, grp));
     HostSmall* hs = hsmall(h);
     TRY(sync_read(h, &hs->v[0], tot, 8));
     TRY(check_device_err(h));
@@ -944,12 +962,9 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     kend(h);
     kbytes(h, SGAGG_K_HIST, n * (srb - 8ll * C) + (long long)nb * ntiles * 4);
     kbegin(h, SGAGG_K_PLAN);
-    k_tilescan<<<(nb * 32 + 255) / 256, 256, 0, h->stream>>>(P<unsigned int>(h->thist[depth]), nb, ntiles,
-                                                           P<long long>(h->btot[depth]));
-    kend(h);
-    kbegin(h, SGAGG_K_PLAN);
     TRY(run_plan(h, P<long long>(h->btot[depth]), nb, dig.ebits, P<long long>(h->bstart[depth]),
-                 P<Chunk>(h->chunks[depth]), P<int>(h->biglist[depth]), &ds->info));
+                 P<Chunk>(h->chunks[depth]), P<int>(h->biglist[depth]), &ds->info, kTileCap, kChunkTarget,
+                 kBigBucket, P<unsigned int>(h->thist[depth]), ntiles));
     kend(h);
     kbytes(h, SGAGG_K_PLAN, (long long)nb * ntiles * 8 + (long long)nb * (8 + 8 + sizeof(Chunk)));
     kbegin(h, SGAGG_K_SCATTER);
@@ -2139,6 +2154,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
   is.key_bits = key_bits;
   is.kmin = kmin_d;
   is.kmax = kmax_d;
+  is.grouped = h->prefold_bins;
   FoldDesc fd{};
   fd.n_state = S;
   int colmap[1024];
@@ -2253,10 +2269,10 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
     }
     std::vector<Chunk> tiles;
     for (int i = i0; i < i1; ++i)
-      for (long long lo = 0; inst[i].n > kTileCap && lo < inst[i].n; lo += kTileCap) {
+      for (long long lo = 0; inst[i].n > kTileCap && lo < inst[i].n; lo += h->prefold_rows) {
         Chunk c{};
         c.lo = lo;
-        c.hi = std::min<long long>(inst[i].n, lo + kTileCap);
+        c.hi = std::min<long long>(inst[i].n, lo + h->prefold_rows);
         c.kind = CH_NORMAL;
         c.pad = i;
         tiles.push_back(c);
@@ -2599,6 +2615,14 @@ sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
     case SGAGG_OPT_MERGE_THREADS:
       if (value != 0 && value != 256) return fail(h, SGAGG_EINVAL, "merge threads must be 0 or 256");
       h->merge_threads = (int)value;
+      return SGAGG_OK;
+    case SGAGG_OPT_PREFOLD_BINS:
+      if (value != 0 && value != 1) return fail(h, SGAGG_EINVAL, "prefold bins must be 0 or 1");
+      h->prefold_bins = (int)value;
+      return SGAGG_OK;
+    case SGAGG_OPT_PREFOLD_ROWS:
+      if (value < 1024 || value > kTileCap) return fail(h, SGAGG_EINVAL, "prefold rows must be 1024..8192");
+      h->prefold_rows = value;
       return SGAGG_OK;
     default: return fail(h, SGAGG_EINVAL, "unknown option");
   }

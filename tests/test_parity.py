@@ -204,6 +204,19 @@ def test_prefold_switch_invariant(prefold):
     check(c["key_cols"], c["payload"], c["aggs"], M=100_000, prefold=prefold)
 
 
+@pytest.mark.parametrize("bins", [0, 1])
+def test_prefold_bins_invariant(bins):
+    """Tile pre-aggregation binned by key range or by a hash of the key, on
+    Zipf ranks used as keys (the frequent keys crowd the low end of the
+    range, so range bins there hold many keys): same result."""
+    n = 200_000
+    keys = datagen.zipf_ranks(21, 1, n, 300_000).to(torch.int64).view(torch.uint64)
+    pay = [datagen.uniform_int(21, 2, n, -1000, 1000)]
+    aggs = [(0, 0), (1, 0), (2, 0), (3, 0)]
+    st, _ = check([keys], pay, aggs, M=100_000, prefold=1, prefold_bins=bins)
+    assert st["prefold_passes"] >= 1
+
+
 @pytest.mark.parametrize("bits", [1, 4, 9, 15])
 def test_radix_bits_invariant(bits):
     c = datagen.config1(n=300_000, seed=8, D=200_000)
@@ -356,6 +369,26 @@ def test_batched_matches_oracle(key_dtype):
         np.testing.assert_array_equal(to_np(r[0]), rk[0])
         for a in range(len(aggs)):
             np.testing.assert_array_equal(to_np(r[1][a]), ra[a])
+
+
+@pytest.mark.parametrize("opts", [dict(prefold_bins=1), dict(prefold_rows=1024), dict(prefold_rows=3000)])
+def test_batched_prefold_options(opts):
+    """The batched call with hash-binned or smaller pre-aggregation tiles:
+    every instance still equals its own oracle result."""
+    sizes = [8193, 20_000, 70_001, 150_000, 9000]
+    domains = [20_000, 5, 100_000, 1_000_000, 60_000]
+    insts = _batched_case(4, sizes, domains)
+    aggs = [(0, 0), (1, 0), (2, 0), (3, 0)]
+    agg = sgagg.Aggregator(1 << 20, **opts)
+    try:
+        res = agg.aggregate_batched([(k.to(DEV), [p.to(DEV) for p in pay]) for k, pay in insts], aggs)
+    finally:
+        agg.close()
+    for (k, pay), r in zip(insts, res):
+        rk, ra = oracle_run([k], pay, aggs)
+        np.testing.assert_array_equal(to_np(r[0]), rk[0])
+        for j in range(len(aggs)):
+            np.testing.assert_array_equal(to_np(r[1][j]), ra[j])
 
 
 def test_batched_clustered_instances():
