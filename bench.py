@@ -14,7 +14,10 @@ host-buffer entry point (pinned inputs copied in and results copied out
 inside the timed region).  `roofline` = the dominant kernel class's
 compulsory bytes per launch / its average CUDA-event duration, against the
 measured HBM copy bandwidth.  `cpu_baseline` = the CPU oracle (sort + fold,
-one thread) on a bounded sample of the same workload.
+one thread) on a bounded sample of the same workload.  The default run adds
+three sub-objects measured on the same GPU afterwards: `small` (latency of a
+1M-row call with 16 runs), `batched` (4,096 instances in one call against one
+call per instance) and `served` (a Poisson request stream).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config c3|c2|c1|c4|c5]
   python bench.py --impl reference     # the oracle arm (CPU, bounded samples)
@@ -224,6 +227,56 @@ def run_reference(args):
             "e2e": {"value": val, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def bench_small(args, dev, steps=50, warmup=10):
+    """Config 1 (1M rows, 16 runs + wide merge): latency of one call, each
+    call ending with the host reading the row count, as a caller would.
+    Returns the sub-object (a dict)."""
+    import torch
+    from paper_2010_00152_gb300 import sgagg
+    w = make_workload("c1", dev)
+    n = int(w["key_cols"][0].numel())
+    M = int(w["M"])
+    aggs = w["aggs"]
+    ok = [torch.empty(n, dtype=k.dtype, device=dev) for k in w["key_cols"]]
+    oa = [torch.empty(n, dtype=torch.int64, device=dev) for _ in aggs]
+    stream = torch.cuda.current_stream(dev)
+    agg = sgagg.Aggregator(M)
+
+    def call():
+        agg.aggregate(w["key_cols"], w["payload"], aggs, capacity=n, out=(ok, oa), sync=False)
+        return agg.rows()
+
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rows = call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
+    st = agg.stats()
+    agg.close()
+    agg = sgagg.Aggregator(M, timing=1)  # one more call for the per-class device times
+    call()
+    stt = agg.stats()
+    agg.close()
+    return {"metric": "ms per call (small config)", "value": ms, "unit": "ms", "higher_is_better": False,
+            "steps": steps, "warmup": warmup, "rows_per_s": n / (ms / 1e3),
+            "config": {"workload": WORKLOADS["c1"]["desc"], "rows": n, "memory_budget_rows": M},
+            "timing": "CUDA events around the calls; every call reads its row count on the host",
+            "out_rows": rows, "runs": st["runs"], "one_pass": st["one_pass"],
+            "gpu_launches_per_call": st["kernel_launches"],
+            "class_ms": {k: round(v["ms"], 4) for k, v in stt["kernels"].items() if v["launches"]},
+            "clocks": clk}
 
 
 def bench_batched(args, dev, steps=None, warmup=None, plain_steps=None):
@@ -455,7 +508,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-sub", action="store_true", help="skip the batched and served sub-objects")
+    ap.add_argument("--no-sub", action="store_true", help="skip the small, batched and served sub-objects")
     ap.add_argument("--sub-requests", type=int, default=4000,
                     help="requests of the served sub-object's Poisson replays")
     ap.add_argument("--instances", type=int, default=None, help="c4: instance count")
@@ -561,8 +614,9 @@ def main():
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(name)
 
-    # the batched (4,096 instances) and served (Poisson request stream)
-    # workloads on the same GPU, after the main workload's buffers are freed
+    # the small (1M rows, latency), batched (4,096 instances) and served
+    # (Poisson request stream) workloads on the same GPU, after the main
+    # workload's buffers are freed
     sub = {}
     temp_bytes = agg.temp_bytes()
     if name == "c3" and world == 1 and not args.no_sub:
@@ -570,6 +624,7 @@ def main():
         agg = None
         del w, ok, oa
         torch.cuda.empty_cache()
+        sub["small"] = bench_small(args, dev)
         sub["batched"] = bench_batched(args, dev, steps=3, warmup=1, plain_steps=1)
         sub["served"] = bench_serving(args, dev, count=args.sub_requests, load_factors=(0.5, 0.8, 1.0))
 

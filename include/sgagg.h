@@ -112,6 +112,9 @@ typedef struct {
     int64_t resident_rows;
     int64_t resident_keys;
     int64_t hybrid_f;
+    /* 1 when the runs of all batches were generated in one pass per step
+     * (small batches, SGAGG_OPT_ONE_PASS), else 0. */
+    int64_t one_pass;
 } sgagg_stats_t;
 
 /* Kernel classes of sgagg_stats_t. */
@@ -181,8 +184,15 @@ typedef enum {
                                      hashing keeps keys crowded at one end of their range
                                      (e.g. Zipf ranks used as keys) from filling a few bins.
                                      Same result. */
-    SGAGG_OPT_PREFOLD_ROWS = 18   /* rows per pre-aggregation tile of sgagg_aggregate_batched,
+    SGAGG_OPT_PREFOLD_ROWS = 18,  /* rows per pre-aggregation tile of sgagg_aggregate_batched,
                                      1024..8192 (default 8192).  Same result. */
+    SGAGG_OPT_ONE_PASS = 19       /* 1 (default): when the input is several batches of more
+                                     than one chunk each, at most 2^24 rows in all and few
+                                     buckets, the runs of all batches are generated in one
+                                     pass per step (one histogram, plan, scatter and
+                                     sort+fold launch for all of them) instead of one batch
+                                     at a time; 0: always a batch at a time.  The runs are
+                                     the same. */
 } sgagg_option;
 
 /*

@@ -162,6 +162,13 @@ struct Digit {
   int seg_shift;            // with seg: segment index = key >> seg_shift
   int seg_n;                // segments in the table
   const SegEntry* seg;      // null: one linear digit over the whole key range
+  // Several batches partitioned in one launch (brows > 0): launch tile t is
+  // tile t % btiles of batch t / btiles (rows [b * brows, (b + 1) * brows)),
+  // and its buckets are b << bbits plus the digit, so every batch keeps
+  // buckets of its own.
+  long long brows;
+  int btiles;
+  int bbits;
 };
 
 // SEG: the digit has a segment table (kernels are compiled for either form,

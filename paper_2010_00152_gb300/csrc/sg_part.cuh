@@ -55,6 +55,22 @@ __device__ __forceinline__ void tile_range(long long n, int ntiles, int t, long 
   *hi = min(n, *lo + per);
 }
 
+// Rows [lo, hi) of launch tile t, and the bucket offset of its batch (0
+// unless the digit partitions several batches at once).
+__device__ __forceinline__ unsigned tile_rows(long long n, int ntiles, const Digit& dig, int t, long long* lo,
+                                              long long* hi) {
+  if (dig.brows == 0) {
+    tile_range(n, ntiles, t, lo, hi);
+    return 0u;
+  }
+  const int b = t / dig.btiles;
+  const long long b0 = (long long)b * dig.brows;
+  tile_range(max(0ll, min(n, b0 + dig.brows) - b0), dig.btiles, t % dig.btiles, lo, hi);
+  *lo += b0;
+  *hi += b0;
+  return (unsigned)b << dig.bbits;
+}
+
 // Digit of one partitioning level: bits [dshift, dshift + log2(nb)) of the
 // coarse digit.
 template <bool SEG>
@@ -75,7 +91,8 @@ k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsig
   for (int d = threadIdx.x; d < nh; d += blockDim.x) sh_hist[d] = 0;
   __syncthreads();
   long long lo, hi;
-  tile_range(n, ntiles, blockIdx.x, &lo, &hi);
+  const unsigned boff = tile_rows(n, ntiles, dig, blockIdx.x, &lo, &hi);
+  const int nlev = dig.brows ? (1 << dig.bbits) : nb;  // buckets of one batch
   constexpr int U = 8;  // independent loads in flight per thread
   for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += (long long)U * blockDim.x) {
     unsigned long long k[U];
@@ -87,7 +104,7 @@ k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsig
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       long long i = i0 + (long long)u * blockDim.x;
-      if (i < hi) atomicAdd(&mine[level_digit<SEG>(dig, k[u], dshift, nb)], 1u);
+      if (i < hi) atomicAdd(&mine[boff + level_digit<SEG>(dig, k[u], dshift, nlev)], 1u);
     }
   }
   __syncthreads();
@@ -368,7 +385,10 @@ constexpr int kPlanSmallMax = 8192;
 
 __global__ void __launch_bounds__(kPlanSmallThreads)
 k_plan_small(unsigned int* thist, int ntiles, long long* w, int nb, int fine_shift, long long target, long long big,
-             long long cap, long long* bstart, Chunk* chunks, int* big_list, PlanInfo* info) {
+             long long cap, long long* bstart, Chunk* chunks, int* big_list, PlanInfo* info, int seg_bits) {
+  // seg_bits > 0: buckets come in batches of 2^seg_bits (a digit over several
+  // batches); a chunk never spans two, and its fine range is its batch's
+  const int segm = seg_bits ? (1 << seg_bits) - 1 : 0;
   __shared__ long long red[32];
   __shared__ long long s_tot[3];
   const int lane = threadIdx.x & 31;
@@ -412,7 +432,8 @@ k_plan_small(unsigned int* thist, int ntiles, long long* w, int nb, int fine_shi
     long long pq2 = pq, pB2 = B0;
     for (int d = d0; d < d1; ++d) {
       const long long x = w[d];
-      st += plan_is_start(x, big, pB2, target, &pb2, &pq2);
+      const bool s0 = plan_is_start(x, big, pB2, target, &pb2, &pq2);
+      st += (s0 || (segm && d > 0 && (d & segm) == 0)) ? 1 : 0;
       if (x <= big) pB2 += x;
     }
   }
@@ -426,7 +447,8 @@ k_plan_small(unsigned int* thist, int ntiles, long long* w, int nb, int fine_shi
   for (int d = d0; d < d1; ++d) {
     const long long x = w[d];
     bstart[d] = pA;
-    if (plan_is_start(x, big, pB, target, &pbig, &pq)) {
+    const bool s0 = plan_is_start(x, big, pB, target, &pbig, &pq);
+    if (s0 || (segm && d > 0 && (d & segm) == 0)) {
       ++cidx;
       chunks[cidx].pad = d;
       chunks[cidx].kind = x > cap ? CH_COPY : CH_NORMAL;
@@ -450,8 +472,9 @@ k_plan_small(unsigned int* thist, int ntiles, long long* w, int nb, int fine_shi
     Chunk& ch = chunks[c];
     ch.lo = bstart[dlo];
     ch.hi = dhi == nb ? s_tot[0] : bstart[dhi];
-    ch.f_lo = dlo << fine_shift;
-    ch.f_hi = dhi << fine_shift;
+    const int seg0 = segm ? (dlo & ~segm) : 0;  // the batch's first bucket (0 without batches)
+    ch.f_lo = (dlo - seg0) << fine_shift;
+    ch.f_hi = (dhi - seg0) << fine_shift;
     if (ch.kind == CH_NORMAL) mx = max(mx, ch.hi - ch.lo);
   }
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -478,7 +501,7 @@ k_scatter(RowSrc src, long long n, Digit dig, int nb, int ntiles, const unsigned
     cursor[d] = (unsigned int)(bstart[d] + thist[(long long)d * ntiles + blockIdx.x]);
   __syncthreads();
   long long lo, hi;
-  tile_range(n, ntiles, blockIdx.x, &lo, &hi);
+  const unsigned boff = tile_rows(n, ntiles, dig, blockIdx.x, &lo, &hi);
   const int W = 1 + src.ncols;
   constexpr int U = 8;  // independent loads in flight per thread
   if (W == 2) {
@@ -494,7 +517,7 @@ k_scatter(RowSrc src, long long n, Digit dig, int nb, int ntiles, const unsigned
       for (int u = 0; u < U; ++u) {
         long long i = i0 + (long long)u * blockDim.x;
         if (i < hi) {
-          unsigned pos = atomicAdd(&cursor[coarse_digit<SEG>(dig, k[u])], 1u);
+          unsigned pos = atomicAdd(&cursor[boff + coarse_digit<SEG>(dig, k[u])], 1u);
           // one 16-byte store: key + the one carried column
           longlong2 r;
           r.x = (long long)k[u];
@@ -516,13 +539,20 @@ k_scatter(RowSrc src, long long n, Digit dig, int nb, int ntiles, const unsigned
     for (int u = 0; u < U; ++u) {
       long long i = i0 + (long long)u * blockDim.x;
       if (i < hi) {
-        unsigned pos = atomicAdd(&cursor[coarse_digit<SEG>(dig, k[u])], 1u);
+        unsigned pos = atomicAdd(&cursor[boff + coarse_digit<SEG>(dig, k[u])], 1u);
         long long* row = aos + (long long)pos * W;
         row[0] = (long long)k[u];
         for (int c = 0; c < src.ncols; ++c) row[1 + c] = src_col(src, c, i);
       }
     }
   }
+}
+
+// Runs generated in one pass lie back to back; run b ends where its sparse
+// index ends: rs[1 + b] = offs[b * stride + nf] (rs[0] = 0, the first start).
+__global__ void k_run_bounds(const long long* offs, long long stride, int nf, int B, long long* rs) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+    rs[1 + b] = offs[(long long)b * stride + nf];
 }
 
 // Rows of all runs in each fine bucket: sizes[f] = sum_r offs[r][f+1] - offs[r][f].

@@ -93,6 +93,9 @@ struct OutSink {
   long long* cols[kMaxCols];        // one per state column
   long long capacity;               // rows writable (absolute positions < capacity)
   long long* offs;                  // fine-bucket offsets of the run written, or null
+  long long offs_stride;            // > 0: several runs at once (MODE_RANGE); the chunk whose
+  int offs_bbits;                   // first bucket is d writes the offsets of run
+                                    // d >> offs_bbits at offs + run * offs_stride
   Digit dig;
   long long* rows_out;              // MODE_DIRECT: the instance's row count (-1: over capacity)
   unsigned long long* rows_sum;     // MODE_DIRECT: rows of all instances (added), or null
@@ -874,8 +877,12 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
   const long long base =
       MODE == MODE_DIRECT ? direct_base(out, count, s_base) : chunk_base(lb, out, cid, count, s_base);
   if (base < 0) return;
-  if (out.offs && count == 0 && threadIdx.x == 0)
-    for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) out.offs[ff] = base;
+  // the run's sparse index (several runs at once: the chunk's own run's)
+  long long* const offs =
+      (MODE == MODE_RANGE && out.offs && out.offs_stride > 0)
+          ? out.offs + (long long)(ch.pad >> out.offs_bbits) * out.offs_stride : out.offs;
+  if (offs && count == 0 && threadIdx.x == 0)
+    for (int ff = ch.f_lo; ff <= ch.f_hi; ++ff) offs[ff] = base;
   const int ns = fd.n_state;
   // keys, count(*) of raw rows
   {
@@ -902,7 +909,7 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
   // the run's sparse index: offs[f] = rows of this run before the first key
   // with fine digit >= f, for every fine bucket of the chunk's key range (a
   // thread per fine bucket, by binary search over the sorted rows)
-  if (out.offs) {
+  if (offs) {
     for (int f = ch.f_lo + (int)threadIdx.x; f <= ch.f_hi; f += kThreads) {
       int lo = 0, hi = n;  // first sorted position whose fine digit is >= f
       while (lo < hi) {
@@ -911,7 +918,7 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
       }
       const int heads = lo >= n ? count
                                 : (int)hpre[lo >> 5] + __popc(hm[lo >> 5] & ((1u << (lo & 31)) - 1u));
-      out.offs[f] = base + heads;
+      offs[f] = base + heads;
     }
   }
   if (few && threadIdx.x == 0) g_gstart[count] = n;

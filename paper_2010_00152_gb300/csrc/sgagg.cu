@@ -125,6 +125,7 @@ struct sgagg_ctx {
   int merge_copy = 0;            // merge staging: 0 bulk copies by the workers, 1 16-byte cp.async,
                                  // 2 bulk copies by the control warp
   int prefold_bins = 0;          // tile pre-aggregation binning: 0 key range, 1 hash of the key
+  int one_pass = 1;              // small batches: every run in one pass per step (0: a batch at a time)
   long long prefold_rows = kTileCap;  // rows per pre-aggregation tile of a batched call
   int hybrid_fanin = 10;         // hybrid run generation (policy 2): F
   int hybrid_f = -1;             // f (-1: from the estimated output size)
@@ -711,11 +712,13 @@ struct Solver {
 // 2^18 buckets (after k_tilescan when thist is given).
 sgagg_status run_plan(sgagg_t h, long long* w, int nb, int fine_shift, long long* bstart, Chunk* chunks,
                       int* biglist, PlanInfo* info, long long cap = kTileCap, long long target = kChunkTarget,
-                      long long big = kBigBucket, unsigned int* thist = nullptr, int ntiles = 0) {
+                      long long big = kBigBucket, unsigned int* thist = nullptr, int ntiles = 0,
+                      int seg_bits = 0) {
   cudaStream_t st = h->stream;
+  if (seg_bits > 0 && nb > kPlanSmallMax) return fail(h, SGAGG_ECUDA, "batched plan over too many buckets");
   if (nb <= kPlanSmallMax) {
     k_plan_small<<<1, kPlanSmallThreads, 0, st>>>(thist, ntiles, w, nb, fine_shift, target, big, cap, bstart, chunks,
-                                                  biglist, info);
+                                                  biglist, info, seg_bits);
     CU(cudaGetLastError());
     return SGAGG_OK;
   }
@@ -1691,6 +1694,83 @@ sgagg_status lowcard_device(sgagg_t h, const RowSrc& raw, long long n, const Fol
 // batch, Sec. 3 and Sec. 6.1), then one wide merge of all runs into the
 // caller's output at *base_in (Sec. 4; nullptr: 0).  stage_io: src is the
 // host-buffer call's staged input, copied batch by batch.
+// Every batch's run in one pass per step, for small batches (where the
+// launches and host round trips of a batch, not its rows, would set the
+// time): the digit gives each batch buckets of its own (batch << Db plus the
+// key digit), the planner never lets a chunk span two batches, and one
+// sort+fold launch writes the runs back to back, each chunk into its batch's
+// sparse index.  The runs are exactly those a batch at a time would write
+// (each is its batch's distinct keys in key order, folded).  *done stays
+// false, with nothing the caller relies on written, when some bucket is
+// bigger than a chunk; the caller then takes the batches one at a time.
+constexpr long long kOnePassRows = 1ll << 24;
+
+sgagg_status runs_one_pass(sgagg_t h, const RowSrc& src, long long n, long long M, long long B, const FoldDesc& fd,
+                           const Digit& gd, const OutSink& o, long long stride, long long* rs_dev, bool* done) {
+  *done = false;
+  cudaStream_t stream = h->stream;
+  Small* ds = dsmall(h);
+  HostSmall* hs = hsmall(h);
+  const int Db = gd.fbits - gd.ebits;
+  const int nb = (int)(B << Db);
+  const int T = (int)std::max(1ll, std::min((M + 8191) / 8192, (2ll * h->num_sms + B - 1) / B));
+  const int ntiles = (int)(B * T);
+  Digit dig = gd;
+  dig.brows = M;
+  dig.btiles = T;
+  dig.bbits = Db;
+  set_part_attrs();
+  const int W = 1 + src.ncols;
+  const long long srb = src_row_bytes(src);
+  TRY(grow(h, h->scatter[0], (size_t)n * W * 8));
+  TRY(grow(h, h->btot[0], (size_t)nb * 8));
+  TRY(grow(h, h->bstart[0], (size_t)(nb + 1) * 8));
+  TRY(grow(h, h->chunks[0], (size_t)nb * sizeof(Chunk)));
+  TRY(grow(h, h->biglist[0], (size_t)nb * 4));
+  TRY(grow(h, h->thist[0], (size_t)nb * ntiles * 4));
+  kbegin(h, SGAGG_K_HIST);
+  HIST_LAUNCH(k_hist, src, (ntiles, kPartThreads, hist_smem_bytes(nb, kPartThreads), stream),
+              (src, n, dig, 0, nb, ntiles, P<unsigned>(h->thist[0])));
+  kend(h);
+  kbytes(h, SGAGG_K_HIST, n * (srb - 8ll * src.ncols) + (long long)nb * ntiles * 4);
+  kbegin(h, SGAGG_K_PLAN);
+  TRY(run_plan(h, P<long long>(h->btot[0]), nb, dig.ebits, P<long long>(h->bstart[0]), P<Chunk>(h->chunks[0]),
+               P<int>(h->biglist[0]), &ds->info, kTileCap, kChunkTarget, kBigBucket, P<unsigned>(h->thist[0]),
+               ntiles, Db));
+  kend(h);
+  kbytes(h, SGAGG_K_PLAN, (long long)nb * ntiles * 8 + (long long)nb * (8 + 8 + sizeof(Chunk)));
+  TRY(sync_read(h, &hs->info, &ds->info, sizeof(PlanInfo)));
+  const PlanInfo info = hs->info;
+  if (info.n_big > 0 || info.max_chunk > kTileCap) return SGAGG_OK;
+  kbegin(h, SGAGG_K_SCATTER);
+  PART_LAUNCH(k_scatter, (ntiles, kPartThreads, nb * 4, stream),
+              (src, n, dig, nb, ntiles, P<unsigned int>(h->thist[0]), P<long long>(h->bstart[0]),
+               P<long long>(h->scatter[0])));
+  kend(h);
+  kbytes(h, SGAGG_K_SCATTER, n * (srb + 8ll * W) + (long long)nb * ntiles * 4);
+  CU(cudaGetLastError());
+  RowSrc aos{};
+  aos.kind = SRC_AOS;
+  aos.ncols = src.ncols;
+  aos.offset = 0;
+  aos.aos = P<long long>(h->scatter[0]);
+  OutSink oo = o;
+  oo.offs_stride = stride;
+  oo.offs_bbits = Db;
+  RunSet norun{};
+  CopySrc nocopy{};
+  TRY(launch_sortfold<MODE_RANGE>(h, SGAGG_K_RUNGEN, P<Chunk>(h->chunks[0]), info.n_chunks, 0, aos, norun, nocopy,
+                                  fd, oo, rs_dev, &ds->total));
+  kbytes(h, SGAGG_K_RUNGEN, n * 8ll * W);
+  kbegin(h, SGAGG_K_OTHER);
+  k_run_bounds<<<(int)((B + 255) / 256), 256, 0, stream>>>(o.offs, stride, 1 << gd.fbits, (int)B, rs_dev);
+  kend(h);
+  CU(cudaGetLastError());
+  ++h->st.one_pass;
+  *done = true;
+  return SGAGG_OK;
+}
+
 sgagg_status batch_runs(sgagg_t h, const RowSrc& src, long long n, long long M, const FoldDesc& fd, int S,
                         const OutSink& user, const Digit& gd, const long long* base_in, bool stage_io) {
   cudaStream_t stream = h->stream;
@@ -1739,8 +1819,20 @@ sgagg_status batch_runs(sgagg_t h, const RowSrc& src, long long n, long long M, 
       }
     }
   }
+  bool one_pass = false;
+  if (h->one_pass && !any_host && !stage_io && B > 1 && M > kTileCap && n <= kOnePassRows && !h->top_prefold &&
+      gd.fbits - gd.ebits >= 1 && (B << (gd.fbits - gd.ebits)) <= kPlanSmallMax) {
+    OutSink o{};
+    o.user = 0;
+    o.keys = P<unsigned long long>(h->arena_keys);
+    for (int s = 0; s < S; ++s) o.cols[s] = P<long long>(h->arena_cols[s]);
+    o.capacity = dev_rows_cap;
+    o.offs = P<long long>(h->offs);
+    o.dig = gd;
+    TRY(runs_one_pass(h, src, n, M, B, fd, gd, o, stride, rs_dev, &one_pass));
+  }
   if (stage_io) TRY(stage_rows(h, 0, std::min<long long>(M, n), 0));
-  for (long long b = 0; b < B; ++b) {
+  for (long long b = 0; b < B && !one_pass; ++b) {
     long long m = std::min(M, n - b * M);
     if (stage_io) {  // copy batch b + 1 while batch b is grouped
       if (b + 1 < B) TRY(stage_rows(h, (b + 1) * M, std::min<long long>(n, (b + 2) * M), (size_t)b + 1));
@@ -2623,6 +2715,9 @@ sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
     case SGAGG_OPT_PREFOLD_ROWS:
       if (value < 1024 || value > kTileCap) return fail(h, SGAGG_EINVAL, "prefold rows must be 1024..8192");
       h->prefold_rows = value;
+      return SGAGG_OK;
+    case SGAGG_OPT_ONE_PASS:
+      h->one_pass = value ? 1 : 0;
       return SGAGG_OK;
     default: return fail(h, SGAGG_EINVAL, "unknown option");
   }

@@ -22,7 +22,7 @@ SGAGG_COUNT, SGAGG_SUM, SGAGG_MIN, SGAGG_MAX = range(4)
  SGAGG_OPT_FANIN_CAP, SGAGG_OPT_FAULT_ALLOC, SGAGG_OPT_TIMING, SGAGG_OPT_TEST_STALL,
  SGAGG_OPT_POLICY, SGAGG_OPT_ABSORB_BATCH, SGAGG_OPT_LOWCARD, SGAGG_OPT_MERGE_THREADS,
  SGAGG_OPT_HYBRID_FANIN, SGAGG_OPT_HYBRID_F, SGAGG_OPT_HYBRID_LAST, SGAGG_OPT_HYBRID_LAST_AUTO,
- SGAGG_OPT_MERGE_COPY, SGAGG_OPT_PREFOLD_BINS, SGAGG_OPT_PREFOLD_ROWS) = range(19)
+ SGAGG_OPT_MERGE_COPY, SGAGG_OPT_PREFOLD_BINS, SGAGG_OPT_PREFOLD_ROWS, SGAGG_OPT_ONE_PASS) = range(20)
 
 
 class sgagg_agg(ctypes.Structure):
@@ -48,7 +48,7 @@ class sgagg_stats_t(ctypes.Structure):
         "merge_tiles", "kernel_launches")] + [
         ("class_launches", ctypes.c_int64 * 9), ("class_bytes", ctypes.c_int64 * 9),
         ("class_ms", ctypes.c_double * 9), ("resident_rows", ctypes.c_int64), ("resident_keys", ctypes.c_int64),
-        ("hybrid_f", ctypes.c_int64)]
+        ("hybrid_f", ctypes.c_int64), ("one_pass", ctypes.c_int64)]
 
     def as_dict(self):
         d = {n: int(getattr(self, n)) for n, t in self._fields_ if t is ctypes.c_int64}
@@ -293,7 +293,8 @@ class Aggregator:
                  "lowcard": SGAGG_OPT_LOWCARD, "merge_threads": SGAGG_OPT_MERGE_THREADS,
                  "hybrid_fanin": SGAGG_OPT_HYBRID_FANIN, "hybrid_f": SGAGG_OPT_HYBRID_F,
                  "hybrid_last": SGAGG_OPT_HYBRID_LAST, "merge_copy": SGAGG_OPT_MERGE_COPY,
-                 "prefold_bins": SGAGG_OPT_PREFOLD_BINS, "prefold_rows": SGAGG_OPT_PREFOLD_ROWS}
+                 "prefold_bins": SGAGG_OPT_PREFOLD_BINS, "prefold_rows": SGAGG_OPT_PREFOLD_ROWS,
+                 "one_pass": SGAGG_OPT_ONE_PASS}
         for k, v in options.items():
             self.set_option(names[k], v)
 

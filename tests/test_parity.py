@@ -122,6 +122,31 @@ def test_c1_full_size_and_run_rows():
     assert tb >= st["run_rows"] * 8 * (1 + len(c["aggs"]))
 
 
+@pytest.mark.parametrize("one_pass", [1, 0])
+@pytest.mark.parametrize("shape", [(1 << 20, 10_000, 65_536), (300_001, 200_000, 20_000)])
+def test_runs_one_pass_or_batch_at_a_time(one_pass, shape):
+    """Small batches: the runs of all batches generated in one pass per step
+    (the default here) or one batch at a time.  Same output as the oracle,
+    and every run's row count, in order, equals the oracle's run generation
+    (Sec. 3: each run holds its batch's distinct keys once)."""
+    n, D, M = shape
+    c = datagen.config1(n=n, seed=17, D=D, M=M)
+    agg = sgagg.Aggregator(M, one_pass=one_pass)
+    try:
+        ok, oa = agg.aggregate([c["key_cols"][0].to(DEV)], [c["payload"][0].to(DEV)], c["aggs"])
+        st = agg.stats()
+        sizes = list(agg.run_sizes())
+    finally:
+        agg.close()
+    assert st["one_pass"] == one_pass
+    rk, ra = oracle_run(c["key_cols"], c["payload"], c["aggs"])
+    np.testing.assert_array_equal(to_np(ok[0]), rk[0])
+    for a in range(len(ra)):
+        np.testing.assert_array_equal(to_np(oa[a]), ra[a])
+    rows, _, _ = oracle.run_generation(to_np(c["key_cols"][0]), [to_np(c["payload"][0])], c["aggs"], M)
+    assert sizes == [int(r) for r in rows]
+
+
 def test_c2_report_shape_prefold():
     c = datagen.config2(n=1 << 22, seed=2)
     st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=c["M"], lowcard=0)
