@@ -490,95 +490,94 @@ constexpr int kCountSlotBits = 12;   // 4,096 slots for at most 2,048 keys
 constexpr int kCountSlots = 1 << kCountSlotBits;
 
 // count[t] = distinct keys of tile t (its rows, for a tile solved apart).
-// Warp 0 lays the tile's slices end to end (a prefix over their lengths)
-// while the others clear the table; then every thread takes kCountPer rows
-// of the tile, finds each row's slice by binary search over the prefix and
-// issues all its key loads before inserting any, so a tile costs about one
-// memory round trip.
-constexpr int kCountPer = (kMergeTile + kCountThreads - 1) / kCountThreads;
+// Warp w takes slices w, w + 8, ...: their bounds and key addresses go to
+// shared memory, and the warp walks its slices' rows as one array (lane +
+// 32 u, kCountUnroll loads in flight per lane), a row's slice found by a
+// short scan of the warp's slice starts.  The keys go into an
+// open-addressing hash set in shared memory (at most kMergeTile keys in
+// twice as many slots, so a free slot is near); the set's size is the count.
+constexpr int kCountWarps = kCountThreads / 32;
+constexpr int kCountWarpSlices = kMaxFanIn / kCountWarps;  // slices of one warp at most
+constexpr int kCountUnroll = 8;
+
+__device__ __forceinline__ unsigned count_hash(unsigned long long key) {
+  const unsigned x = (unsigned)key ^ (unsigned)(key >> 32);
+  return (x * 0x9E3779B1u) >> (32 - kCountSlotBits);
+}
+
 __global__ void __launch_bounds__(kCountThreads) k_merge_count(const Chunk* __restrict__ chunks,
                                                                const long long* __restrict__ tslo, RunSet runs,
                                                                long long* count, int* err) {
-  __shared__ unsigned long long tab[kCountSlots];
-  __shared__ int pre[kMaxFanIn + 1];       // tile rows before slice r
-  __shared__ long long slo[kMaxFanIn];     // first row of slice r in its run
-  __shared__ int s_cnt, s_top, s_n;
+  __shared__ __align__(16) unsigned long long tab[kCountSlots];
+  __shared__ const long long* wadr[kCountWarps][kCountWarpSlices];  // key address of a slice's first row
+  __shared__ int wst[kCountWarps][kCountWarpSlices + 1];           // warp rows before each slice
+  __shared__ int s_cnt, s_top;
   const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const Chunk ch = chunks[t];
   if (ch.kind == CH_COPY) {
     if (tid == 0) count[t] = ch.hi - ch.lo;
     return;
   }
+  ulonglong2* t2 = reinterpret_cast<ulonglong2*>(tab);
+  for (int i = tid; i < kCountSlots / 2; i += kCountThreads) t2[i] = make_ulonglong2(~0ull, ~0ull);  // empty
+  if (tid == 0) {
+    s_cnt = 0;
+    s_top = 0;
+  }
   const int k = runs.k;
-  if (w == 0) {
-    int run = 0;
-    for (int b = 0; b < k; b += 32) {
-      const int r = b + lane;
-      long long lo = 0, hi = 0;
-      if (r < k) {
-        lo = tslo[(long long)t * k + r];
-        hi = tslo[(long long)(t + 1) * k + r];
-      }
-      const int len = (int)min(max(hi - lo, 0ll), (long long)kMergeTile + 1);
-      int x = len;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (r < k) {
-        slo[r] = lo;
-        pre[r + 1] = run + x;
-      }
-      run = min(run + __shfl_sync(0xffffffffu, x, 31), kMergeTile + 1);
+  const int ns = k > w ? (k - w + kCountWarps - 1) / kCountWarps : 0;  // this warp's slices
+  int run = 0;
+  for (int q0 = 0; q0 < ns; q0 += 32) {
+    const int q = q0 + lane;
+    int len = 0;
+    if (q < ns) {
+      const int r = w + kCountWarps * q;
+      const long long lo = tslo[(long long)t * k + r], hi = tslo[(long long)(t + 1) * k + r];
+      len = (int)min(max(hi - lo, 0ll), (long long)kMergeTile);
+      wadr[w][q] = runs.ptrs[(long long)r * (1 + runs.ncols)] + lo;
     }
-    if (lane == 0) {
-      pre[0] = 0;
-      s_n = run;
-      s_cnt = 0;
-      s_top = 0;
+    int x = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-  } else {
-    for (int i = tid - 32; i < kCountSlots; i += kCountThreads - 32) tab[i] = ~0ull;  // empty; key ~0 apart
+    if (q < ns) wst[w][q] = run + x - len;
+    run = min(run + __shfl_sync(0xffffffffu, x, 31), kMergeTile);
   }
-  __syncthreads();
-  const int n = s_n;
-  if (n > kMergeTile) {  // the planner never makes such tiles
-    if (tid == 0) err_raise(err, ERR_INTERNAL);
-    return;
-  }
-  unsigned long long key[kCountPer];
-#pragma unroll
-  for (int j = 0; j < kCountPer; ++j) {
-    const int i = tid + j * kCountThreads;
-    key[j] = ~0ull;
-    if (i < n) {
-      int lo = 0, hi = k - 1;  // the slice r with pre[r] <= i < pre[r + 1]
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= i) lo = mid; else hi = mid - 1;
-      }
-      key[j] = (unsigned long long)__ldg(runs.ptrs[(long long)lo * (1 + runs.ncols)] + slo[lo] + (i - pre[lo]));
-    }
-  }
+  if (lane == 0) wst[w][ns] = run;
+  __syncthreads();  // the table is empty; every warp's slices are laid out
   int mine = 0;
+  for (int b = 0; b < run; b += 32 * kCountUnroll) {
+    unsigned long long key[kCountUnroll];
 #pragma unroll
-  for (int j = 0; j < kCountPer; ++j) {
-    if (tid + j * kCountThreads >= n) continue;
-    const unsigned long long kk = key[j];
-    if (kk == ~0ull) {
-      if (atomicExch(&s_top, 1) == 0) ++mine;
-      continue;
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const int p = b + lane + 32 * u;
+      key[u] = 0;
+      if (p < run) {
+        int q = 0;
+        while (q + 1 < ns && wst[w][q + 1] <= p) ++q;
+        key[u] = (unsigned long long)__ldg(wadr[w][q] + (p - wst[w][q]));
+      }
     }
-    unsigned slot = (unsigned)((kk * 0x9E3779B97F4A7C15ull) >> (64 - kCountSlotBits));
-    int probes = 0;
-    while (true) {  // a tile has at most kMergeTile keys in twice as many slots: a free slot is near
-      const unsigned long long old = atomicCAS(&tab[slot], ~0ull, kk);
-      if (old == ~0ull) { ++mine; break; }
-      if (old == kk) break;
-      slot = (slot + 1) & (kCountSlots - 1);
-      if (++probes == kCountSlots) {  // cannot happen with at most half the slots taken
-        err_raise(err, ERR_INTERNAL);
-        break;
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      if (b + lane + 32 * u >= run) continue;
+      const unsigned long long kk = key[u];
+      if (kk == ~0ull) {  // the empty mark as a key: counted apart
+        if (atomicExch(&s_top, 1) == 0) ++mine;
+        continue;
+      }
+      unsigned slot = count_hash(kk);
+      int probes = 0;
+      while (true) {
+        const unsigned long long old = atomicCAS(&tab[slot], ~0ull, kk);
+        if (old == ~0ull) { ++mine; break; }
+        if (old == kk) break;
+        slot = (slot + 1) & (kCountSlots - 1);
+        if (++probes == kCountSlots) {  // cannot happen with at most half the slots taken
+          err_raise(err, ERR_INTERNAL);
+          break;
+        }
       }
     }
   }
