@@ -186,13 +186,17 @@ typedef enum {
                                      Same result. */
     SGAGG_OPT_PREFOLD_ROWS = 18,  /* rows per pre-aggregation tile of sgagg_aggregate_batched,
                                      1024..8192 (default 8192).  Same result. */
-    SGAGG_OPT_ONE_PASS = 19       /* 1 (default): when the input is several batches of more
+    SGAGG_OPT_ONE_PASS = 19,      /* 1 (default): when the input is several batches of more
                                      than one chunk each, at most 2^24 rows in all and few
                                      buckets, the runs of all batches are generated in one
                                      pass per step (one histogram, plan, scatter and
                                      sort+fold launch for all of them) instead of one batch
                                      at a time; 0: always a batch at a time.  The runs are
                                      the same. */
+    SGAGG_OPT_PART_LEVELS = 20    /* partitioning of a batch before its chunk sorts: 0
+                                     (default) two staged levels above 2^7 buckets, else
+                                     one; 1 always one level (every row written once to
+                                     its final bucket).  Same result. */
 } sgagg_option;
 
 /*

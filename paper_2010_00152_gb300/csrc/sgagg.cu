@@ -126,6 +126,7 @@ struct sgagg_ctx {
                                  // 2 bulk copies by the control warp
   int prefold_bins = 0;          // tile pre-aggregation binning: 0 key range, 1 hash of the key
   int one_pass = 1;              // small batches: every run in one pass per step (0: a batch at a time)
+  int part_levels = 0;           // partition levels: 0 auto (two above 2^7 buckets), 1 always one
   long long prefold_rows = kTileCap;  // rows per pre-aggregation tile of a batched call
   int hybrid_fanin = 10;         // hybrid run generation (policy 2): F
   int hybrid_f = -1;             // f (-1: from the estimated output size)
@@ -893,7 +894,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
   TRY(grow(h, h->bstart[depth], (size_t)(nb + 1) * 8));
   TRY(grow(h, h->chunks[depth], (size_t)nb * sizeof(Chunk)));
   TRY(grow(h, h->biglist[depth], (size_t)nb * 4));
-  if (staged && Db > kLevel1Bits) {
+  if (staged && Db > kLevel1Bits && h->part_levels != 1) {
     // two levels: 2^kLevel1Bits buckets, then the remaining D2 digit bits
     const int D2 = Db - kLevel1Bits, nb1 = 1 << kLevel1Bits, nb2 = 1 << D2;
     const long long nt2max = (n + kTile2 - 1) / kTile2 + nb1;
@@ -2718,6 +2719,10 @@ sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
       return SGAGG_OK;
     case SGAGG_OPT_ONE_PASS:
       h->one_pass = value ? 1 : 0;
+      return SGAGG_OK;
+    case SGAGG_OPT_PART_LEVELS:
+      if (value != 0 && value != 1) return fail(h, SGAGG_EINVAL, "partition levels must be 0 or 1");
+      h->part_levels = (int)value;
       return SGAGG_OK;
     default: return fail(h, SGAGG_EINVAL, "unknown option");
   }

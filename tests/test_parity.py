@@ -242,6 +242,14 @@ def test_prefold_bins_invariant(bins):
     assert st["prefold_passes"] >= 1
 
 
+@pytest.mark.parametrize("bits", [0, 9, 15])
+def test_single_level_partition(bits):
+    """Every row written once to its final bucket (no second partition
+    level), at the automatic and at wide digits: same result."""
+    c = datagen.config1(n=300_000, seed=19, D=200_000)
+    check(c["key_cols"], c["payload"], c["aggs"], M=150_000, radix_bits=bits, part_levels=1)
+
+
 @pytest.mark.parametrize("bits", [1, 4, 9, 15])
 def test_radix_bits_invariant(bits):
     c = datagen.config1(n=300_000, seed=8, D=200_000)
