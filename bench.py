@@ -279,6 +279,103 @@ def bench_small(args, dev, steps=50, warmup=10):
             "clocks": clk}
 
 
+def tune(args, dev):
+    """Measure candidate option sets for the batched call (4,096 instances)
+    and for the 512M-row and 1M-row calls, and write the fastest of each
+    shape to the autotuner's cache (paper_2010_00152_gb300/tuning.json, or
+    --tune-out).  Every candidate gives the same result."""
+    import torch
+    import datagen
+    from paper_2010_00152_gb300 import sgagg, tuning
+    cache = tuning.load(args.tune_out) if os.path.exists(args.tune_out) else {}
+    note = "CUDA events, %d calls after %d warm-up, one GB300"
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+
+    def measure(make_call, cands, steps, warm):
+        out = []
+        for opts in cands:
+            call, close = make_call(opts)
+            for _ in range(warm):
+                call()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append((opts, e0.elapsed_time(e1) / steps))
+            close()
+            print(json.dumps({"candidate": opts, "ms": round(out[-1][1], 3)}), flush=True)
+        return out
+
+    # batched: the instances of the batched workload, descriptors built once
+    count = args.instances or WORKLOADS["c4"]["n"]
+    specs = datagen.config4_instances(count=count, seed=1)
+    insts = [datagen.config4_instance(sp, device=dev) for sp in specs]
+    aggs = insts[0]["aggs"]
+    n_total = sum(sp["rows"] for sp in specs)
+    rows_dev = torch.zeros(count, dtype=torch.int64, device=dev)
+    descs, keep = [], []
+    for i, c in enumerate(insts):
+        k, p = c["key_cols"][0], c["payload"][0]
+        cap = max(1, min(k.numel(), specs[i]["D"]))
+        ok = torch.empty(cap, dtype=k.dtype, device=dev)
+        oa = [torch.empty(cap, dtype=torch.int64, device=dev) for _ in aggs]
+        pp = torch.tensor([p.data_ptr()], dtype=torch.int64, device=dev)
+        op = torch.tensor([a.data_ptr() for a in oa], dtype=torch.int64, device=dev)
+        keep += [ok, oa, pp, op]
+        descs.append(sgagg.sgagg_instance(k.data_ptr(), 4, 1, pp.data_ptr(), k.numel(), ok.data_ptr(),
+                                          op.data_ptr(), cap, rows_dev.data_ptr() + 8 * i))
+    torch.cuda.synchronize()
+
+    def batched_call(opts):
+        agg = sgagg.Aggregator(1 << 22, **opts)
+        return (lambda: (sgagg.sgagg_aggregate_batched(agg.h, descs, aggs, s), agg.rows())), agg.close
+
+    agg = sgagg.Aggregator(1 << 22)
+    sgagg.sgagg_aggregate_batched(agg.h, descs, aggs, s)
+    dup = 1.0 - agg.rows() / max(1, n_total)
+    agg.close()
+    cands = [dict(batch_group_rows=1 << g, prefold_rows=r) for g in (25, 26, 27, 28) for r in (8192, 4096)]
+    key = tuning.shape_key("batched", n_total, 32, len(aggs), dup)
+    best = tuning.record(cache, key, measure(batched_call, cands, 3, 1), note % (3, 1))
+    print(json.dumps({"shape": key, "best": best}), flush=True)
+    del insts, keep, descs
+    torch.cuda.empty_cache()
+
+    # plain calls: the 512M-row and the 1M-row workloads
+    for name, cands, steps in (("c3", [dict(), dict(merge_copy=1), dict(merge_copy=2)], 3),
+                               ("c1", [dict(), dict(one_pass=0)], 20)):
+        w = make_workload(name, dev)
+        n = int(w["key_cols"][0].numel())
+        M = int(w["M"])
+        ok = [torch.empty(n, dtype=k.dtype, device=dev) for k in w["key_cols"]]
+        oa = [torch.empty(n, dtype=torch.int64, device=dev) for _ in w["aggs"]]
+
+        def plain_call(opts):
+            agg = sgagg.Aggregator(M, **opts)
+
+            def call():
+                agg.aggregate(w["key_cols"], w["payload"], w["aggs"], capacity=n, out=(ok, oa), sync=False)
+                return agg.rows()
+            return call, agg.close
+
+        c, close = plain_call({})
+        dup = 1.0 - c() / n
+        close()
+        kb = 8 * sum(k.element_size() for k in w["key_cols"])
+        key = tuning.shape_key("aggregate", n, kb, len(w["aggs"]), dup)
+        best = tuning.record(cache, key, measure(plain_call, cands, steps, 3), note % (steps, 3))
+        print(json.dumps({"shape": key, "best": best}), flush=True)
+        del w, ok, oa
+        torch.cuda.empty_cache()
+    tuning.save(cache, args.tune_out)
+    return 0
+
+
 def bench_batched(args, dev, steps=None, warmup=None, plain_steps=None):
     """Config 4: the batched call against the plain loop of one call per
     instance over the same instances (both through the C ABI).  Returns the
@@ -311,9 +408,18 @@ def bench_batched(args, dev, steps=None, warmup=None, plain_steps=None):
                                           rows_dev.data_ptr() + 8 * i))
         outs.append((ok, oa))
     torch.cuda.synchronize()
-    agg = sgagg.Aggregator(1 << 22, timing=1)
     stream = torch.cuda.current_stream(dev)
     s = stream.cuda_stream
+    # the autotuner's options for this shape: the duplicate share comes from
+    # one call with the defaults (as a repeated workload would know it)
+    from paper_2010_00152_gb300 import tuning
+    agg = sgagg.Aggregator(1 << 22)
+    sgagg.sgagg_aggregate_batched(agg.h, descs, aggs, s)
+    dup = 1.0 - agg.rows() / max(1, n_total)
+    agg.close()
+    tkey = tuning.shape_key("batched", n_total, 32, len(aggs), dup)
+    topts, tsrc, tmatch = tuning.choose(tkey)
+    agg = sgagg.Aggregator(1 << 22, timing=1, **topts)
 
     def batched():
         sgagg.sgagg_aggregate_batched(agg.h, descs, aggs, s)
@@ -359,7 +465,8 @@ def bench_batched(args, dev, steps=None, warmup=None, plain_steps=None):
             "speedup_vs_plain": ms_p / ms_b, "out_rows": rows_b, "clocks": clk,
             "timing": "CUDA events on the call stream around each form's timed steps",
             "kernels": {k: v for k, v in st["kernels"].items() if v["launches"]},
-            "gpu_launches": st["kernel_launches"] * steps}
+            "gpu_launches": st["kernel_launches"] * steps,
+            "autotune": {"shape": tkey, "options": topts, "source": tsrc, "matched": tmatch}}
     agg.close()
     del insts, outs, keep, descs
     torch.cuda.empty_cache()
@@ -512,6 +619,9 @@ def main():
     ap.add_argument("--sub-requests", type=int, default=4000,
                     help="requests of the served sub-object's Poisson replays")
     ap.add_argument("--instances", type=int, default=None, help="c4: instance count")
+    ap.add_argument("--tune", action="store_true",
+                    help="measure the autotuner's candidate options and write its cache")
+    ap.add_argument("--tune-out", default=None, help="cache file to write (default: the package's tuning.json)")
     ap.add_argument("--requests", type=int, default=None, help="c5: request count")
     ap.add_argument("--capacity-requests", type=int, default=1000,
                     help="c5: requests run back to back to measure the plain form's capacity")
@@ -534,6 +644,10 @@ def main():
     build.build()
 
     name = args.config
+    if args.tune:
+        from paper_2010_00152_gb300 import tuning
+        args.tune_out = args.tune_out or tuning.CACHE
+        return tune(args, dev)
     if name == "c4":
         print(json.dumps(bench_batched(args, dev)))
         return 0
@@ -546,10 +660,19 @@ def main():
     aggs = w["aggs"]
     torch.cuda.synchronize()
 
-    agg = sgagg.Aggregator(M, timing=1)
     ok = [torch.empty(n, dtype=k.dtype, device=dev) for k in w["key_cols"]]
     oa = [torch.empty(n, dtype=torch.int64, device=dev) for _ in aggs]
     stream = torch.cuda.current_stream(dev)
+    # the autotuner's options for this shape (result-invariant): the
+    # duplicate share from a first, untimed warm-up call with the defaults
+    from paper_2010_00152_gb300 import tuning
+    agg = sgagg.Aggregator(M)
+    agg.aggregate(w["key_cols"], w["payload"], aggs, capacity=n, out=(ok, oa), sync=False)
+    dup = 1.0 - agg.rows() / max(1, n)
+    agg.close()
+    tkey = tuning.shape_key("aggregate", n, 8 * sum(k.element_size() for k in w["key_cols"]), len(aggs), dup)
+    topts, tsrc, tmatch = tuning.choose(tkey)
+    agg = sgagg.Aggregator(M, timing=1, **topts)
 
     def step():
         agg.aggregate(w["key_cols"], w["payload"], aggs, capacity=n, out=(ok, oa), sync=False)
@@ -648,6 +771,7 @@ def main():
             "temp_bytes": temp_bytes, "output_bytes": int(out_b),
             "runs": st["runs"], "run_rows": st["run_rows"], "out_rows": rows,
             "kernels": kernels, "clocks": clk, "gpu_launches": launches,
+            "autotune": {"shape": tkey, "options": topts, "source": tsrc, "matched": tmatch},
             "e2e": e2e, "cpu_baseline": cpu,
         }
         line.update(sub)

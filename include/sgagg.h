@@ -193,10 +193,14 @@ typedef enum {
                                      sort+fold launch for all of them) instead of one batch
                                      at a time; 0: always a batch at a time.  The runs are
                                      the same. */
-    SGAGG_OPT_PART_LEVELS = 20    /* partitioning of a batch before its chunk sorts: 0
+    SGAGG_OPT_PART_LEVELS = 20,   /* partitioning of a batch before its chunk sorts: 0
                                      (default) two staged levels above 2^7 buckets, else
                                      one; 1 always one level (every row written once to
                                      its final bucket).  Same result. */
+    SGAGG_OPT_BATCH_GROUP_ROWS = 21 /* sgagg_aggregate_batched: rows of the multi-chunk
+                                     instances grouped in one pass (2^16..2^31, default
+                                     2^25); bigger groups mean fewer passes and host round
+                                     trips and more scratch memory.  Same result. */
 } sgagg_option;
 
 /*

@@ -56,7 +56,7 @@ constexpr size_t kRunSlack = 16;
 constexpr int kMaxDepth = 70;
 constexpr long long kMaxBatch = 1ll << 30;
 constexpr int kSample = 16384;
-constexpr long long kBatchGroupRows = 1ll << 25;   // rows per group of a batched call
+constexpr long long kBatchGroupRows = 1ll << 25;   // rows per group of a batched call (default)
 
 struct DevBuf {
   void* p = nullptr;
@@ -127,6 +127,7 @@ struct sgagg_ctx {
   int prefold_bins = 0;          // tile pre-aggregation binning: 0 key range, 1 hash of the key
   int one_pass = 1;              // small batches: every run in one pass per step (0: a batch at a time)
   int part_levels = 0;           // partition levels: 0 auto (two above 2^7 buckets), 1 always one
+  long long batch_group_rows = kBatchGroupRows;  // batched call: rows of the instances grouped at once
   long long prefold_rows = kTileCap;  // rows per pre-aggregation tile of a batched call
   int hybrid_fanin = 10;         // hybrid run generation (policy 2): F
   int hybrid_f = -1;             // f (-1: from the estimated output size)
@@ -2228,7 +2229,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
   if (count == 0) return SGAGG_OK;
 
   // instance table (all instances); groups of consecutive instances of at
-  // most kBatchGroupRows rows bound the scratch
+  // most h->batch_group_rows rows bound the scratch
   TRY(grow(h, h->binst, (size_t)count * sizeof(InstDesc)));
   TRY(grow(h, h->bseg, (size_t)count * sizeof(SegEntry)));
   TRY(grow(h, h->brange, (size_t)count * 16));
@@ -2355,7 +2356,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
     int i1 = i0;
     long long grows = 0;
     auto big_rows = [&](int i) { return inst[i].n > kTileCap ? inst[i].n : 0ll; };
-    while (i1 < count && (i1 == i0 || grows + big_rows(i1) <= kBatchGroupRows)) grows += big_rows(i1++);
+    while (i1 < count && (i1 == i0 || grows + big_rows(i1) <= h->batch_group_rows)) grows += big_rows(i1++);
     if (grows == 0) {  // only instances of the direct launch
       i0 = i1;
       continue;
@@ -2723,6 +2724,10 @@ sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
     case SGAGG_OPT_PART_LEVELS:
       if (value != 0 && value != 1) return fail(h, SGAGG_EINVAL, "partition levels must be 0 or 1");
       h->part_levels = (int)value;
+      return SGAGG_OK;
+    case SGAGG_OPT_BATCH_GROUP_ROWS:
+      if (value < (1 << 16) || value > (1ll << 31)) return fail(h, SGAGG_EINVAL, "batch group rows must be 2^16..2^31");
+      h->batch_group_rows = value;
       return SGAGG_OK;
     default: return fail(h, SGAGG_EINVAL, "unknown option");
   }

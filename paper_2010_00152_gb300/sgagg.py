@@ -23,7 +23,7 @@ SGAGG_COUNT, SGAGG_SUM, SGAGG_MIN, SGAGG_MAX = range(4)
  SGAGG_OPT_POLICY, SGAGG_OPT_ABSORB_BATCH, SGAGG_OPT_LOWCARD, SGAGG_OPT_MERGE_THREADS,
  SGAGG_OPT_HYBRID_FANIN, SGAGG_OPT_HYBRID_F, SGAGG_OPT_HYBRID_LAST, SGAGG_OPT_HYBRID_LAST_AUTO,
  SGAGG_OPT_MERGE_COPY, SGAGG_OPT_PREFOLD_BINS, SGAGG_OPT_PREFOLD_ROWS, SGAGG_OPT_ONE_PASS,
- SGAGG_OPT_PART_LEVELS) = range(21)
+ SGAGG_OPT_PART_LEVELS, SGAGG_OPT_BATCH_GROUP_ROWS) = range(22)
 
 
 class sgagg_agg(ctypes.Structure):
@@ -295,7 +295,8 @@ class Aggregator:
                  "hybrid_fanin": SGAGG_OPT_HYBRID_FANIN, "hybrid_f": SGAGG_OPT_HYBRID_F,
                  "hybrid_last": SGAGG_OPT_HYBRID_LAST, "merge_copy": SGAGG_OPT_MERGE_COPY,
                  "prefold_bins": SGAGG_OPT_PREFOLD_BINS, "prefold_rows": SGAGG_OPT_PREFOLD_ROWS,
-                 "one_pass": SGAGG_OPT_ONE_PASS, "part_levels": SGAGG_OPT_PART_LEVELS}
+                 "one_pass": SGAGG_OPT_ONE_PASS, "part_levels": SGAGG_OPT_PART_LEVELS,
+                 "batch_group_rows": SGAGG_OPT_BATCH_GROUP_ROWS}
         for k, v in options.items():
             self.set_option(names[k], v)
 

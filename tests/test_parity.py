@@ -404,10 +404,12 @@ def test_batched_matches_oracle(key_dtype):
             np.testing.assert_array_equal(to_np(r[1][a]), ra[a])
 
 
-@pytest.mark.parametrize("opts", [dict(prefold_bins=1), dict(prefold_rows=1024), dict(prefold_rows=3000)])
+@pytest.mark.parametrize("opts", [dict(prefold_bins=1), dict(prefold_rows=1024), dict(prefold_rows=3000),
+                                  dict(batch_group_rows=1 << 16), dict(batch_group_rows=1 << 20)])
 def test_batched_prefold_options(opts):
-    """The batched call with hash-binned or smaller pre-aggregation tiles:
-    every instance still equals its own oracle result."""
+    """The batched call with hash-binned or smaller pre-aggregation tiles, or
+    its instances grouped in smaller or bigger passes: every instance still
+    equals its own oracle result."""
     sizes = [8193, 20_000, 70_001, 150_000, 9000]
     domains = [20_000, 5, 100_000, 1_000_000, 60_000]
     insts = _batched_case(4, sizes, domains)
