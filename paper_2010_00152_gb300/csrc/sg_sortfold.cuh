@@ -1,11 +1,12 @@
 // sg_sortfold.cuh -- sort a chunk of rows in shared memory and fold equal
-// keys (the in-cache batch sort + duplicate detection of Sec. 6.1, and the
-// absorbing of equal keys from many runs in the wide merge of Sec. 4).
+// keys (the in-cache batch sort + duplicate detection of Sec. 6.1): the
+// run-generation leaf, tile pre-aggregation, one-chunk inputs and the
+// one-chunk instances of a batched call.  (The wide merge of Sec. 4 has a
+// kernel of its own, sg_merge.cuh.)
 //
 // One CTA takes one chunk (ticket order) of at most kTileCap rows:
 //   1. load the chunk's keys into shared memory (a row range of one source,
-//      or one slice from each of k sorted runs, all loads in flight at once;
-//      the runs' aggregate columns are prefetched into L2 meanwhile);
+//      all loads in flight at once);
 //   2. sort a permutation of the chunk by key: a counting sort on the top
 //      kBinBits bits of (key - chunk min); one pass over adjacent positions
 //      flags the bins still out of key order, and only those are finished:
@@ -30,12 +31,12 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kBinBits = 13;
 constexpr int kBins = 1 << kBinBits;
 constexpr int kBinsPerThread = kBins / kThreads;  // 16
-constexpr int kMaxFanIn = 256;             // runs one merge chunk can read
+constexpr int kMaxFanIn = 256;             // runs one wide-merge tile can read
 constexpr int kFewGroups = 16;             // CTA-per-group fold below this many keys
 constexpr int kAccBlock = 8;               // state columns folded per pass
 
 enum : int { CH_NORMAL = 0, CH_COPY = 1 };
-enum : int { MODE_RANGE = 0, MODE_RUNS = 1, MODE_TILES = 2, MODE_INST = 3, MODE_DIRECT = 4 };
+enum : int { MODE_RANGE = 0, MODE_TILES = 2, MODE_INST = 3, MODE_DIRECT = 4 };
 
 // One instance of a batched call (same layout as sgagg_instance).
 struct InstDesc {
@@ -65,7 +66,7 @@ struct InstSet {
 
 struct Chunk {
   long long lo, hi;   // MODE_RANGE: source rows; CH_COPY: rows of the copy source
-  int f_lo, f_hi;     // fine buckets covered (offsets of runs; MODE_RUNS slices)
+  int f_lo, f_hi;     // fine buckets covered (the run's sparse index; merge tiles' slices)
   int kind;
   int pad;
 };
@@ -109,16 +110,9 @@ struct SortSmem {
   uint16_t* whist;            // [kWarps * 256] LSD per-warp digit counts; or the bin flags,
                               // big-bin and flagged-bin lists; then the head bitmask and
                               // its word prefix
-  long long* slo;             // [kMaxFanIn] merge: slice start per run, less the chunk
-                              // position of the slice's first row
-  long long* spre;            // [kMaxFanIn + 1] merge: slice prefix
-  unsigned long long* sadr;   // [kMaxFanIn] merge: address of chunk row 0 in each run's
-                              // current column (keys, then each staged column)
 };
 
-constexpr size_t kSortSmemBytes =
-    kTileCap * 8 + kTileCap * 2 + (kBins / 2) * 4 + kWarps * 256 * 2 + kMaxFanIn * 8 + (kMaxFanIn + 1) * 8 +
-    kMaxFanIn * 8 + 64;
+constexpr size_t kSortSmemBytes = kTileCap * 8 + kTileCap * 2 + (kBins / 2) * 4 + kWarps * 256 * 2 + 64;
 static_assert(kBins >= kTileCap, "the LSD ping-pong buffer lives in the bins area");
 // two CTAs per SM: 2 x (dynamic + static (< 2.5 KB) + 1 KB reserved) within 228 KB
 static_assert(kSortSmemBytes <= 113000, "k_sortfold must keep two CTAs per SM");
@@ -129,9 +123,6 @@ __device__ __forceinline__ SortSmem carve(unsigned char* base) {
   s.idx = reinterpret_cast<uint16_t*>(base + kTileCap * 8);
   s.bins = reinterpret_cast<uint32_t*>(base + kTileCap * 10);
   s.whist = reinterpret_cast<uint16_t*>(base + kTileCap * 10 + (kBins / 2) * 4);
-  s.slo = reinterpret_cast<long long*>(base + kTileCap * 10 + (kBins / 2) * 4 + kWarps * 256 * 2);
-  s.spre = s.slo + kMaxFanIn;
-  s.sadr = reinterpret_cast<unsigned long long*>(s.spre + kMaxFanIn + 1);
   return s;
 }
 
@@ -178,29 +169,18 @@ __device__ __forceinline__ long long warp_reduce(int op, long long v) {
 // Row access.
 // ---------------------------------------------------------------------------
 struct ChunkView {
-  long long lo;     // first source row (MODE_RANGE / MODE_TILES)
+  long long lo;     // first source row
   int n;
-  int k;            // MODE_RUNS: runs
 };
 
-// Advance a run cursor r (MODE_RUNS) to the run holding position i >= its start.
-__device__ __forceinline__ int run_advance(const SortSmem& s, int k, int r, int i) {
-  while (r + 1 < k && s.spre[r + 1] <= i) ++r;
-  return r;
-}
-
 template <int MODE>
-__device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, const RunSet& runs,
-                                          const ChunkView& cv, unsigned long long* lmin, unsigned long long* lmax) {
-  if (MODE == MODE_RUNS || src_keys_direct(src)) {
+__device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, const ChunkView& cv,
+                                          unsigned long long* lmin, unsigned long long* lmax) {
+  if (src_keys_direct(src)) {
     // 8-byte keys: copied global to shared by cp.async, all in flight at once
-    int r = 0;
     for (int i = threadIdx.x; i < cv.n; i += kThreads) {
       const unsigned long long* p;
-      if (MODE == MODE_RUNS) {
-        r = run_advance(s, cv.k, r, i);
-        p = reinterpret_cast<const unsigned long long*>(s.sadr[r]) + i;
-      } else if (MODE == MODE_RANGE) {
+      if (MODE == MODE_RANGE) {
         p = reinterpret_cast<const unsigned long long*>(src.aos + (cv.lo + i) * (1 + src.ncols));
       } else {
         p = src_key_ptr(src, cv.lo + i);
@@ -222,7 +202,7 @@ __device__ __forceinline__ void load_keys(const SortSmem& s, const RowSrc& src, 
     for (int u = 0; u < U; ++u) {
       int i = base + u * kThreads;
       if (i < cv.n) {
-        v[u] = src_key(src, cv.lo + i);  // (MODE_RUNS always takes the path above)
+        v[u] = src_key(src, cv.lo + i);
       }
     }
 #pragma unroll
@@ -651,21 +631,11 @@ __shared__ int g_lcnt[kWarps + 1];
 // order and all in flight at once; complete when it returns (visible to the
 // other threads after a barrier).
 template <int MODE>
-__device__ __forceinline__ void stage_column(const SortSmem& s, const RowSrc& src, const RunSet& runs,
-                                             const ChunkView& cv, int c, const uint16_t* inv, long long* dst) {
-  if (MODE == MODE_RUNS) {  // each run's base address for column c
-    for (int r = threadIdx.x; r < cv.k; r += kThreads)
-      s.sadr[r] = reinterpret_cast<unsigned long long>(runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c]) +
-                  8ull * (unsigned long long)s.slo[r];
-    __syncthreads();
-  }
-  int r = 0;
+__device__ __forceinline__ void stage_column(const RowSrc& src, const ChunkView& cv, int c, const uint16_t* inv,
+                                             long long* dst) {
   for (int i = threadIdx.x; i < cv.n; i += kThreads) {
     const long long* p;
-    if (MODE == MODE_RUNS) {
-      r = run_advance(s, cv.k, r, i);
-      p = reinterpret_cast<const long long*>(s.sadr[r]) + i;
-    } else if (MODE == MODE_RANGE) {
+    if (MODE == MODE_RANGE) {
       p = src.aos + (cv.lo + i) * (1 + src.ncols) + 1 + c;
     } else {
       const int64_t row = src.offset + cv.lo + i;
@@ -805,7 +775,7 @@ __device__ void fold_scan(const uint32_t* hm, const uint16_t* hpre, const long l
 // sort says that groups may exceed 32 rows) the whole CTA folds one group at
 // a time.
 template <int MODE, int KS, bool BIGS>
-__device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& runs, const ChunkView& cv,
+__device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const ChunkView& cv,
                             const FoldDesc& fd, const OutSink& out, const LookBack& lb, const Chunk& ch,
                             int cid, long long* s_base) {
   const int n = cv.n;
@@ -924,13 +894,13 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
   if (few && threadIdx.x == 0) g_gstart[count] = n;
   // aggregates, one source column at a time
   long long* col = reinterpret_cast<long long*>(s.keys);
-  const int ncols = (MODE == MODE_RUNS) ? runs.ncols : src.ncols;
+  const int ncols = src.ncols;
   for (int c = 0; c < ncols; ++c) {
     bool used = false;
     for (int a = 0; a < ns; ++a) used |= (fd.src[a] == c);
     if (!used) continue;  // block-uniform
     __syncthreads();      // everyone is done with the previous contents (keys, offsets, column)
-    stage_column<MODE>(s, src, runs, cv, c, inv, col);
+    stage_column<MODE>(src, cv, c, inv, col);
     __syncthreads();
     if (few) {
       fold_few(s, fd, out, col, c, count, base);
@@ -977,7 +947,7 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const RunSet& 
 // ---------------------------------------------------------------------------
 template <int MODE, int KS>
 __global__ void __launch_bounds__(kThreads, 2)
-k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, CopySrc copy, FoldDesc fd,
+k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, CopySrc copy, FoldDesc fd,
            OutSink out, LookBack lb, long long tile_n, int tile_f_hi, InstSet is) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem s = carve(smem_raw);
@@ -1055,65 +1025,15 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
 
   ChunkView cv;
   cv.lo = ch.lo;
-  cv.k = 0;
-  if (MODE == MODE_RUNS) {
-    const int k = runs.k;
-    cv.k = k;
-    for (int r = threadIdx.x; r < k; r += kThreads) {
-      long long lo = runs.offs[r][ch.f_lo];
-      long long hi = runs.offs[r][ch.f_hi];
-      s.slo[r] = lo;
-      s.spre[r + 1] = hi - lo;
-      // pull the slice's aggregate columns into L2 while the keys sort
-      for (int c = 0; c < runs.ncols; ++c) {
-        const long long* p = runs.ptrs[(long long)r * (1 + runs.ncols) + 1 + c] + lo;
-        unsigned long long a0 = reinterpret_cast<unsigned long long>(p) & ~15ull;
-        unsigned long long a1 = (reinterpret_cast<unsigned long long>(p + (hi - lo)) + 15ull) & ~15ull;
-        if (a1 > a0)
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((unsigned)(a1 - a0))
-                       : "memory");
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      // prefix over k <= kMaxFanIn slice lengths
-      long long run = 0;
-      for (int b = 0; b < k; b += 32) {
-        int r = b + threadIdx.x;
-        long long v = r < k ? s.spre[r + 1] : 0;
-        long long x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-          long long y = __shfl_up_sync(0xffffffffu, x, o);
-          if ((int)threadIdx.x >= o) x += y;
-        }
-        if (r < k) {
-          s.spre[r + 1] = run + x;
-          // slice start less the chunk position of its first row: chunk row
-          // i of run r is row slo[r] + i of its arrays
-          const long long off = s.slo[r] - (run + x - v);
-          s.slo[r] = off;
-          s.sadr[r] = reinterpret_cast<unsigned long long>(runs.ptrs[(long long)r * (1 + runs.ncols)]) +
-                      8ull * (unsigned long long)off;
-        }
-        run += __shfl_sync(0xffffffffu, x, 31);
-      }
-      if (threadIdx.x == 0) {
-        s.spre[0] = 0;
-        s_n = (int)min(run, (long long)kTileCap + 1);
-      }
-    }
-    __syncthreads();
-  } else {
-    if (threadIdx.x == 0) s_n = (int)(ch.hi - ch.lo);
-    __syncthreads();
-  }
+  if (threadIdx.x == 0) s_n = (int)(ch.hi - ch.lo);
+  __syncthreads();
   cv.n = s_n;
   if (cv.n > kTileCap) {  // the planner never makes such chunks
     if (threadIdx.x == 0) err_raise(lb.err, ERR_INTERNAL);
     return;
   }
   unsigned long long lmin = ~0ull, lmax = 0ull;
-  load_keys<MODE>(s, src, runs, cv, &lmin, &lmax);
+  load_keys<MODE>(s, src, cv, &lmin, &lmax);
   // its first barrier completes the load
   const bool bigs = chunk_sort(s, cv.n, lmin, lmax, (MODE == MODE_TILES || MODE == MODE_INST) && is.grouped);
   if (MODE == MODE_INST && is.kmin && threadIdx.x == 0 && cv.n > 0) {
@@ -1123,8 +1043,8 @@ k_sortfold(const Chunk* __restrict__ chunks, RowSrc src_param, RunSet runs, Copy
     atomicMin(is.kmin + ch.pad, g_kmin & m);
     atomicMax(is.kmax + ch.pad, g_kmax & m);
   }
-  if (bigs) fold_sorted<MODE, KS, true>(s, src, runs, cv, fd, dst, lb, ch, cid, &s_base);
-  else fold_sorted<MODE, KS, false>(s, src, runs, cv, fd, dst, lb, ch, cid, &s_base);
+  if (bigs) fold_sorted<MODE, KS, true>(s, src, cv, fd, dst, lb, ch, cid, &s_base);
+  else fold_sorted<MODE, KS, false>(s, src, cv, fd, dst, lb, ch, cid, &s_base);
 }
 
 }  // namespace sg

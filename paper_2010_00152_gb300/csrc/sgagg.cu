@@ -505,11 +505,11 @@ void set_smem_attr() {
 
 // Launch the sort+fold kernel specialized for the number of aggregates.
 template <int MODE, int KS>
-void launch_ks(int grid, cudaStream_t st, const Chunk* dchunks, const RowSrc& src, const RunSet& runs,
+void launch_ks(int grid, cudaStream_t st, const Chunk* dchunks, const RowSrc& src,
                const CopySrc& copy, const FoldDesc& fd, const OutSink& out, const LookBack& lb,
                long long tile_n, int tile_f_hi, const InstSet& is = InstSet{}) {
   set_smem_attr<MODE, KS>();
-  k_sortfold<MODE, KS><<<grid, kThreads, kSortSmemBytes, st>>>(dchunks, src, runs, copy, fd, out, lb, tile_n,
+  k_sortfold<MODE, KS><<<grid, kThreads, kSortSmemBytes, st>>>(dchunks, src, copy, fd, out, lb, tile_n,
                                                               tile_f_hi, is);
 }
 
@@ -561,7 +561,7 @@ FoldDesc identity_fold(const FoldDesc& raw) {
 // Launch the sort+fold kernel over n_chunks chunks.
 template <int MODE>
 sgagg_status launch_sortfold(sgagg_t h, int cls, const Chunk* dchunks, int n_chunks, long long tile_n,
-                             const RowSrc& src, const RunSet& runs, const CopySrc& copy,
+                             const RowSrc& src, const CopySrc& copy,
                              const FoldDesc& fd, const OutSink& out, const long long* base_in,
                              long long* total_out, int tile_f_hi = 0, const InstSet& is = InstSet{}) {
   if (n_chunks <= 0) {
@@ -586,15 +586,15 @@ sgagg_status launch_sortfold(sgagg_t h, int cls, const Chunk* dchunks, int n_chu
   if (h->test_stall == 1) h->test_stall = 0;
   kbegin(h, cls);
   if (fd.n_state <= 2)
-    launch_ks<MODE, 2>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
+    launch_ks<MODE, 2>(n_chunks, h->stream, dchunks, src, copy, fd, out, lb, tile_n, tile_f_hi, is);
   else if (fd.n_state <= 4)
-    launch_ks<MODE, 4>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
+    launch_ks<MODE, 4>(n_chunks, h->stream, dchunks, src, copy, fd, out, lb, tile_n, tile_f_hi, is);
   else if (fd.n_state <= 8)
-    launch_ks<MODE, 8>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
+    launch_ks<MODE, 8>(n_chunks, h->stream, dchunks, src, copy, fd, out, lb, tile_n, tile_f_hi, is);
   else if (fd.n_state <= 16)
-    launch_ks<MODE, 16>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
+    launch_ks<MODE, 16>(n_chunks, h->stream, dchunks, src, copy, fd, out, lb, tile_n, tile_f_hi, is);
   else
-    launch_ks<MODE, 32>(n_chunks, h->stream, dchunks, src, runs, copy, fd, out, lb, tile_n, tile_f_hi, is);
+    launch_ks<MODE, 32>(n_chunks, h->stream, dchunks, src, copy, fd, out, lb, tile_n, tile_f_hi, is);
   kend(h);
   CU(cudaGetLastError());
   return SGAGG_OK;
@@ -780,12 +780,11 @@ sgagg_status prefold(sgagg_t h, RowSrc* src, long long* n, FoldDesc* fd, int for
     for (int s = 0; s < S; ++s) o.cols[s] = P<long long>(cb[s]);
     o.capacity = *n;
     o.offs = nullptr;
-    RunSet rs{};
     CopySrc cs{};
     long long* tot = &dsmall(h)->pftot;
     InstSet grp{};
     grp.grouped = h->prefold_bins;
-    TRY(launch_sortfold<MODE_TILES>(h, SGAGG_K_PREFOLD, nullptr, (int)ntile, *n, *src, rs, cs, *fd, o,
+    TRY(launch_sortfold<MODE_TILES>(h, SGAGG_K_PREFOLD, nullptr, (int)ntile, *n, *src, cs, *fd, o,
                                     nullptr, tot, 0, grp));
     HostSmall* hs = hsmall(h);
     TRY(sync_read(h, &hs->v[0], tot, 8));
@@ -818,7 +817,6 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
   RowSrc src = src0;
   FoldDesc fd = fd0;
   HostSmall* hs = hsmall(h);
-  RunSet norun{};
   CopySrc nocopy{};
 
   // keys all equal / small: pre-fold decision from a sample (depth > 0 or
@@ -875,7 +873,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
 
   if (n <= kTileCap) {
     // one chunk, straight from the source (one tile covering the fine range)
-    TRY(launch_sortfold<MODE_TILES>(h, SGAGG_K_RUNGEN, nullptr, 1, n, src, norun, nocopy, fd, out, base_in,
+    TRY(launch_sortfold<MODE_TILES>(h, SGAGG_K_RUNGEN, nullptr, 1, n, src, nocopy, fd, out, base_in,
                                     total_out, out.offs ? (1 << dig.fbits) : 0));
     kbytes(h, SGAGG_K_RUNGEN, n * src_row_bytes(src));
     return SGAGG_OK;
@@ -1038,7 +1036,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     copy.keys = co.keys;
     for (int s = 0; s < S; ++s) copy.cols[s] = co.cols[s];
   }
-  TRY(launch_sortfold<MODE_RANGE>(h, SGAGG_K_RUNGEN, P<Chunk>(h->chunks[depth]), info.n_chunks, 0, aos, norun,
+  TRY(launch_sortfold<MODE_RANGE>(h, SGAGG_K_RUNGEN, P<Chunk>(h->chunks[depth]), info.n_chunks, 0, aos,
                                   copy, fd, out, base_in, total_out));
   kbytes(h, SGAGG_K_RUNGEN, n * 8ll * W);
   return SGAGG_OK;
@@ -1759,9 +1757,8 @@ sgagg_status runs_one_pass(sgagg_t h, const RowSrc& src, long long n, long long 
   OutSink oo = o;
   oo.offs_stride = stride;
   oo.offs_bbits = Db;
-  RunSet norun{};
   CopySrc nocopy{};
-  TRY(launch_sortfold<MODE_RANGE>(h, SGAGG_K_RUNGEN, P<Chunk>(h->chunks[0]), info.n_chunks, 0, aos, norun, nocopy,
+  TRY(launch_sortfold<MODE_RANGE>(h, SGAGG_K_RUNGEN, P<Chunk>(h->chunks[0]), info.n_chunks, 0, aos, nocopy,
                                   fd, oo, rs_dev, &ds->total));
   kbytes(h, SGAGG_K_RUNGEN, n * 8ll * W);
   kbegin(h, SGAGG_K_OTHER);
@@ -2294,9 +2291,8 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
       CU(cudaMemcpyAsync(h->bdirect.p, dch.data(), dch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, stream));
       OutSink o{};
       o.rows_sum = reinterpret_cast<unsigned long long*>(&ds->dsum);
-      RunSet norun{};
       CopySrc nocopy{};
-      TRY(launch_sortfold<MODE_DIRECT>(h, SGAGG_K_RUNGEN, P<Chunk>(h->bdirect), (int)dch.size(), 0, raw, norun,
+      TRY(launch_sortfold<MODE_DIRECT>(h, SGAGG_K_RUNGEN, P<Chunk>(h->bdirect), (int)dch.size(), 0, raw,
                                        nocopy, fd, o, nullptr, nullptr, 0, is));
       long long dn = 0;
       for (const Chunk& c : dch) dn += c.hi;
@@ -2383,11 +2379,10 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
     o.keys = P<unsigned long long>(h->bkeys);
     for (int a = 0; a < S; ++a) o.cols[a] = P<long long>(h->bcols[a]);
     o.capacity = grows;
-    RunSet norun{};
     CopySrc nocopy{};
     long long n1 = 0;
     if (ntiles) {
-      TRY(launch_sortfold<MODE_INST>(h, SGAGG_K_PREFOLD, P<Chunk>(h->bchunks), (int)ntiles, 0, raw, norun, nocopy,
+      TRY(launch_sortfold<MODE_INST>(h, SGAGG_K_PREFOLD, P<Chunk>(h->bchunks), (int)ntiles, 0, raw, nocopy,
                                      fd, o, nullptr, &ds->pftot, 0, is));
       TRY(sync_read(h, &hs->v[0], &ds->pftot, 8));
       TRY(check_device_err(h));
@@ -2617,18 +2612,17 @@ extern "C" sgagg_status sgagg_aggregate_noalloc(const sgagg_keys* keys, const in
     lb.base_in = nullptr;
     lb.spin_limit = 1ll << 26;
     lb.n_chunks = 1;
-    RunSet norun{};
     CopySrc nocopy{};
     if (fd.n_state <= 2)
-      launch_ks<MODE_TILES, 2>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+      launch_ks<MODE_TILES, 2>(1, st, nullptr, raw, nocopy, fd, o, lb, n, 0);
     else if (fd.n_state <= 4)
-      launch_ks<MODE_TILES, 4>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+      launch_ks<MODE_TILES, 4>(1, st, nullptr, raw, nocopy, fd, o, lb, n, 0);
     else if (fd.n_state <= 8)
-      launch_ks<MODE_TILES, 8>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+      launch_ks<MODE_TILES, 8>(1, st, nullptr, raw, nocopy, fd, o, lb, n, 0);
     else if (fd.n_state <= 16)
-      launch_ks<MODE_TILES, 16>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+      launch_ks<MODE_TILES, 16>(1, st, nullptr, raw, nocopy, fd, o, lb, n, 0);
     else
-      launch_ks<MODE_TILES, 32>(1, st, nullptr, raw, norun, nocopy, fd, o, lb, n, 0);
+      launch_ks<MODE_TILES, 32>(1, st, nullptr, raw, nocopy, fd, o, lb, n, 0);
     if (cudaGetLastError() != cudaSuccess) return na_fail(SGAGG_ECUDA, "sgagg_aggregate_noalloc: launch failed");
   }
   k_noalloc_finish<<<1, 1, 0, st>>>(reinterpret_cast<const int*>(base + kNaErr),
