@@ -765,6 +765,83 @@ __device__ void fold_scan(const uint32_t* hm, const uint16_t* hpre, const long l
   }
 }
 
+// fold_scan for the report pattern of one column -- its sum, min and max --
+// in one pass: the windows, head masks, segment lengths and value loads are
+// shared and the three scans interleaved; same results as fold_scan once per
+// aggregate.
+__device__ void fold_scan_smm(const uint32_t* hm, const uint16_t* hpre, const long long* col, int n, int fh, int xe,
+                              long long* dsum, long long* dmin, long long* dmax_, long long cap, long long base) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = 0xffffffffu >> (31 - lane);
+  long long cs = op_id<OP_SUM>(), cn = op_id<OP_MIN>(), cx = op_id<OP_MAX>();
+  long long ls = cs, ln = cn, lx = cx;
+  bool pend = false;  // warp-uniform: lane partials not yet in the carries
+  for (int b = fh & ~31; b < xe; b += 32) {
+    const unsigned hb = hm[b >> 5];
+    const unsigned hn = b + 32 < n ? hm[(b >> 5) + 1] : 1u;  // next window's heads (past n: a head)
+    const int p = b + lane;
+    const bool own = p >= fh && p < xe;
+    const long long raw = own ? col[p] : 0;
+    const long long vs = own ? raw : op_id<OP_SUM>(), vn = own ? raw : op_id<OP_MIN>(),
+                    vx = own ? raw : op_id<OP_MAX>();
+    if (hb == 0 && b >= fh && !(hn & 1u) && b + 32 < xe) {
+      // warp-uniform: the window lies inside one group, which goes on after it
+      ls = op_do<OP_SUM>(ls, vs);
+      ln = op_do<OP_MIN>(ln, vn);
+      lx = op_do<OP_MAX>(lx, vx);
+      pend = true;
+      continue;
+    }
+    if (pend) {
+      for (int o = 16; o > 0; o >>= 1) {
+        ls = op_do<OP_SUM>(ls, __shfl_xor_sync(0xffffffffu, ls, o));
+        ln = op_do<OP_MIN>(ln, __shfl_xor_sync(0xffffffffu, ln, o));
+        lx = op_do<OP_MAX>(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+      }
+      cs = op_do<OP_SUM>(cs, ls);
+      cn = op_do<OP_MIN>(cn, ln);
+      cx = op_do<OP_MAX>(cx, lx);
+      ls = op_id<OP_SUM>();
+      ln = op_id<OP_MIN>();
+      lx = op_id<OP_MAX>();
+      pend = false;
+    }
+    const unsigned le = hb & below;  // heads at or below the lane
+    const int ss = 31 - __clz(le);   // its group's head lane; -1: an earlier window
+    const int d = lane - max(ss, 0); // earlier lanes of its group in this window
+    const int dm = (int)__reduce_max_sync(0xffffffffu, (unsigned)d);
+    long long xs = vs, xn = vn, xx = vx;
+    for (int o = 1; o <= dm; o <<= 1) {
+      const long long us = __shfl_up_sync(0xffffffffu, xs, o);
+      const long long un = __shfl_up_sync(0xffffffffu, xn, o);
+      const long long ux = __shfl_up_sync(0xffffffffu, xx, o);
+      if (o <= d) {
+        xs = op_do<OP_SUM>(xs, us);
+        xn = op_do<OP_MIN>(xn, un);
+        xx = op_do<OP_MAX>(xx, ux);
+      }
+    }
+    if (ss < 0) {
+      xs = op_do<OP_SUM>(xs, cs);
+      xn = op_do<OP_MIN>(xn, cn);
+      xx = op_do<OP_MAX>(xx, cx);
+    }
+    cs = __shfl_sync(0xffffffffu, xs, 31);
+    cn = __shfl_sync(0xffffffffu, xn, 31);
+    cx = __shfl_sync(0xffffffffu, xx, 31);
+    // the last position of a group: the next one is a head (or the range ends)
+    const unsigned lastm = (hb >> 1) | (hn << 31);
+    if (own && (((lastm >> lane) & 1u) || p + 1 == xe)) {
+      const long long pos = base + (long long)hpre[b >> 5] + __popc(le) - 1;
+      if (pos < cap) {
+        dsum[pos] = xs;
+        dmin[pos] = xn;
+        dmax_[pos] = xx;
+      }
+    }
+  }
+}
+
 // Fold the sorted chunk: heads (first rows of key groups) into a bitmask and
 // the chunk's distinct-key count -> its output offset by look-back; keys and
 // count(*) per head; then the aggregates one source column at a time, the
@@ -906,6 +983,39 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const ChunkVie
       fold_few(s, fd, out, col, c, count, base);
       continue;
     }
+    // the report pattern on this column (exactly a sum, a min and a max):
+    // folded in one pass (block-uniform)
+    int a_sum = -1, a_min = -1, a_max = -1, n_on = 0;
+    for (int a = 0; a < ns; ++a) {
+      if (fd.src[a] != c) continue;
+      ++n_on;
+      if (fd.op[a] == OP_SUM) a_sum = a; else if (fd.op[a] == OP_MIN) a_min = a; else a_max = a;
+    }
+    // (compiled only where three aggregates fit: KS >= 3)
+    const bool smm = KS >= 3 && n_on == 3 && a_sum >= 0 && a_min >= 0 && a_max >= 0;
+    if (lanefold && smm) {
+      int run = g_lcnt[w];
+      for (int b = wb; b < we; b += 32) {
+        const int p = b + lane;
+        const unsigned hb = hm[b >> 5];
+        if ((hb >> lane) & 1u) {
+          const long long pos = base + run + __popc(hb & lt);
+          const int e = group_end(hm, p, n);
+          long long as = col[p], an = as, ax = as;
+          for (int q = p + 1; q < e; ++q) {
+            const long long v = col[q];
+            as = op_do<OP_SUM>(as, v);
+            an = op_do<OP_MIN>(an, v);
+            ax = op_do<OP_MAX>(ax, v);
+          }
+          sink_val(out, a_sum, pos, as);
+          sink_val(out, a_min, pos, an);
+          sink_val(out, a_max, pos, ax);
+        }
+        run += __popc(hb);
+      }
+      continue;
+    }
     if (lanefold) {
       // a lane per group (every group has at most 32 rows)
       int run = g_lcnt[w];
@@ -930,6 +1040,11 @@ __device__ void fold_sorted(const SortSmem& s, const RowSrc& src, const ChunkVie
       continue;
     }
     if (fh >= xe) continue;  // warp-uniform: no group of this warp
+    if (smm) {
+      fold_scan_smm(hm, hpre, col, n, fh, xe, out.cols[a_sum], out.cols[a_min], out.cols[a_max], out.capacity,
+                    base);
+      continue;
+    }
 #pragma unroll(KS <= 8 ? KS : 1)
     for (int a = 0; a < KS; ++a) {
       if (a < ns && fd.src[a] == c) {
