@@ -229,6 +229,24 @@ def test_prefold_switch_invariant(prefold):
     check(c["key_cols"], c["payload"], c["aggs"], M=100_000, prefold=prefold)
 
 
+@pytest.mark.parametrize("aggs", [
+    [(3, 0), (1, 0), (0, 0), (2, 0)],                  # max, sum, count, min: the pattern out of order
+    [(1, 0), (2, 0), (3, 0), (1, 0)],                  # a repeated sum: not the pattern
+    [(2, 1), (1, 0), (3, 1), (2, 0), (1, 1), (3, 0)],  # the pattern on two columns, interleaved
+])
+@pytest.mark.parametrize("n, D", [(8191, 8000), (60_000, 2000), (70_000, 7)])
+def test_aggregate_orders(aggs, n, D):
+    """Sum, min and max of one column are folded in one pass when they are
+    exactly that triple: each result must land in its own output column
+    whatever the aggregates' order, and other lists take the per-aggregate
+    fold.  Sizes cover one-row groups (a lane per group), small groups
+    (segmented scans) and a few large groups."""
+    c = datagen.config1(n=n, seed=31, D=D)
+    pay = [c["payload"][0], datagen.uniform_int(31, 7, n, -10**15, 10**15)]
+    check(c["key_cols"], pay, aggs, M=1 << 30)
+    check(c["key_cols"], pay, aggs, M=max(1, n // 5))
+
+
 @pytest.mark.parametrize("bins", [0, 1])
 def test_prefold_bins_invariant(bins):
     """Tile pre-aggregation binned by key range or by a hash of the key, on
