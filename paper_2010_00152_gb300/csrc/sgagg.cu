@@ -1611,8 +1611,18 @@ sgagg_status lowcard_device(sgagg_t h, const RowSrc& raw, long long n, const Fol
   }
   a.n_col = raw.ncols;
   const int T = (size_t)kd * S * 8 * 256 <= 110 * 1024 ? 256 : 128;
-  const size_t smem = (size_t)kd * S * 8 * T;
-  const int blocks = h->num_sms * (T == 256 && smem <= 110 * 1024 ? 2 : 1);
+  // the report pattern: count(*), then sum / min / max of every payload
+  // column in column order
+  int cp = (S >= 1 && (S - 1) % 3 == 0 && fd.src[0] < 0) ? (S - 1) / 3 : 0;
+  for (int c = 0; c < cp; ++c)
+    if (fd.src[1 + 3 * c] != c || fd.src[2 + 3 * c] != c || fd.src[3 + 3 * c] != c || fd.op[1 + 3 * c] != OP_SUM ||
+        fd.op[2 + 3 * c] != OP_MIN || fd.op[3 + 3 * c] != OP_MAX || raw.ncols != cp)
+      cp = 0;
+  if (cp > 4 || T != 256) cp = 0;
+  // the report kernel keeps one set of accumulators per lane pair (128 per
+  // block, three CTAs per SM); the general kernel one per thread
+  const size_t smem = (size_t)kd * S * 8 * (cp >= 1 ? 128 : T);
+  const int blocks = h->num_sms * (cp >= 1 ? 3 : (T == 256 && smem <= 110 * 1024 ? 2 : 1));
   TRY(grow(h, h->lc_part, (size_t)blocks * kd * std::max(1, S) * 8));
   a.partial = P<long long>(h->lc_part);
   Small* ds = dsmall(h);
@@ -1627,14 +1637,6 @@ sgagg_status lowcard_device(sgagg_t h, const RowSrc& raw, long long n, const Fol
     CU(cudaFuncSetAttribute(k_lowcard<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024));
     once.done(dev);
   }
-  // the report pattern: count(*), then sum / min / max of every payload
-  // column in column order
-  int cp = (S >= 1 && (S - 1) % 3 == 0 && fd.src[0] < 0) ? (S - 1) / 3 : 0;
-  for (int c = 0; c < cp; ++c)
-    if (fd.src[1 + 3 * c] != c || fd.src[2 + 3 * c] != c || fd.src[3 + 3 * c] != c || fd.op[1 + 3 * c] != OP_SUM ||
-        fd.op[2 + 3 * c] != OP_MIN || fd.op[3 + 3 * c] != OP_MAX || raw.ncols != cp)
-      cp = 0;
-  if (cp > 4 || T != 256) cp = 0;
   const int kl = raw.key.n_cols == 1 && raw.key.bytes[0] == 8 ? 1
                  : (raw.key.n_cols == 2 && raw.key.bytes[0] == 1 && raw.key.bytes[1] == 1 ? 2 : 0);
   static DeviceOnce once_r;
