@@ -1622,7 +1622,9 @@ sgagg_status lowcard_device(sgagg_t h, const RowSrc& raw, long long n, const Fol
   // the report kernel keeps one set of accumulators per lane pair (128 per
   // block, three CTAs per SM); the general kernel one per thread
   const size_t smem = (size_t)kd * S * 8 * (cp >= 1 ? 128 : T);
-  const int blocks = h->num_sms * (cp >= 1 ? 3 : (T == 256 && smem <= 110 * 1024 ? 2 : 1));
+  // the general kernel: as many blocks per SM as their accumulators fit (at
+  // most 4, 227 KB of shared memory per SM)
+  const int blocks = h->num_sms * (cp >= 1 ? 3 : (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024))));
   TRY(grow(h, h->lc_part, (size_t)blocks * kd * std::max(1, S) * 8));
   a.partial = P<long long>(h->lc_part);
   Small* ds = dsmall(h);
