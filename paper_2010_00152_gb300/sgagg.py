@@ -281,24 +281,67 @@ def sgagg_aggregate_batched(h, instances, aggs, stream=0):
 
 
 # ---- convenience wrapper over torch tensors ------------------------------
-class Aggregator:
-    """One handle.  aggregate() groups device tensors and returns tensors."""
+OPTION_NAMES = {"prefold": SGAGG_OPT_PREFOLD, "arena_cap": SGAGG_OPT_ARENA_CAP,
+                "radix_bits": SGAGG_OPT_RADIX_BITS, "spin_limit": SGAGG_OPT_SPIN_LIMIT,
+                "fanin_cap": SGAGG_OPT_FANIN_CAP, "fault_alloc": SGAGG_OPT_FAULT_ALLOC,
+                "timing": SGAGG_OPT_TIMING, "test_stall": SGAGG_OPT_TEST_STALL,
+                "policy": SGAGG_OPT_POLICY, "absorb_batch": SGAGG_OPT_ABSORB_BATCH,
+                "lowcard": SGAGG_OPT_LOWCARD, "merge_threads": SGAGG_OPT_MERGE_THREADS,
+                "hybrid_fanin": SGAGG_OPT_HYBRID_FANIN, "hybrid_f": SGAGG_OPT_HYBRID_F,
+                "hybrid_last": SGAGG_OPT_HYBRID_LAST, "merge_copy": SGAGG_OPT_MERGE_COPY,
+                "prefold_bins": SGAGG_OPT_PREFOLD_BINS, "prefold_rows": SGAGG_OPT_PREFOLD_ROWS,
+                "one_pass": SGAGG_OPT_ONE_PASS, "part_levels": SGAGG_OPT_PART_LEVELS,
+                "batch_group_rows": SGAGG_OPT_BATCH_GROUP_ROWS}
 
-    def __init__(self, memory_budget_rows, **options):
+# The options the autotuner may set, with the library's defaults (restored
+# when a later call's shape leaves one out).  All of them leave results
+# unchanged.
+TUNABLE_DEFAULTS = {"prefold": -1, "radix_bits": 0, "fanin_cap": 0, "merge_copy": 0, "prefold_bins": 0,
+                    "prefold_rows": 8192, "one_pass": 1, "part_levels": 0, "batch_group_rows": 1 << 25,
+                    "lowcard": 1, "merge_threads": 0}
+
+
+class Aggregator:
+    """One handle.  aggregate() groups device tensors and returns tensors.
+
+    autotune=True: before every call, the options the autotuner's cache
+    (tuning.py; `cache` = another cache file) gives for the call's shape are
+    set -- the duplicate share from the handle's previous call of the same
+    kind, when there was one.  Options passed here explicitly are left as
+    given.  `last_autotune` tells what was chosen."""
+
+    def __init__(self, memory_budget_rows, autotune=False, cache=None, **options):
         self.h = sgagg_create(memory_budget_rows)
-        names = {"prefold": SGAGG_OPT_PREFOLD, "arena_cap": SGAGG_OPT_ARENA_CAP,
-                 "radix_bits": SGAGG_OPT_RADIX_BITS, "spin_limit": SGAGG_OPT_SPIN_LIMIT,
-                 "fanin_cap": SGAGG_OPT_FANIN_CAP, "fault_alloc": SGAGG_OPT_FAULT_ALLOC,
-                 "timing": SGAGG_OPT_TIMING, "test_stall": SGAGG_OPT_TEST_STALL,
-                 "policy": SGAGG_OPT_POLICY, "absorb_batch": SGAGG_OPT_ABSORB_BATCH,
-                 "lowcard": SGAGG_OPT_LOWCARD, "merge_threads": SGAGG_OPT_MERGE_THREADS,
-                 "hybrid_fanin": SGAGG_OPT_HYBRID_FANIN, "hybrid_f": SGAGG_OPT_HYBRID_F,
-                 "hybrid_last": SGAGG_OPT_HYBRID_LAST, "merge_copy": SGAGG_OPT_MERGE_COPY,
-                 "prefold_bins": SGAGG_OPT_PREFOLD_BINS, "prefold_rows": SGAGG_OPT_PREFOLD_ROWS,
-                 "one_pass": SGAGG_OPT_ONE_PASS, "part_levels": SGAGG_OPT_PART_LEVELS,
-                 "batch_group_rows": SGAGG_OPT_BATCH_GROUP_ROWS}
         for k, v in options.items():
-            self.set_option(names[k], v)
+            self.set_option(OPTION_NAMES[k], v)
+        self.autotune = autotune
+        self._cache_path = cache
+        self._cache = None
+        self._user = set(options)
+        self._tuned = {}
+        self._last_dup = {}
+        self.last_autotune = None
+
+    def _apply_tuning(self, call, n_rows, key_bits, n_aggs):
+        from . import tuning
+        if self._cache is None:
+            self._cache = tuning.load(self._cache_path or tuning.CACHE)
+        key = tuning.shape_key(call, n_rows, key_bits, n_aggs, self._last_dup.get(call))
+        opts, source, matched = tuning.choose(key, self._cache)
+        opts = {k: v for k, v in opts.items() if k in TUNABLE_DEFAULTS and k not in self._user}
+        for k in [k for k in self._tuned if k not in opts]:
+            self.set_option(OPTION_NAMES[k], TUNABLE_DEFAULTS[k])
+            del self._tuned[k]
+        for k, v in opts.items():
+            if self._tuned.get(k) != v:
+                self.set_option(OPTION_NAMES[k], v)
+                self._tuned[k] = v
+        self.last_autotune = {"shape": key, "options": opts, "source": source, "matched": matched}
+
+    def _record_dup(self, call):
+        st = sgagg_stats(self.h)
+        if st["n_rows"] > 0:
+            self._last_dup[call] = 1.0 - st["out_rows"] / st["n_rows"]
 
     def close(self):
         if self.h is not None:
@@ -330,12 +373,16 @@ class Aggregator:
         else:
             ok, oa = out
         s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+        if self.autotune:
+            self._apply_tuning("aggregate", n, 8 * sum(k.element_size() for k in key_cols), len(aggs))
         sgagg_aggregate(self.h, [k.data_ptr() for k in key_cols], [k.element_size() for k in key_cols],
                         [p.data_ptr() for p in payload], n, aggs, [k.data_ptr() for k in ok],
                         [a.data_ptr() for a in oa], cap, s)
         if not sync:
             return ok, oa
         rows = sgagg_result_rows(self.h)
+        if self.autotune:
+            self._record_dup("aggregate")
         return [k[:rows] for k in ok], [a[:rows] for a in oa]
 
     def aggregate_batched(self, instances, aggs, capacities=None, stream=None):
@@ -361,8 +408,13 @@ class Aggregator:
                                         op.data_ptr(), cap, rows.data_ptr() + 8 * i))
             outs.append((ok, oa))
         s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+        if self.autotune:
+            self._apply_tuning("batched", sum(int(k.numel()) for k, _ in instances),
+                               8 * max([k.element_size() for k, _ in instances] or [1]), len(aggs))
         sgagg_aggregate_batched(self.h, descs, aggs, s)
         torch.cuda.synchronize(dev)
+        if self.autotune:
+            self._record_dup("batched")
         r = rows.cpu().tolist()
         res = []
         for i, (ok, oa) in enumerate(outs):

@@ -444,6 +444,39 @@ def test_batched_prefold_options(opts):
             np.testing.assert_array_equal(to_np(r[1][j]), ra[j])
 
 
+def test_batched_autotune(tmp_path):
+    """Aggregator(autotune=True) sets the options a cache gives for the
+    call's shape: here instance groups of 2^16 rows, seen as one
+    pre-aggregation pass per group.  Same results as the oracle."""
+    from paper_2010_00152_gb300 import tuning
+    sizes = [8193, 20_000, 70_001, 150_000, 9000]
+    domains = [20_000, 5, 100_000, 1_000_000, 60_000]
+    insts = _batched_case(6, sizes, domains)
+    aggs = [(0, 0), (1, 0), (2, 0), (3, 0)]
+    cache = {}
+    key = tuning.shape_key("batched", sum(sizes), 32, len(aggs))
+    for d in range(4):  # whatever duplicate share the first call measures
+        tuning.record(cache, key + "|d%d" % d, [({"batch_group_rows": 1 << 16}, 1.0)], "test")
+    path = tmp_path / "tuning.json"
+    tuning.save(cache, str(path))
+    agg = sgagg.Aggregator(1 << 20, autotune=True, cache=str(path))
+    try:
+        for _ in range(2):
+            res = agg.aggregate_batched([(k.to(DEV), [p.to(DEV) for p in pay]) for k, pay in insts], aggs)
+            for (k, pay), r in zip(insts, res):
+                rk, ra = oracle_run([k], pay, aggs)
+                np.testing.assert_array_equal(to_np(r[0]), rk[0])
+                for j in range(len(aggs)):
+                    np.testing.assert_array_equal(to_np(r[1][j]), ra[j])
+        st = agg.stats()
+        chosen = agg.last_autotune
+    finally:
+        agg.close()
+    assert chosen["options"] == {"batch_group_rows": 1 << 16}, chosen
+    assert chosen["source"] in ("cache", "nearest")
+    assert st["prefold_passes"] > 1
+
+
 def test_batched_clustered_instances():
     """Instances whose keys crowd one end of their range (one bucket of the
     per-instance digit far above a chunk), one key value, and a wide spread;
