@@ -25,8 +25,8 @@ def case(n, D, seed):
     return k, pay
 
 
-def run(k, pay, M, F, f, last=None):
-    opts = dict(policy=2, hybrid_fanin=F, hybrid_f=f)
+def run(k, pay, M, F, f, last=None, **extra):
+    opts = dict(policy=2, hybrid_fanin=F, hybrid_f=f, **extra)
     if last is not None:
         opts["hybrid_last"] = last
     agg = sgagg.Aggregator(M, **opts)
@@ -37,8 +37,8 @@ def run(k, pay, M, F, f, last=None):
         agg.close()
 
 
-def check(k, pay, M, F, f, last):
-    gk, ga, st, sizes = run(k, pay, M, F, f, last)
+def check(k, pay, M, F, f, last, **extra):
+    gk, ga, st, sizes = run(k, pay, M, F, f, last, **extra)
     kn, pn = k.numpy(), [p.numpy() for p in pay]
     runs, absorbed, resident, (rk, ra) = oracle.hybrid_runs(kn, pn, AGGS, M, F, f, last)
     np.testing.assert_array_equal(gk, rk)
@@ -59,6 +59,18 @@ def test_hybrid_matches_oracle(M, F, D, n):
     last = oracle.hybrid_bound(k.numpy(), M, F, f)
     st, runs = check(k, pay, M, F, f, last)
     assert st["runs"] == len(runs)  # at most 256 runs: one wide merge takes them all
+
+
+@pytest.mark.parametrize("one_pass", [1, 0])
+def test_hybrid_runs_in_one_pass(one_pass):
+    """Spilled rows in runs of more than one chunk (f/F * M = 50,000 rows):
+    their runs generated in one pass, or a batch at a time.  The output and
+    every run's row count equal the oracle's."""
+    n, D, M, F, f = 400_003, 150_000, 100_000, 4, 2
+    k, pay = case(n, D, 7)
+    last = oracle.hybrid_bound(k.numpy(), M, F, f)
+    st, runs = check(k, pay, M, F, f, last, one_pass=one_pass)
+    assert len(runs) > 1 and st["one_pass"] == one_pass
 
 
 def test_hybrid_paper_example_shape():

@@ -147,6 +147,20 @@ def test_runs_one_pass_or_batch_at_a_time(one_pass, shape):
     assert sizes == [int(r) for r in rows]
 
 
+@pytest.mark.parametrize("opts", [dict(), dict(fanin_cap=4)])
+def test_runs_one_pass_composite_key(opts):
+    """A composite key of two 16-bit columns over 8 batches of 40,000 rows:
+    all runs in one pass, then one wide merge (or preliminary merges of at
+    most 4 runs first).  Same output as the oracle."""
+    n = 320_000
+    k0 = datagen.uniform_int(41, 1, n, 0, 300).to(torch.int64).to(torch.uint16)
+    k1 = datagen.uniform_int(41, 2, n, 0, 999).to(torch.int64).to(torch.uint16)
+    pay = [datagen.uniform_int(41, 3, n, -10**9, 10**9)]
+    st, _ = check([k0, k1], pay, AGG4, M=40_000, prefold=0, **opts)
+    # 8 runs from the batches; with the fan-in cap, preliminary merges write more
+    assert st["one_pass"] == 1 and (st["runs"] == 8 if not opts else st["runs"] > 8)
+
+
 def test_c2_report_shape_prefold():
     c = datagen.config2(n=1 << 22, seed=2)
     st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=c["M"], lowcard=0)
