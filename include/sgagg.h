@@ -197,10 +197,14 @@ typedef enum {
                                      (default) two staged levels above 2^7 buckets, else
                                      one; 1 always one level (every row written once to
                                      its final bucket).  Same result. */
-    SGAGG_OPT_BATCH_GROUP_ROWS = 21 /* sgagg_aggregate_batched: rows of the multi-chunk
+    SGAGG_OPT_BATCH_GROUP_ROWS = 21, /* sgagg_aggregate_batched: rows of the multi-chunk
                                      instances grouped in one pass (2^16..2^31, default
                                      2^25); bigger groups mean fewer passes and host round
                                      trips and more scratch memory.  Same result. */
+    SGAGG_OPT_TIMING_CLASSES = 22 /* with SGAGG_OPT_TIMING on: the kernel classes timed, a
+                                     mask of bits 1 << SGAGG_K_* (default: all).  Two
+                                     events per timed launch cost about 1.4 us of GPU time
+                                     each; timing one class keeps that off the others. */
 } sgagg_option;
 
 /*

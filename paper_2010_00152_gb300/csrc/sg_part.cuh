@@ -706,6 +706,11 @@ k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, u
 // One CTA per level-1 bucket: turns the bucket's tile histograms into absolute
 // write positions (thist2, in place) and writes the final bucket totals
 // btot[b * nb2 + d] (fine-grained buckets in key order).
+// A thread walks its digit's column of tile counts kScan2Batch tiles at a
+// time: the batch's loads are issued before its stores, so a bucket of T
+// tiles waits on about T / kScan2Batch memory latencies instead of T.
+constexpr int kScan2Batch = 8;
+
 __global__ void __launch_bounds__(kPartThreads)
 k_scan2(const long long* bstart1, int nb2, const int* tfirst, unsigned* thist2, long long* btot) {
   const int b = blockIdx.x;
@@ -713,16 +718,29 @@ k_scan2(const long long* bstart1, int nb2, const int* tfirst, unsigned* thist2, 
   const int d = threadIdx.x;
   int tot = 0;
   if (d < nb2)
-    for (int t = t0; t < t1; ++t) {
-      unsigned c = thist2[(long long)t * nb2 + d];
-      thist2[(long long)t * nb2 + d] = (unsigned)tot;
-      tot += (int)c;
+    for (int t = t0; t < t1; t += kScan2Batch) {
+      unsigned c[kScan2Batch];
+#pragma unroll
+      for (int u = 0; u < kScan2Batch; ++u) c[u] = t + u < t1 ? thist2[(long long)(t + u) * nb2 + d] : 0u;
+#pragma unroll
+      for (int u = 0; u < kScan2Batch; ++u)
+        if (t + u < t1) {
+          thist2[(long long)(t + u) * nb2 + d] = (unsigned)tot;
+          tot += (int)c[u];
+        }
     }
   int all;
   int ex = block_excl_sum(d < nb2 ? tot : 0, &all);
   if (d < nb2) {
     const unsigned start = (unsigned)(bstart1[b] + ex);
-    for (int t = t0; t < t1; ++t) thist2[(long long)t * nb2 + d] += start;
+    for (int t = t0; t < t1; t += kScan2Batch) {
+      unsigned c[kScan2Batch];
+#pragma unroll
+      for (int u = 0; u < kScan2Batch; ++u) c[u] = t + u < t1 ? thist2[(long long)(t + u) * nb2 + d] : 0u;
+#pragma unroll
+      for (int u = 0; u < kScan2Batch; ++u)
+        if (t + u < t1) thist2[(long long)(t + u) * nb2 + d] = c[u] + start;
+    }
     btot[(long long)b * nb2 + d] = tot;
   }
 }

@@ -120,6 +120,8 @@ struct sgagg_ctx {
   int fault_alloc = 0;
   int alloc_count = 0;
   int timing = 0;
+  long long timing_mask = -1;    // SGAGG_OPT_TIMING_CLASSES
+  bool timer_open = false;       // kbegin recorded the start event of the open launch
   int test_stall = 0;
   int policy = 0;                // 0: a run per batch, 1: absorbing index
   long long absorb_batch = 0;    // rows per batch of the absorbing policy (0: auto)
@@ -309,7 +311,8 @@ sgagg_status fail(sgagg_t h, sgagg_status s, const char* fmt, const char* a = ""
 void kbegin(sgagg_t h, int cls) {
   ++h->st.class_launches[cls];
   ++h->st.kernel_launches;
-  if (!h->timing) return;
+  h->timer_open = h->timing && ((h->timing_mask >> cls) & 1);
+  if (!h->timer_open) return;
   if (h->ntimers == (int)h->timers.size()) {
     sgagg_ctx::KT t;
     cudaEventCreate(&t.a);
@@ -322,7 +325,8 @@ void kbegin(sgagg_t h, int cls) {
 }
 
 void kend(sgagg_t h) {
-  if (!h->timing) return;
+  if (!h->timer_open) return;
+  h->timer_open = false;
   cudaEventRecord(h->timers[h->ntimers].b, h->stream);
   ++h->ntimers;
   h->timers_read = false;
@@ -2775,6 +2779,9 @@ sgagg_status sgagg_set_option(sgagg_t h, int32_t key, int64_t value) {
     case SGAGG_OPT_BATCH_GROUP_ROWS:
       if (value < (1 << 16) || value > (1ll << 31)) return fail(h, SGAGG_EINVAL, "batch group rows must be 2^16..2^31");
       h->batch_group_rows = value;
+      return SGAGG_OK;
+    case SGAGG_OPT_TIMING_CLASSES:
+      h->timing_mask = value;
       return SGAGG_OK;
     default: return fail(h, SGAGG_EINVAL, "unknown option");
   }

@@ -23,7 +23,7 @@ SGAGG_COUNT, SGAGG_SUM, SGAGG_MIN, SGAGG_MAX = range(4)
  SGAGG_OPT_POLICY, SGAGG_OPT_ABSORB_BATCH, SGAGG_OPT_LOWCARD, SGAGG_OPT_MERGE_THREADS,
  SGAGG_OPT_HYBRID_FANIN, SGAGG_OPT_HYBRID_F, SGAGG_OPT_HYBRID_LAST, SGAGG_OPT_HYBRID_LAST_AUTO,
  SGAGG_OPT_MERGE_COPY, SGAGG_OPT_PREFOLD_BINS, SGAGG_OPT_PREFOLD_ROWS, SGAGG_OPT_ONE_PASS,
- SGAGG_OPT_PART_LEVELS, SGAGG_OPT_BATCH_GROUP_ROWS) = range(22)
+ SGAGG_OPT_PART_LEVELS, SGAGG_OPT_BATCH_GROUP_ROWS, SGAGG_OPT_TIMING_CLASSES) = range(23)
 
 
 class sgagg_agg(ctypes.Structure):
@@ -291,7 +291,7 @@ OPTION_NAMES = {"prefold": SGAGG_OPT_PREFOLD, "arena_cap": SGAGG_OPT_ARENA_CAP,
                 "hybrid_last": SGAGG_OPT_HYBRID_LAST, "merge_copy": SGAGG_OPT_MERGE_COPY,
                 "prefold_bins": SGAGG_OPT_PREFOLD_BINS, "prefold_rows": SGAGG_OPT_PREFOLD_ROWS,
                 "one_pass": SGAGG_OPT_ONE_PASS, "part_levels": SGAGG_OPT_PART_LEVELS,
-                "batch_group_rows": SGAGG_OPT_BATCH_GROUP_ROWS}
+                "batch_group_rows": SGAGG_OPT_BATCH_GROUP_ROWS, "timing_classes": SGAGG_OPT_TIMING_CLASSES}
 
 # The options the autotuner may set, with the library's defaults (restored
 # when a later call's shape leaves one out).  All of them leave results

@@ -211,6 +211,22 @@ def test_c3_shape_reduced():
     assert st["runs"] == 16 and st["run_rows"] == sum(rows)
 
 
+@pytest.mark.parametrize("mask", [-1, 1 << sgagg.KERNEL_CLASSES.index("merge"), 0])
+def test_timing_classes(mask):
+    """Per-launch CUDA-event timing of some kernel classes only: the result
+    is the oracle's, timed classes report time, the others none, and every
+    launch is still counted."""
+    c = datagen.config3(n=1 << 21, seed=2, D=1 << 20, M=1 << 17)
+    st, _ = check(c["key_cols"], c["payload"], c["aggs"], M=c["M"], timing=1, timing_classes=mask)
+    k = st["kernels"]
+    for i, name in enumerate(sgagg.KERNEL_CLASSES):
+        if k[name]["launches"] == 0:
+            continue
+        assert (k[name]["ms"] > 0) == bool((mask >> i) & 1), (name, k[name])
+    assert k["merge"]["launches"] == 3 and k["rungen"]["launches"] >= 1
+    assert st["kernel_launches"] == sum(v["launches"] for v in k.values())
+
+
 @pytest.mark.parametrize("widths", [[1], [2], [4], [8], [1, 1], [2, 4], [1, 2, 1], [4, 4], [1, 1, 1, 1, 1, 1, 1, 1]])
 def test_composite_keys(widths):
     n = 120_000
