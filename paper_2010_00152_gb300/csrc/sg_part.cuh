@@ -93,7 +93,9 @@ k_hist(RowSrc src, long long n, Digit dig, int dshift, int nb, int ntiles, unsig
   long long lo, hi;
   const unsigned boff = tile_rows(n, ntiles, dig, blockIdx.x, &lo, &hi);
   const int nlev = dig.brows ? (1 << dig.bbits) : nb;  // buckets of one batch
-  constexpr int U = 8;  // independent loads in flight per thread
+  // independent loads in flight per thread: the grid is two CTAs per SM (the
+  // scatter's tiles), so each thread keeps 16 keys (128 B) coming
+  constexpr int U = 16;
   for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += (long long)U * blockDim.x) {
     unsigned long long k[U];
 #pragma unroll
@@ -607,7 +609,7 @@ constexpr int kStageCols = 4;        // carried columns the staged scatter handl
 constexpr int kTile2 = 8192;         // rows per level-2 tile
 
 // Exclusive prefix of w[0..nb) into out[0..nb] (single CTA of kPartThreads).
-__global__ void __launch_bounds__(kPartThreads) k_excl_scan(const long long* w, int nb, long long* out) {
+__device__ __forceinline__ void excl_scan_block(const long long* w, int nb, long long* out) {
   __shared__ long long carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
@@ -625,6 +627,10 @@ __global__ void __launch_bounds__(kPartThreads) k_excl_scan(const long long* w, 
   if (threadIdx.x == 0) out[nb] = carry;
 }
 
+__global__ void __launch_bounds__(kPartThreads) k_excl_scan(const long long* w, int nb, long long* out) {
+  excl_scan_block(w, nb, out);
+}
+
 struct Tile2 {
   long long lo, hi;   // rows of the level-1 output
   int bucket;         // level-1 bucket
@@ -633,8 +639,7 @@ struct Tile2 {
 
 // Level-2 tiles: bucket b of the level-1 output is cut into ceil(size/kTile2)
 // tiles; tfirst[b] = index of its first tile, tfirst[nb1] = tile count.
-__global__ void __launch_bounds__(kPartThreads)
-k_tiles2(const long long* bstart1, int nb1, Tile2* tiles, int* tfirst) {
+__device__ __forceinline__ void tiles2_block(const long long* bstart1, int nb1, Tile2* tiles, int* tfirst) {
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
@@ -667,7 +672,27 @@ k_tiles2(const long long* bstart1, int nb1, Tile2* tiles, int* tfirst) {
   if (threadIdx.x == 0) tfirst[nb1] = carry;
 }
 
+// Level-1 bucket starts from their totals, then the level-2 tiles over them
+// (one CTA; the tiles depend only on the starts, so they are cut before the
+// level-1 scatter runs, in the same launch).
+__global__ void __launch_bounds__(kPartThreads)
+k_scan_tiles2(const long long* btot1, int nb1, long long* bstart1, Tile2* tiles, int* tfirst) {
+  excl_scan_block(btot1, nb1, bstart1);
+  __syncthreads();  // bstart1 (global, written by this CTA) is read below
+  tiles2_block(bstart1, nb1, tiles, tfirst);
+}
+
 // Level-2 histograms: thist2[t * nb2 + d] = rows of tile t with digit d.
+// A tile is only kTile2 rows (16 per thread), so the private histograms are
+// shared by groups of warps (warp w adds to copy w % kHist2Copies): a copy
+// per warp (16 x 256 counters zeroed, then summed) is as many shared-memory
+// operations as the tile's rows take to count.
+constexpr int kHist2Copies = 4;
+
+inline size_t hist2_smem_bytes(int nb2) {
+  return (size_t)(nb2 <= kPrivBuckets ? nb2 * kHist2Copies : nb2) * 4;
+}
+
 template <bool SEG, bool DIRECT>
 __global__ void __launch_bounds__(kPartThreads)
 k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, unsigned* thist2) {
@@ -675,8 +700,8 @@ k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, u
   const int t = blockIdx.x;
   if (t >= *ntiles) return;
   const bool priv = nb2 <= kPrivBuckets;
-  unsigned* mine = priv ? sh2 + (threadIdx.x >> 5) * nb2 : sh2;
-  const int nh = priv ? nb2 * (blockDim.x >> 5) : nb2;
+  unsigned* mine = priv ? sh2 + ((threadIdx.x >> 5) % kHist2Copies) * nb2 : sh2;
+  const int nh = priv ? nb2 * kHist2Copies : nb2;
   for (int d = threadIdx.x; d < nh; d += blockDim.x) sh2[d] = 0;
   __syncthreads();
   const Tile2 tl = tiles[t];
@@ -698,7 +723,7 @@ k_hist2(RowSrc src, Digit dig, int nb2, const Tile2* tiles, const int* ntiles, u
   for (int d = threadIdx.x; d < nb2; d += blockDim.x) {
     unsigned v = sh2[d];
     if (priv)
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v += sh2[w * nb2 + d];
+      for (int w = 1; w < kHist2Copies; ++w) v += sh2[w * nb2 + d];
     thist2[(long long)t * nb2 + d] = v;
   }
 }

@@ -976,7 +976,8 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     kbegin(h, SGAGG_K_PLAN);
     k_tilescan<<<(nb1 * 32 + 255) / 256, 256, 0, h->stream>>>(P<unsigned>(h->thist1[depth]), nb1, ntiles,
                                                             P<long long>(h->btot1[depth]));
-    k_excl_scan<<<1, kPartThreads, 0, h->stream>>>(P<long long>(h->btot1[depth]), nb1, P<long long>(h->bstart1[depth]));
+    k_scan_tiles2<<<1, kPartThreads, 0, h->stream>>>(P<long long>(h->btot1[depth]), nb1, P<long long>(h->bstart1[depth]),
+                                                     P<Tile2>(h->tiles2[depth]), P<int>(h->tfirst[depth]));
     kend(h);
     ++h->st.class_launches[SGAGG_K_PLAN];
     ++h->st.kernel_launches;
@@ -993,12 +994,8 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
     a.keys = P<unsigned long long>(h->akeys[depth]);
     for (int c = 0; c < C; ++c) a.cols[c] = acp[c];
     int* ntd = P<int>(h->tfirst[depth]) + nb1;
-    kbegin(h, SGAGG_K_PLAN);
-    k_tiles2<<<1, kPartThreads, 0, h->stream>>>(P<long long>(h->bstart1[depth]), nb1, P<Tile2>(h->tiles2[depth]),
-                                               P<int>(h->tfirst[depth]));
-    kend(h);
     kbegin(h, SGAGG_K_HIST);
-    HIST_LAUNCH(k_hist2, a, ((int)nt2max, kPartThreads, hist_smem_bytes(nb2, kPartThreads), h->stream),
+    HIST_LAUNCH(k_hist2, a, ((int)nt2max, kPartThreads, hist2_smem_bytes(nb2), h->stream),
                 (a, dig, nb2, P<Tile2>(h->tiles2[depth]), ntd, P<unsigned>(h->thist2[depth])));
     kend(h);
     kbytes(h, SGAGG_K_HIST, n * 8ll + nt2max * nb2 * 4);
