@@ -55,3 +55,25 @@ def test_traffic_key_ignores_comments_only():
     assert bench._code_only(code) == bench._code_only("int f(int a) {\n\n    return a + 1;\n}\n")
     assert bench._code_only(code) != bench._code_only("int f(int a) {\n  return a + 2;\n}\n")
     assert len(bench.src_sha()) == 16
+
+
+def test_traffic_keyed_to_the_class_headers(tmp_path, monkeypatch):
+    """A class's DRAM counters stay valid while the headers its kernels are
+    compiled from keep their code; any other header may change."""
+    import bench
+    csrc = tmp_path / "paper_2010_00152_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    for f, body in (("sg_common.cuh", "int a;"), ("sg_sortfold.cuh", "int b;"), ("sg_merge.cuh", "int c;"),
+                    ("sg_part.cuh", "int d;")):
+        (csrc / f).write_text(body)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.src_sha(bench.CLASS_HEADERS["merge"])
+    (tmp_path / "profiles" / "traffic.json").write_text(
+        '{"merge": {"dram_bytes_per_launch": 123, "src_sha": "%s"}}' % sha)
+    assert bench.traffic_for("merge") == 123
+    assert bench.traffic_for("rungen") is None                    # no counters for that class
+    (csrc / "sg_part.cuh").write_text("int d;  // comment\nint e;")  # a partition kernel changes
+    assert bench.traffic_for("merge") == 123
+    (csrc / "sg_merge.cuh").write_text("int c2;")                  # the merge kernel changes
+    assert bench.traffic_for("merge") is None
