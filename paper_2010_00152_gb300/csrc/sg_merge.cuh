@@ -646,11 +646,19 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
   const LookBack& lb = a.lb;
   const OutSink& out = a.out;
 
+  const int cid = blockIdx.x;
+  // the control warp's first 32 slice bounds and everyone's chunk are read
+  // before the barrier, so their latency overlaps it (tslo holds
+  // (n_chunks + 1) x k entries and every tile, copy chunks too, has a row)
+  long long lo0 = 0, hi0 = 0;
+  if (control && lane < a.runs.k) {
+    lo0 = a.tslo[(long long)cid * a.runs.k + lane];
+    hi0 = a.tslo[(long long)(cid + 1) * a.runs.k + lane];
+  }
+  const Chunk ch = a.chunks[cid];
   if (tid == THREADS) s_err = err_load(lb.err);
   __syncthreads();
-  const int cid = blockIdx.x;
   if (s_err) return;  // block-uniform
-  const Chunk ch = a.chunks[cid];
 
   if (ch.kind == CH_COPY) {  // a key range solved apart: its rows are copied verbatim
     const long long n = ch.hi - ch.lo;
@@ -686,8 +694,8 @@ __global__ void __launch_bounds__(THREADS + 32, (THREADS <= 256 ? 3 : 2)) k_merg
       long long lo = 0;
       int len = 0, ph = 0, cnt = 0;
       if (r < k) {
-        lo = a.tslo[(long long)cid * k + r];
-        const long long hi = a.tslo[(long long)(cid + 1) * k + r];
+        lo = b == 0 ? lo0 : a.tslo[(long long)cid * k + r];
+        const long long hi = b == 0 ? hi0 : a.tslo[(long long)(cid + 1) * k + r];
         len = (int)min(max(hi - lo, 0ll), (long long)capk);  // oversized tiles are refused below
         ph = (a.bulk != 0 && len > 0) ? (int)(lo & 1) : 0;
         cnt = len == 0 ? 0 : ((len + ph + 1) & ~1);

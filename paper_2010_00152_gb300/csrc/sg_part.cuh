@@ -21,9 +21,12 @@ constexpr int kPartThreads = 512;
 constexpr int kPrivBuckets = 256;   // per-warp private histograms up to this many buckets
 
 // Keys of `count` rows spread evenly over [0, n), for the planner's probe.
+// Row floor(i * n / count) for sample i, in 64-bit arithmetic: with
+// n = q * count + rem, it is i * q + floor(i * rem / count) (i, rem < count).
 __global__ void k_sample(RowSrc src, long long n, int count, unsigned long long* out) {
+  const long long q = n / count, rem = n % count;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    long long r = (long long)((__int128)i * n / count);
+    const long long r = (long long)i * q + ((long long)i * rem) / count;
     out[i] = src_key(src, r);
   }
 }

@@ -889,7 +889,7 @@ sgagg_status solve(sgagg_t h, const RowSrc& src0, long long n, const FoldDesc& f
       int cnt = (int)std::min<long long>(n, 4096);
       TRY(grow(h, h->sample, (size_t)kSample * 8));
       kbegin(h, SGAGG_K_PROBE);
-      k_sample<<<8, 256, 0, h->stream>>>(src, n, cnt, P<unsigned long long>(h->sample));
+      k_sample<<<std::max(1, (cnt + 255) / 256), 256, 0, h->stream>>>(src, n, cnt, P<unsigned long long>(h->sample));
       kend(h);
       TRY(sync_read(h, hs->sample, h->sample.p, (size_t)cnt * 8));
       unsigned long long mn, mx;
@@ -2135,7 +2135,7 @@ sgagg_status aggregate_device(sgagg_t h, const sgagg_keys* keys, const int64_t* 
     host_sample(*h->hio, raw.key, n, scount, hs->sample);
   } else {
     kbegin(h, SGAGG_K_PROBE);
-    k_sample<<<16, 256, 0, stream>>>(raw, n, scount, P<unsigned long long>(h->sample));
+    k_sample<<<std::max(1, (scount + 255) / 256), 256, 0, stream>>>(raw, n, scount, P<unsigned long long>(h->sample));
     kend(h);
     TRY(sync_read(h, hs->sample, h->sample.p, (size_t)scount * 8));
   }
@@ -2508,7 +2508,7 @@ sgagg_status aggregate_batched(sgagg_t h, const sgagg_instance* inst, int32_t co
         int cnt = (int)std::min<long long>(n1, 4096);
         TRY(grow(h, h->sample, (size_t)kSample * 8));
         kbegin(h, SGAGG_K_PROBE);
-        k_sample<<<8, 256, 0, stream>>>(part, n1, cnt, P<unsigned long long>(h->sample));
+        k_sample<<<std::max(1, (cnt + 255) / 256), 256, 0, stream>>>(part, n1, cnt, P<unsigned long long>(h->sample));
         kend(h);
         TRY(sync_read(h, hs->sample, h->sample.p, (size_t)cnt * 8));
         unsigned long long mn, mx;
